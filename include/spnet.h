@@ -1,0 +1,251 @@
+/*
+ * spnet.h -- C ABI of the GB300 solver for spatial network models.
+ *
+ * The library solves (K u, v) = (f, v) for u in V (the node functions that
+ * vanish on the Dirichlet set, Section 3, eq. weakform) by preconditioned
+ * conjugate gradients (Section 4.2) with the two-level additive Schwarz
+ * preconditioner of Section 4.1:
+ *
+ *     B r = R_0^T A_0^{-1} R_0 r + sum_j E_j A_j^{-1} E_j^T r,
+ *
+ * where R_0 evaluates the Q1 basis of the Cartesian mesh T_H (Section 2.3) at
+ * the network's free dofs, A_0 = R_0 A R_0^T, and A_j is the block of the free
+ * matrix A on the patch U(y_j) of mesh node y_j (eq. defPj).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: SPNET_OK (0) or a negative SPNET_ERR_* code;
+ *    spnet_last_error() gives the message of the last failure on the calling
+ *    thread.
+ *  - `mem` says where every array argument of that call lives:
+ *    SPNET_MEM_HOST (ordinary host memory) or SPNET_MEM_DEVICE (device memory
+ *    of the current CUDA device).  Input arrays are borrowed for the duration
+ *    of the call and copied; output arrays are owned by the caller.
+ *  - Dofs are numbered node-major: dof = ndof * node + component.
+ *  - `stream` is a cudaStream_t (passed as void*); 0 means the legacy default
+ *    stream.  All work of an operator and of its preconditioners is issued on
+ *    the operator's stream.  Calls return after their results are complete.
+ *  - Handles are opaque and owned by the library until *_destroy.  A
+ *    preconditioner keeps a reference to its operator: destroy it first.
+ *  - Nothing here is thread-safe per handle; distinct handles may be used
+ *    from distinct threads.
+ */
+#ifndef SPNET_H
+#define SPNET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPNET_OK 0
+#define SPNET_ERR_BAD_INPUT (-1)       /* malformed arguments, asymmetric K, NaN, bad indices */
+#define SPNET_ERR_NOT_SPD (-2)         /* a pivot <= 0 in a local or coarse factorisation */
+#define SPNET_ERR_NO_MEMORY (-3)       /* device allocation failed */
+#define SPNET_ERR_NO_CONVERGENCE (-4)  /* maxit reached; the iterate is still returned */
+#define SPNET_ERR_TIMEOUT (-5)         /* a bounded device wait expired */
+#define SPNET_ERR_CUDA (-6)            /* a CUDA runtime error */
+#define SPNET_ERR_UNSUPPORTED (-7)     /* a size beyond the limits of this build */
+#define SPNET_ERR_BAD_H (-8)           /* l_i / H is not an integer >= 1 */
+
+#define SPNET_MEM_HOST 0
+#define SPNET_MEM_DEVICE 1
+
+#define SPNET_MODEL_SCALAR 0  /* eq. scalarmodel: K = sum_e c_e (d_i - d_j)(d_i - d_j)^T */
+#define SPNET_MODEL_TRUSS3 1  /* eq. tensile + lateral term: 3x3 blocks c_e (n n^T + 0.1 I) */
+
+#define SPNET_PREC_FP64 0   /* factors, coarse inverse and local solves in FP64 */
+#define SPNET_PREC_MIXED 1  /* factors and coarse inverse stored and applied in FP32 */
+
+#define SPNET_STARS_INTERIOR 0  /* stars at mesh nodes off the boundary of Omega */
+#define SPNET_STARS_ALL 1       /* stars at every mesh node y_1..y_m (Section 4.1) */
+
+typedef struct spnet_op_s* spnet_op_t;
+typedef struct spnet_pc_s* spnet_pc_t;
+
+typedef struct {
+  int precision;     /* SPNET_PREC_* (default SPNET_PREC_MIXED) */
+  int star_set;      /* SPNET_STARS_* (default SPNET_STARS_INTERIOR) */
+  int flexible;      /* 1: Polak-Ribiere beta (r, z - z_old)/(r_old, z_old); 0: textbook
+                        beta; -1: flexible iff precision is MIXED (default -1) */
+  int max_restarts;  /* restarts from the recomputed residual (default 2) */
+  int reserved[12];
+} spnet_options;
+
+typedef struct {
+  int iterations;          /* products with A (CG steps) */
+  int restarts;            /* restarts from the recomputed residual */
+  int converged;           /* 1 if the recomputed relative residual <= rtol */
+  int status;              /* SPNET_OK or SPNET_ERR_NO_CONVERGENCE */
+  double relres;           /* ||b - A x||_2 / ||b||_2, recomputed in FP64 at the end */
+  double relres_recursive; /* the recursive residual when the iteration stopped */
+  double solve_ms;         /* device time of this right-hand side's solve */
+  double reserved[4];
+} spnet_stats;
+
+typedef struct {
+  int64_t n_dof, n_free, n_dirichlet, nnz_ff, nnz_fd;
+  int dim, ndof;
+  int64_t reserved[6];
+} spnet_op_info;
+
+typedef struct {
+  int nH[3];            /* elements per axis */
+  int n_elem, n_mesh;   /* elements, mesh nodes */
+  int m0;               /* coarse dofs (dimension of V_H) */
+  int n_stars;          /* non-empty stars */
+  int max_star;         /* largest star (dofs) */
+  int64_t sum_star;     /* sum of star sizes */
+  int64_t factor_nnz;   /* off-diagonal entries of all local Cholesky factors */
+  int64_t total_levels; /* sum over stars of the level count of the local solves */
+  int max_levels;       /* largest level count of one star */
+  int precision, star_set, flexible;
+  double setup_ms;      /* device time of setup_preconditioner */
+  int64_t device_bytes; /* device memory held by the preconditioner */
+  int64_t reserved[5];
+} spnet_pc_info;
+
+/* spnet_assemble -- assemble K on all n_nodes*ndof dofs from an edge list.
+ *
+ * Scalar model (model = SPNET_MODEL_SCALAR, ndof = 1), Example 3.2
+ * eq. (scalarmodel): every edge e = {i, j} with conductance coef[e] =
+ * gamma_e / |x_i - x_j| adds coef[e] (d_i - d_j)(d_i - d_j)^T.
+ * Structural model (SPNET_MODEL_TRUSS3, ndof = 3), eq. (tensile) plus a
+ * lateral term: the edge adds the 3x3 block coef[e] (n n^T + 0.1 I) with
+ * n = dirs[3e..3e+2] (unit) in the pattern [[+,-],[-,+]].
+ *
+ * edges: [2*n_edges] int64 node ids (i, j), i != j; coef: [n_edges];
+ * dirs: [3*n_edges] for TRUSS3, ignored (may be NULL) for SCALAR.
+ * Output CSR (caller-owned, in `mem`): row_ptr [n_dof+1], col [cap_nnz],
+ * val [cap_nnz]; columns sorted ascending within each row, parallel edges
+ * summed, the diagonal always present.  cap_nnz >= ndof*ndof*(n_nodes +
+ * 2*n_edges) always suffices.  *nnz_out (host) receives the entry count.
+ * Errors: BAD_INPUT (bad ids, self-loops, non-finite coefficients), UNSUPPORTED
+ * (cap_nnz too small or more than 2^31-1 entries).
+ */
+int spnet_assemble(int model, int64_t n_nodes, int64_t n_edges, const int64_t* edges,
+                   const double* coef, const double* dirs, int mem, void* stream,
+                   int64_t* row_ptr, int32_t* col, double* val, int64_t cap_nnz,
+                   int64_t* nnz_out);
+
+/* build_network_operator -- the free-dof operator of a network problem.
+ *
+ * Section 3: with Dirichlet dofs D (values g) and free dofs I, the solver
+ * works on A = K_II and the lifted right-hand side b = f_I - K_ID g_D.
+ * dim in {2, 3}; ndof in {1, 3}; coords [n_nodes*dim] inside
+ * Omega = [0, domain_hi[0]] x ... ; K given as CSR on all n_nodes*ndof dofs
+ * (row_ptr [n_dof+1] int64, col_idx [nnz] int32 sorted ascending per row,
+ * vals [nnz]), symmetric; dirichlet_dofs [n_dirichlet] strictly ascending.
+ * Errors: BAD_INPUT (unsorted/out-of-range indices, asymmetric K_II beyond
+ * 1e-12 relative, non-positive diagonal, coordinates outside Omega).
+ */
+int build_network_operator(int dim, int ndof, int64_t n_nodes, const double* coords,
+                           const int64_t* row_ptr, const int32_t* col_idx, const double* vals,
+                           int64_t n_dirichlet, const int64_t* dirichlet_dofs,
+                           const double* domain_hi, int mem, void* stream, spnet_op_t* out);
+
+/* setup_preconditioner -- the two-level additive Schwarz preconditioner B.
+ *
+ * Section 2.3 / 4.1.  H must divide every side length (l_i / H integral).
+ * gamma_faces [ndof] (host): per component, the bitmask of box faces on which
+ * that component is Dirichlet (bit 2*axis for x_axis = 0, bit 2*axis+1 for
+ * x_axis = l_axis); mesh nodes on those faces carry no coarse dof.  Coarse
+ * basis functions are truncated to free dofs; a function that vanishes at
+ * every free dof of its component is dropped.  opts may be NULL (defaults).
+ * Errors: BAD_H, NOT_SPD (a local or coarse pivot <= 0), UNSUPPORTED
+ * (a star beyond 65535 dofs), NO_MEMORY.
+ */
+int setup_preconditioner(spnet_op_t op, double H, const int* gamma_faces,
+                         const spnet_options* opts, spnet_pc_t* out);
+
+/* pcg_solve -- preconditioned conjugate gradients for nrhs right-hand sides.
+ *
+ * Section 4.2.  f [nrhs*n_dof] (values at Dirichlet dofs ignored),
+ * g [nrhs*n_dirichlet] Dirichlet values in the order of dirichlet_dofs,
+ * x [nrhs*n_dof]: on entry the initial guess if use_x0 (free dofs only), on
+ * exit u_hat = u + g on all dofs.  Stops when ||r||_2 <= rtol ||b||_2 on the
+ * recursive residual, then recomputes b - A x in FP64 and restarts from it
+ * (at most max_restarts times) if it is above the tolerance.  stats [nrhs]
+ * is host memory (may be NULL).  Returns NO_CONVERGENCE if any right-hand
+ * side misses rtol within maxit steps (x is still written).
+ */
+int pcg_solve(spnet_op_t op, spnet_pc_t pc, int nrhs, const double* f, const double* g,
+              double* x, int use_x0, double rtol, int maxit, int mem, spnet_stats* stats);
+
+int spnet_op_destroy(spnet_op_t op);
+int spnet_pc_destroy(spnet_pc_t pc);
+
+/* spnet_last_error -- copy the calling thread's last error message (NUL-terminated). */
+int spnet_last_error(char* buf, size_t len);
+
+int spnet_op_get_info(spnet_op_t op, spnet_op_info* info);
+int spnet_pc_get_info(spnet_pc_t pc, spnet_pc_info* info);
+
+/* The steps of one preconditioner application, for checking each one on its
+ * own.  Vectors on the free dofs are in ascending-dof order ("free order");
+ * coarse vectors are in coarse-dof order (mesh node ascending, lexicographic
+ * with axis 0 fastest, then component).
+ *
+ * spnet_spmv          y = A x                         (Section 3, A = K_II)
+ * spnet_pc_apply      z = B r                         (Section 4.1-4.2)
+ * spnet_pc_restrict   r_c = R_0 r                     (Section 2.3: Q1 values at free dofs)
+ * spnet_pc_coarse     z_c = A_0^{-1} r_c              (P_0, eq. defPj)
+ * spnet_pc_prolong    z = R_0^T z_c
+ * spnet_pc_stars      z = sum_j E_j A_j^{-1} E_j^T r  (P_j, eq. defPj)
+ */
+int spnet_spmv(spnet_op_t op, const double* x, double* y, int mem);
+int spnet_pc_apply(spnet_pc_t pc, const double* r, double* z, int mem);
+int spnet_pc_restrict(spnet_pc_t pc, const double* r, double* rc, int mem);
+int spnet_pc_coarse(spnet_pc_t pc, const double* rc, double* zc, int mem);
+int spnet_pc_prolong(spnet_pc_t pc, const double* zc, double* z, int mem);
+int spnet_pc_stars(spnet_pc_t pc, const double* r, double* z, int mem);
+
+/* spnet_pc_export -- copy set-up data to host memory (for inspection).
+ * what: SPNET_EXPORT_ELEMENTS   int32 [n_free]     linear host element of each free dof
+ *       SPNET_EXPORT_Q1         double [n_free*2^d] Q1 values, free-dof major
+ *       SPNET_EXPORT_COARSE_MAP int32 [n_mesh*ndof] coarse index of (mesh node, component), -1 if none
+ *       SPNET_EXPORT_STAR_SIZES int32 [n_stars]    dofs of each star (stars in mesh order)
+ *       SPNET_EXPORT_STAR_MESH  int32 [n_stars]    mesh node of each star
+ *       SPNET_EXPORT_A0         double [m0*m0]     the Galerkin matrix A_0 (row-major)
+ *       SPNET_EXPORT_STAR_LEVELS int32 [n_stars]   level count of each star's local solve
+ * bytes must be at least the size listed.
+ */
+#define SPNET_EXPORT_ELEMENTS 0
+#define SPNET_EXPORT_Q1 1
+#define SPNET_EXPORT_COARSE_MAP 2
+#define SPNET_EXPORT_STAR_SIZES 3
+#define SPNET_EXPORT_STAR_MESH 4
+#define SPNET_EXPORT_A0 5
+#define SPNET_EXPORT_STAR_LEVELS 6
+int spnet_pc_export(spnet_pc_t pc, int what, void* host_buf, size_t bytes);
+
+/* Instrumentation (process-wide; not part of the paper's method).
+ * spnet_launch_count   kernels the library has launched since it was loaded.
+ * spnet_profile_enable 1: time every launch of the kernels below with CUDA
+ *                      events recorded on the launching stream; 0: stop.
+ * spnet_profile_read   launches and total milliseconds of one kernel since the
+ *                      last reset (reading waits for the recorded events).
+ * spnet_profile_reset  clear the accumulated timings. */
+#define SPNET_KERNEL_SPMV 0
+#define SPNET_KERNEL_UPDATE 1
+#define SPNET_KERNEL_RESTRICT 2
+#define SPNET_KERNEL_STARS 3
+#define SPNET_KERNEL_COARSE 4
+#define SPNET_KERNEL_COMBINE 5
+#define SPNET_KERNEL_DIRECTION 6
+#define SPNET_KERNEL_STAR_SYMBOLIC 7
+#define SPNET_KERNEL_STAR_NUMERIC 8
+#define SPNET_KERNEL_SWEEP 9
+#define SPNET_KERNEL_GALERKIN 10
+#define SPNET_KERNEL_COUNT 11
+int spnet_launch_count(int64_t* count);
+int spnet_profile_enable(int on);
+int spnet_profile_read(int kernel, int64_t* launches, double* total_ms);
+int spnet_profile_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPNET_H */

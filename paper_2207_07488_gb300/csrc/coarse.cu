@@ -1,0 +1,201 @@
+// The coarse solve z_c = A_0^{-1} r_c of P_0 (Section 4.1, eq. defPj).
+//
+// A_0 (m0 x m0, SPD) is inverted once at set-up by block Gauss-Jordan sweeps
+// (pivot blocks of 32): sweeping pivot block K maps
+//   A_ij -> A_ij - A_iK P A_Kj,  A_iK -> A_iK P,  A_Kj -> P A_Kj,  A_KK -> -P
+// with P = A_KK^{-1}; after sweeping every block the matrix holds -A^{-1}.
+// For an SPD matrix the pivot blocks are Schur complements, hence SPD, so no
+// pivoting is needed.  Each application is then one dense matrix-vector
+// product that every SM can share, instead of two dependent triangular solves.
+// The sweeps and the product run in FP64 or, for the mixed-precision
+// preconditioner, in FP32.
+#include <cmath>
+
+#include "spnet_internal.cuh"
+
+namespace spnet {
+
+constexpr int NB = 32;
+
+// invert the SPD pivot block D = Z[k0.., k0..] (kb x kb) into P (FP64 arithmetic)
+template <class T>
+__global__ void k_pivot_inverse(T* Z, int64_t m0, int k0, int kb, double* P, int* flags) {
+  __shared__ double D[NB][NB + 1];
+  __shared__ double col[NB], row[NB];
+  __shared__ double piv;
+  const int i = threadIdx.y, j = threadIdx.x;
+  if (i < kb && j < kb) D[i][j] = (double)Z[(int64_t)(k0 + i) * m0 + (k0 + j)];
+  __syncthreads();
+  for (int p = 0; p < kb; ++p) {
+    if (i == 0 && j == 0) {
+      piv = D[p][p];
+      if (!(piv > 0.0)) {
+        atomicOr(flags, FLAG_COARSE_SPD);
+        piv = 1.0;
+      }
+    }
+    if (i == 0 && j < kb) row[j] = D[p][j];
+    if (j == 0 && i < kb) col[i] = D[i][p];
+    __syncthreads();
+    if (i < kb && j < kb) {
+      const double ip = 1.0 / piv;
+      if (i != p && j != p) D[i][j] -= col[i] * row[j] * ip;
+      else if (i == p && j == p) D[i][j] = -ip;
+      else if (i == p) D[i][j] = row[j] * ip;
+      else D[i][j] = col[i] * ip;
+    }
+    __syncthreads();
+  }
+  if (i < kb && j < kb) P[i * NB + j] = -D[i][j];
+}
+
+// R = Z[k0:k0+kb, :] (copy of the pivot rows), Tm = P R
+template <class T>
+__global__ void k_panel(const T* Z, int64_t m0, int k0, int kb, const double* P, T* R, T* Tm) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < m0;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    T col[NB];
+    for (int t = 0; t < kb; ++t) col[t] = Z[(int64_t)(k0 + t) * m0 + c];
+    for (int t = 0; t < kb; ++t) R[(int64_t)t * m0 + c] = col[t];
+    for (int t = 0; t < kb; ++t) {
+      T acc = 0;
+      for (int u = 0; u < kb; ++u) acc += (T)P[t * NB + u] * col[u];
+      Tm[(int64_t)t * m0 + c] = acc;
+    }
+  }
+}
+
+// the rank-kb sweep update of every entry (64x64 tiles, 4x4 per thread)
+template <class T>
+__global__ void __launch_bounds__(256) k_sweep(T* Z, int64_t m0, int k0, int kb, const double* P,
+                                               const T* __restrict__ R, const T* __restrict__ Tm) {
+  __shared__ T sR[NB][64];
+  __shared__ T sT[NB][64];
+  const int64_t i0 = (int64_t)blockIdx.y * 64, j0 = (int64_t)blockIdx.x * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  for (int q = threadIdx.x; q < NB * 64; q += 256) {
+    int t = q / 64, c = q % 64;
+    sR[t][c] = (t < kb && i0 + c < m0) ? R[(int64_t)t * m0 + i0 + c] : (T)0;
+    sT[t][c] = (t < kb && j0 + c < m0) ? Tm[(int64_t)t * m0 + j0 + c] : (T)0;
+  }
+  __syncthreads();
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+  for (int t = 0; t < kb; ++t) {
+    T ri[4], tj[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) ri[a] = sR[t][ty * 4 + a];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) tj[b] = sT[t][tx * 4 + b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] += ri[a] * tj[b];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t i = i0 + ty * 4 + a;
+    if (i >= m0) continue;
+    const bool iK = i >= k0 && i < k0 + kb;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int64_t j = j0 + tx * 4 + b;
+      if (j >= m0) continue;
+      const bool jK = j >= k0 && j < k0 + kb;
+      T* zz = &Z[i * m0 + j];
+      if (!iK && !jK) *zz -= acc[a][b];
+      else if (iK && jK) *zz = (T)(-P[(i - k0) * NB + (j - k0)]);
+      else if (iK) *zz = sT[i - k0][tx * 4 + b];
+      else *zz = Tm[(j - k0) * m0 + i];  // A_iK P = (P A_Ki)^T by symmetry
+    }
+  }
+}
+
+template <class T>
+__global__ void k_negate_from(const double* A0, T* Z, int64_t n, int mode) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    if (mode == 0) Z[q] = (T)A0[q];
+    else Z[q] = -Z[q];
+  }
+}
+
+template <class T>
+static int invert_impl(spnet_pc_s* pc, const double* A0) {
+  cudaStream_t s = pc->op->stream;
+  const int64_t m0 = pc->m0;
+  DevArena tmp;
+  tmp.stream = s;
+  struct Guard {
+    DevArena& a;
+    ~Guard() { a.free_all(); }
+  } guard{tmp};
+  T* Z = nullptr;
+  SPNET_TRY(pc->mem.get(&Z, m0 * m0));
+  pc->Z = Z;
+  double* P = nullptr;
+  T *R = nullptr, *Tm = nullptr;
+  SPNET_TRY(tmp.get(&P, NB * NB));
+  SPNET_TRY(tmp.get(&R, NB * m0));
+  SPNET_TRY(tmp.get(&Tm, NB * m0));
+  const int grid = 4 * num_sms();
+  note_launch();
+  k_negate_from<T><<<grid, 256, 0, s>>>(A0, Z, m0 * m0, 0);
+  SPNET_CUDA_TRY(cudaMemsetAsync(pc->op->dflags, 0, sizeof(int), s));
+  dim3 tiles((unsigned)((m0 + 63) / 64), (unsigned)((m0 + 63) / 64));
+  for (int k0 = 0; k0 < m0; k0 += NB) {
+    const int kb = (int)((m0 - k0) < NB ? (m0 - k0) : NB);
+    note_launch();
+    k_pivot_inverse<T><<<1, dim3(NB, NB), 0, s>>>(Z, m0, k0, kb, P, pc->op->dflags);
+    note_launch();
+    k_panel<T><<<(unsigned)((m0 + 255) / 256), 256, 0, s>>>(Z, m0, k0, kb, P, R, Tm);
+    note_launch();
+    ProfScope ps(KID_SWEEP, s);
+    k_sweep<T><<<tiles, 256, 0, s>>>(Z, m0, k0, kb, P, R, Tm);
+  }
+  note_launch();
+  k_negate_from<T><<<grid, 256, 0, s>>>(A0, Z, m0 * m0, 1);
+  SPNET_CUDA_TRY(cudaGetLastError());
+  return check_flags(pc->op->dflags, s, "setup_preconditioner (coarse matrix)");
+}
+
+int pc_coarse_invert(spnet_pc_s* pc, double* A0) {
+  if (pc->m0 == 0) return SPNET_OK;
+  if (pc->precision == SPNET_PREC_FP64) return invert_impl<double>(pc, A0);
+  return invert_impl<float>(pc, A0);
+}
+
+// z_c = Z r_c: one warp per row
+template <class T>
+__global__ void __launch_bounds__(256) k_coarse_gemv(const T* __restrict__ Z, int64_t m0,
+                                                     const double* __restrict__ rc,
+                                                     double* __restrict__ zc, const int* done) {
+  if (done && *done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < m0; row += nw) {
+    const T* zr = Z + row * m0;
+    T acc = 0;
+    for (int64_t c = lane; c < m0; c += 32) acc += zr[c] * (T)__ldg(&rc[c]);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) zc[row] = (double)acc;
+  }
+}
+
+void launch_coarse_apply(spnet_pc_s* pc, const double* rc, double* zc, const int* done,
+                         cudaStream_t s) {
+  if (pc->m0 == 0) return;
+  int blocks = (int)((pc->m0 + 7) / 8);
+  if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
+  note_launch();
+  ProfScope ps(KID_COARSE, s);
+  if (pc->precision == SPNET_PREC_FP64)
+    k_coarse_gemv<double><<<blocks, 256, 0, s>>>((const double*)pc->Z, pc->m0, rc, zc, done);
+  else
+    k_coarse_gemv<float><<<blocks, 256, 0, s>>>((const float*)pc->Z, pc->m0, rc, zc, done);
+}
+
+}  // namespace spnet

@@ -1,0 +1,266 @@
+// Internal declarations shared by the translation units of libspnet.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/spnet.h"
+
+namespace spnet {
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+const std::string& last_error();
+int fail(int code, const std::string& msg);
+
+struct Status {
+  int code = SPNET_OK;
+  std::string msg;
+};
+
+#define SPNET_CUDA_TRY(expr)                                                          \
+  do {                                                                                \
+    cudaError_t _e = (expr);                                                          \
+    if (_e != cudaSuccess) {                                                          \
+      return ::spnet::fail(_e == cudaErrorMemoryAllocation ? SPNET_ERR_NO_MEMORY      \
+                                                           : SPNET_ERR_CUDA,          \
+                           std::string(#expr) + ": " + cudaGetErrorString(_e));       \
+    }                                                                                 \
+  } while (0)
+
+#define SPNET_TRY(expr)           \
+  do {                            \
+    int _rc = (expr);             \
+    if (_rc != SPNET_OK) return _rc; \
+  } while (0)
+
+// device-side error flags (bitmask in a device int)
+enum : int {
+  FLAG_BAD_INPUT = 1,
+  FLAG_NOT_SPD = 2,
+  FLAG_ASYM = 4,
+  FLAG_POOL = 8,        // star factor pool too small (retry with a larger pool)
+  FLAG_STAR_BIG = 16,   // star or dense core beyond the scratch capacity
+  FLAG_NONFINITE = 32,
+  FLAG_OUT_OF_BOX = 64,
+  FLAG_UNSORTED = 128,
+  FLAG_COARSE_SPD = 256,
+};
+
+// ---------------------------------------------------------------------------
+// stream-ordered device buffers
+// ---------------------------------------------------------------------------
+struct DevArena {
+  cudaStream_t stream = 0;
+  std::vector<void*> ptrs;
+  int64_t bytes = 0;
+  int alloc(void** p, size_t n);
+  template <class T>
+  int get(T** p, size_t count) {
+    return alloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  }
+  void release(void* p);
+  void free_all();
+};
+
+// ---------------------------------------------------------------------------
+// operator and preconditioner handles
+// ---------------------------------------------------------------------------
+struct Csr {
+  int64_t n = 0, nnz = 0;
+  int64_t* ptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+};
+
+struct Scal {
+  double rz, rz_old, pq, rr, bb, alpha, beta, rz_flex;
+  double rr_true;
+  int iter, done, restarts, pad;
+};
+
+}  // namespace spnet
+
+struct spnet_op_s {
+  int dim = 0, ndof = 0;
+  int64_t n_nodes = 0, n_dof = 0, n_free = 0, n_dir = 0;
+  double domain[3] = {1, 1, 1};
+  cudaStream_t stream = 0;
+  spnet::DevArena mem;
+  double* coords = nullptr;     // [n_nodes*dim]
+  int64_t* dir_dofs = nullptr;  // [n_dir]
+  int64_t* free_dofs = nullptr; // [n_free]
+  int64_t* free_of = nullptr;   // [n_dof]: free index, or -(position in dir_dofs) - 2
+  spnet::Csr ff, fd;            // K_II, K_ID
+  int* dflags = nullptr;
+  double* spmv_tmp = nullptr;   // [2*n_free] scratch for spnet_spmv on host arrays
+  int refcount = 0;
+};
+
+struct spnet_pc_s {
+  spnet_op_s* op = nullptr;
+  spnet::DevArena mem;
+  int precision = SPNET_PREC_MIXED, star_set = SPNET_STARS_INTERIOR, flexible = 1, max_restarts = 2;
+  int d = 0, ndof = 1, nc = 4;  // nc = 2^d corners
+  int gamma[3] = {0, 0, 0};     // Dirichlet face bitmask per component
+  int nH[3] = {1, 1, 1};
+  int n_elem = 0, n_mesh = 0;
+  double H = 0;
+  int64_t N = 0;  // free dofs
+  // permutation: pc position <-> free index
+  int32_t* perm = nullptr;     // [N] free index at pc position
+  int32_t* iperm = nullptr;    // [N]
+  int32_t* elem_of = nullptr;  // [N] element of pc position
+  int8_t* comp_of = nullptr;   // [N]
+  int32_t* elem_ptr = nullptr; // [n_elem+1]
+  double* q1w = nullptr;       // [nc][N]
+  spnet::Csr K;                // A in pc order
+  // coarse space
+  int m0 = 0;
+  int32_t* cidx = nullptr;     // [n_mesh*ndof]
+  void* Z = nullptr;           // [m0*m0] A_0^{-1} (float or double by precision)
+  double* A0 = nullptr;        // [m0*m0] copy of A_0 if m0 <= A0_KEEP
+  // stars
+  int S = 0, max_star = 0, max_levels = 0;
+  int64_t sum_s = 0, factor_nnz = 0, total_levels = 0;
+  int32_t* star_mesh = nullptr;    // [S]
+  int32_t* star_of_mesh = nullptr; // [n_mesh]
+  int64_t* star_ptr = nullptr;     // [S+1]
+  int32_t* elem_star_off = nullptr;// [n_elem*nc], -1 if no star at that corner
+  char* pool = nullptr;
+  int64_t pool_bytes = 0;
+  int64_t* star_off = nullptr;     // [S] byte offset of each star's factor blob
+  int32_t* star_n = nullptr;       // [S]
+  int32_t* star_lev = nullptr;     // [S]
+  int32_t* star_nnz = nullptr;     // [S]
+  // work vectors (pc order)
+  double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *b = nullptr;
+  double *w = nullptr, *rc = nullptr, *zc = nullptr, *partial = nullptr, *vtmp = nullptr;
+  void* ybuf = nullptr;
+  spnet::Scal* scal = nullptr;
+  int G = 0;         // reduction grid
+  int spmv_lanes = 1;
+  double setup_ms = 0;
+};
+
+namespace spnet {
+
+// ---------------------------------------------------------------------------
+// the Cartesian mesh T_H: elements numbered lexicographically with axis 0
+// fastest, mesh nodes likewise over (n_a + 1) per axis, corner c of an element
+// has bit a set when it sits at the upper end of axis a
+// ---------------------------------------------------------------------------
+struct Mesh {
+  int d, nc;
+  int n[3];  // elements per axis
+};
+
+__device__ __forceinline__ void elem_multi(const Mesh& m, int e, int* ex) {
+  ex[0] = e % m.n[0];
+  int t = e / m.n[0];
+  ex[1] = t % m.n[1];
+  ex[2] = m.d == 3 ? t / m.n[1] : 0;
+}
+
+// mesh node at corner c of element e (corner bit a = offset along axis a)
+__device__ __forceinline__ int mesh_of(const Mesh& m, int e, int c) {
+  int ex[3];
+  elem_multi(m, e, ex);
+  int k = ex[0] + (c & 1);
+  k += (m.n[0] + 1) * (ex[1] + ((c >> 1) & 1));
+  if (m.d == 3) k += (m.n[0] + 1) * (m.n[1] + 1) * (ex[2] + ((c >> 2) & 1));
+  return k;
+}
+
+__device__ __forceinline__ void mesh_multi(const Mesh& m, int k, int* km) {
+  km[0] = k % (m.n[0] + 1);
+  int t = k / (m.n[0] + 1);
+  km[1] = t % (m.n[1] + 1);
+  km[2] = m.d == 3 ? t / (m.n[1] + 1) : 0;
+}
+
+// element e' = k - 1 + c' around mesh node k, or -1 outside the mesh
+__device__ __forceinline__ int elem_around(const Mesh& m, const int* km, int cp) {
+  int e = 0, stride = 1;
+  for (int a = 0; a < m.d; ++a) {
+    int ea = km[a] - 1 + ((cp >> a) & 1);
+    if (ea < 0 || ea >= m.n[a]) return -1;
+    e += ea * stride;
+    stride *= m.n[a];
+  }
+  return e;
+}
+
+inline Mesh mesh_of_pc(const spnet_pc_s* pc) {
+  Mesh m;
+  m.d = pc->d;
+  m.nc = pc->nc;
+  for (int a = 0; a < 3; ++a) m.n[a] = pc->nH[a];
+  return m;
+}
+
+constexpr int RED_BLOCK = 256;
+constexpr int A0_KEEP = 2048;
+
+// util.cu
+enum KernelId {
+  KID_SPMV = 0, KID_UPDATE, KID_RESTRICT, KID_STARS, KID_COARSE, KID_COMBINE, KID_DIRECTION,
+  KID_STAR_SYMBOLIC, KID_STAR_NUMERIC, KID_SWEEP, KID_GALERKIN, KID_COUNT
+};
+void note_launch();
+long long launch_count();
+struct ProfScope {
+  int id;
+  cudaStream_t s;
+  cudaEvent_t a{}, b{};
+  bool active = false;
+  ProfScope(int id, cudaStream_t s);
+  ~ProfScope();
+};
+void profile_enable(int on);
+void profile_read(int id, long long* n, double* ms);
+void profile_reset();
+int scan_exclusive(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s, DevArena& mem);
+int scan_exclusive64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, DevArena& mem);
+int copy_in(const void* src, void* dst, size_t bytes, int mem, cudaStream_t s);
+int copy_out(const void* src, void* dst, size_t bytes, int mem, cudaStream_t s);
+int check_flags(int* dflags, cudaStream_t s, const char* where);
+void fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
+int num_sms();
+double elapsed_ms(cudaEvent_t a, cudaEvent_t b);
+
+// operator.cu
+void launch_spmv(const Csr& A, const double* x, double* y, double* partial_pq, int G, int lanes,
+                 const int* done, cudaStream_t s);
+int choose_spmv_lanes(const Csr& A);
+
+// setup.cu
+int pc_setup_structure(spnet_pc_s* pc);
+int pc_galerkin(spnet_pc_s* pc, double* A0_dense);
+
+// starfact.cu
+int pc_factor_stars(spnet_pc_s* pc);
+void launch_star_solve(spnet_pc_s* pc, const double* r, const int* done, cudaStream_t s);
+
+// coarse.cu
+int pc_coarse_invert(spnet_pc_s* pc, double* A0_dense);
+void launch_coarse_apply(spnet_pc_s* pc, const double* rc, double* zc, const int* done,
+                         cudaStream_t s);
+
+// pcg.cu
+void launch_restrict(spnet_pc_s* pc, const double* r, double* rc, const int* done, cudaStream_t s);
+void launch_combine(spnet_pc_s* pc, const double* r, double* z, int with_coarse, int with_stars,
+                    int with_dots, const int* done, cudaStream_t s);
+int pc_apply_free(spnet_pc_s* pc, const double* r_free_dev, double* z_free_dev, int which);
+void to_pc(spnet_pc_s* pc, const double* free_vec, double* pc_vec);
+void from_pc(spnet_pc_s* pc, const double* pc_vec, double* free_vec);
+int export_item(spnet_pc_s* pc, int what, void* host_buf);
+int pcg_run(spnet_op_s* op, spnet_pc_s* pc, int nrhs, const double* f, const double* g, double* x,
+            int use_x0, double rtol, int maxit, int mem, spnet_stats* stats);
+
+}  // namespace spnet

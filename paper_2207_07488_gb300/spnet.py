@@ -1,0 +1,376 @@
+"""ctypes binding of libspnet (include/spnet.h): argument marshalling only.
+
+Arrays may be numpy arrays (host memory, SPNET_MEM_HOST) or CUDA torch
+tensors (device memory, SPNET_MEM_DEVICE); every computation runs in the
+library's CUDA kernels.  If the library is missing or cannot be loaded the
+import of the handles raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERRORS = {
+    -1: "BAD_INPUT", -2: "NOT_SPD", -3: "NO_MEMORY", -4: "NO_CONVERGENCE", -5: "TIMEOUT",
+    -6: "CUDA", -7: "UNSUPPORTED", -8: "BAD_H",
+}
+MEM_HOST, MEM_DEVICE = 0, 1
+MODEL_SCALAR, MODEL_TRUSS3 = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+STARS_INTERIOR, STARS_ALL = 0, 1
+EXPORT_ELEMENTS, EXPORT_Q1, EXPORT_COARSE_MAP, EXPORT_STAR_SIZES = 0, 1, 2, 3
+EXPORT_STAR_MESH, EXPORT_A0, EXPORT_STAR_LEVELS = 4, 5, 6
+
+EXPORTED = [
+    "spnet_assemble", "build_network_operator", "setup_preconditioner", "pcg_solve",
+    "spnet_op_destroy", "spnet_pc_destroy", "spnet_last_error", "spnet_op_get_info",
+    "spnet_pc_get_info", "spnet_spmv", "spnet_pc_apply", "spnet_pc_restrict", "spnet_pc_coarse",
+    "spnet_pc_prolong", "spnet_pc_stars", "spnet_pc_export", "spnet_launch_count",
+    "spnet_profile_enable", "spnet_profile_read", "spnet_profile_reset",
+]
+KERNELS = ["spmv", "update", "restrict", "stars", "coarse", "combine", "direction",
+           "star_symbolic", "star_numeric", "sweep", "galerkin"]
+
+
+class SpnetError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("star_set", C.c_int), ("flexible", C.c_int),
+                ("max_restarts", C.c_int), ("reserved", C.c_int * 12)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
+                ("status", C.c_int), ("relres", C.c_double), ("relres_recursive", C.c_double),
+                ("solve_ms", C.c_double), ("reserved", C.c_double * 4)]
+
+
+class OpInfo(C.Structure):
+    _fields_ = [("n_dof", C.c_int64), ("n_free", C.c_int64), ("n_dirichlet", C.c_int64),
+                ("nnz_ff", C.c_int64), ("nnz_fd", C.c_int64), ("dim", C.c_int), ("ndof", C.c_int),
+                ("reserved", C.c_int64 * 6)]
+
+
+class PcInfo(C.Structure):
+    _fields_ = [("nH", C.c_int * 3), ("n_elem", C.c_int), ("n_mesh", C.c_int), ("m0", C.c_int),
+                ("n_stars", C.c_int), ("max_star", C.c_int), ("sum_star", C.c_int64),
+                ("factor_nnz", C.c_int64), ("total_levels", C.c_int64), ("max_levels", C.c_int),
+                ("precision", C.c_int), ("star_set", C.c_int), ("flexible", C.c_int),
+                ("setup_ms", C.c_double), ("device_bytes", C.c_int64), ("reserved", C.c_int64 * 5)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libspnet.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libspnet is not built ({path} missing)")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    i64, i32, dbl = C.c_int64, C.c_int, C.c_double
+    lib.spnet_assemble.argtypes = [i32, i64, i64, P, P, P, i32, P, P, P, P, i64, C.POINTER(i64)]
+    lib.build_network_operator.argtypes = [i32, i32, i64, P, P, P, P, i64, P, P, i32, P, C.POINTER(P)]
+    lib.setup_preconditioner.argtypes = [P, dbl, C.POINTER(C.c_int), C.POINTER(Options), C.POINTER(P)]
+    lib.pcg_solve.argtypes = [P, P, i32, P, P, P, i32, dbl, i32, i32, C.POINTER(Stats)]
+    lib.spnet_op_destroy.argtypes = [P]
+    lib.spnet_pc_destroy.argtypes = [P]
+    lib.spnet_last_error.argtypes = [C.c_char_p, C.c_size_t]
+    lib.spnet_op_get_info.argtypes = [P, C.POINTER(OpInfo)]
+    lib.spnet_pc_get_info.argtypes = [P, C.POINTER(PcInfo)]
+    for name in ("spnet_spmv", "spnet_pc_apply", "spnet_pc_restrict", "spnet_pc_coarse",
+                 "spnet_pc_prolong", "spnet_pc_stars"):
+        getattr(lib, name).argtypes = [P, P, P, i32]
+    lib.spnet_pc_export.argtypes = [P, i32, P, C.c_size_t]
+    lib.spnet_launch_count.argtypes = [C.POINTER(i64)]
+    lib.spnet_profile_enable.argtypes = [i32]
+    lib.spnet_profile_read.argtypes = [i32, C.POINTER(i64), C.POINTER(dbl)]
+    lib.spnet_profile_reset.argtypes = []
+    for name in EXPORTED:
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(4096)
+    load().spnet_last_error(buf, len(buf))
+    return buf.value.decode(errors="replace")
+
+
+def launch_count() -> int:
+    n = C.c_int64(0)
+    _check(load().spnet_launch_count(C.byref(n)))
+    return int(n.value)
+
+
+def profile_enable(on: bool = True):
+    _check(load().spnet_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(load().spnet_profile_reset())
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total ms)} since the last reset."""
+    lib = load()
+    out = {}
+    for k, name in enumerate(KERNELS):
+        n, ms = C.c_int64(0), C.c_double(0.0)
+        _check(lib.spnet_profile_read(k, C.byref(n), C.byref(ms)))
+        out[name] = (int(n.value), float(ms.value))
+    return out
+
+
+def _check(rc):
+    if rc != OK:
+        raise SpnetError(rc, last_error())
+    return rc
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _arg(a, dtype):
+    """(pointer, mem, keep-alive) for a numpy array or a CUDA torch tensor."""
+    if a is None:
+        return None, None, None
+    if _is_torch(a):
+        import torch
+        tdt = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32}[dtype]
+        if a.dtype != tdt or not a.is_contiguous():
+            a = a.to(tdt).contiguous()
+        if not a.is_cuda:
+            a = a.numpy()
+        else:
+            return C.c_void_p(a.data_ptr()), MEM_DEVICE, a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return C.c_void_p(arr.ctypes.data), MEM_HOST, arr
+
+
+def _same_mem(*mems):
+    ms = {m for m in mems if m is not None}
+    if len(ms) > 1:
+        raise ValueError("all arrays of one call must live in the same memory (host or device)")
+    return ms.pop() if ms else MEM_HOST
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def assemble(model, n_nodes, edges, coef, dirs=None, stream=None):
+    """K on all dofs as host CSR arrays (row_ptr int64, col int32, val float64)."""
+    lib = load()
+    ndof = 1 if model == MODEL_SCALAR else 3
+    edges = np.ascontiguousarray(edges, dtype=np.int64)
+    m = edges.shape[0]
+    cap = ndof * ndof * (n_nodes + 2 * m)
+    rp = np.zeros(n_nodes * ndof + 1, np.int64)
+    col = np.zeros(max(cap, 1), np.int32)
+    val = np.zeros(max(cap, 1), np.float64)
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    d = np.ascontiguousarray(dirs, dtype=np.float64) if dirs is not None else None
+    nnz = C.c_int64(0)
+    _check(lib.spnet_assemble(model, n_nodes, m, edges.ctypes.data, coef.ctypes.data,
+                              d.ctypes.data if d is not None else None, MEM_HOST,
+                              _stream_ptr(stream), rp.ctypes.data, col.ctypes.data,
+                              val.ctypes.data, cap, C.byref(nnz)))
+    n = nnz.value
+    return rp, col[:n].copy(), val[:n].copy()
+
+
+class Operator:
+    """build_network_operator: A = K_II and K_ID of a network problem."""
+
+    def __init__(self, dim, ndof, coords, row_ptr, col, val, dirichlet_dofs, domain, stream=None):
+        lib = load()
+        self._lib = lib
+        self.handle = C.c_void_p()
+        X, m1, k1 = _arg(coords, np.float64)
+        rp, m2, k2 = _arg(row_ptr, np.int64)
+        cl, m3, k3 = _arg(col, np.int32)
+        vl, m4, k4 = _arg(val, np.float64)
+        dd, m5, k5 = _arg(dirichlet_dofs, np.int64)
+        mem = _same_mem(m1, m2, m3, m4, m5)
+        dom = np.ascontiguousarray(domain, dtype=np.float64)
+        n_nodes = int(np.asarray(coords.shape)[0])
+        nd = 0 if dirichlet_dofs is None else int(len(dirichlet_dofs))
+        self.stream = stream
+        _check(lib.build_network_operator(dim, ndof, n_nodes, X, rp, cl, vl, nd, dd,
+                                          dom.ctypes.data, mem, _stream_ptr(stream),
+                                          C.byref(self.handle)))
+        self.dim, self.ndof, self.n_nodes = dim, ndof, n_nodes
+        self.info = self.get_info()
+
+    @classmethod
+    def from_problem(cls, problem, stream=None, device=False):
+        """Assemble K with the library and build the operator of a networks.Problem."""
+        net = problem.net
+        if problem.model == "scalar":
+            rp, col, val = assemble(MODEL_SCALAR, net.n_nodes, net.edges, net.cond, stream=stream)
+        else:
+            rp, col, val = assemble(MODEL_TRUSS3, net.n_nodes, net.edges, net.stiff, net.dirs,
+                                    stream=stream)
+        arrs = [net.coords, rp, col, val, problem.dirichlet_dofs]
+        if device:
+            import torch
+            arrs = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+        return cls(net.dim, problem.ndof, *arrs, domain=net.domain, stream=stream)
+
+    def get_info(self):
+        info = OpInfo()
+        _check(self._lib.spnet_op_get_info(self.handle, C.byref(info)))
+        return info
+
+    def spmv(self, x):
+        xp, mem, keep = _arg(x, np.float64)
+        if mem == MEM_DEVICE:
+            import torch
+            y = torch.empty_like(keep)
+            _check(self._lib.spnet_spmv(self.handle, xp, C.c_void_p(y.data_ptr()), mem))
+            return y
+        y = np.zeros(self.info.n_free)
+        _check(self._lib.spnet_spmv(self.handle, xp, y.ctypes.data, mem))
+        return y
+
+    def close(self):
+        if self.handle:
+            _check(self._lib.spnet_op_destroy(self.handle))
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Preconditioner:
+    """setup_preconditioner: the two-level additive Schwarz preconditioner."""
+
+    def __init__(self, op: Operator, H, gamma_faces, precision=PREC_MIXED, star_set=STARS_INTERIOR,
+                 flexible=-1, max_restarts=2):
+        self._lib = op._lib
+        self.op = op
+        self.handle = C.c_void_p()
+        o = Options()
+        o.precision, o.star_set, o.flexible, o.max_restarts = precision, star_set, flexible, max_restarts
+        gf = (C.c_int * 3)(*(list(gamma_faces) + [0, 0, 0])[:3])
+        _check(self._lib.setup_preconditioner(op.handle, float(H), gf, C.byref(o),
+                                              C.byref(self.handle)))
+        self.info = self.get_info()
+
+    def get_info(self):
+        info = PcInfo()
+        _check(self._lib.spnet_pc_get_info(self.handle, C.byref(info)))
+        return info
+
+    def _vec_call(self, fn, v, n_out):
+        vp, mem, keep = _arg(v, np.float64)
+        if mem == MEM_DEVICE:
+            import torch
+            out = torch.zeros(max(n_out, 1), dtype=torch.float64, device=keep.device)[:n_out]
+            _check(fn(self.handle, vp, C.c_void_p(out.data_ptr()), mem))
+            return out
+        out = np.zeros(n_out)
+        _check(fn(self.handle, vp, out.ctypes.data if n_out else C.c_void_p(), mem))
+        return out
+
+    def apply(self, r):
+        return self._vec_call(self._lib.spnet_pc_apply, r, self.op.info.n_free)
+
+    def stars(self, r):
+        return self._vec_call(self._lib.spnet_pc_stars, r, self.op.info.n_free)
+
+    def restrict(self, r):
+        return self._vec_call(self._lib.spnet_pc_restrict, r, self.info.m0)
+
+    def coarse(self, rc):
+        return self._vec_call(self._lib.spnet_pc_coarse, rc, self.info.m0)
+
+    def prolong(self, zc):
+        return self._vec_call(self._lib.spnet_pc_prolong, zc, self.op.info.n_free)
+
+    def export(self, what):
+        i = self.info
+        nfree = self.op.info.n_free
+        spec = {
+            EXPORT_ELEMENTS: (np.int32, (nfree,)),
+            EXPORT_Q1: (np.float64, (nfree, 2 ** self.op.dim)),
+            EXPORT_COARSE_MAP: (np.int32, (i.n_mesh * self.op.ndof,)),
+            EXPORT_STAR_SIZES: (np.int32, (i.n_stars,)),
+            EXPORT_STAR_MESH: (np.int32, (i.n_stars,)),
+            EXPORT_STAR_LEVELS: (np.int32, (i.n_stars,)),
+            EXPORT_A0: (np.float64, (i.m0, i.m0)),
+        }[what]
+        out = np.zeros(spec[1], dtype=spec[0])
+        _check(self._lib.spnet_pc_export(self.handle, what, out.ctypes.data, out.nbytes))
+        return out
+
+    def close(self):
+        if self.handle:
+            _check(self._lib.spnet_pc_destroy(self.handle))
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pcg_solve(op: Operator, pc: Preconditioner, f, g, x0=None, rtol=1e-8, maxit=1000,
+              raise_on_noconv=True):
+    """Solve for one or several right-hand sides.
+
+    f: (n_dof,) or (nrhs, n_dof); g: (n_dir,) or (nrhs, n_dir).  Returns
+    (u_hat, stats) with u_hat of the same leading shape as f.
+    """
+    lib = op._lib
+    single = len(f.shape) == 1
+    nrhs = 1 if single else int(f.shape[0])
+    fp, m1, kf = _arg(f, np.float64)
+    gp, m2, kg = _arg(g, np.float64)
+    mem = _same_mem(m1, m2)
+    stats = (Stats * nrhs)()
+    if mem == MEM_DEVICE:
+        import torch
+        if x0 is not None:
+            x = x0.to(torch.float64).clone().contiguous()
+        else:
+            x = torch.zeros(tuple(f.shape), dtype=torch.float64, device=kf.device)
+        xp = C.c_void_p(x.data_ptr())
+    else:
+        x = np.zeros(tuple(f.shape)) if x0 is None else np.array(x0, dtype=np.float64)
+        xp = C.c_void_p(x.ctypes.data)
+    rc = lib.pcg_solve(op.handle, pc.handle, nrhs, fp, gp, xp, 1 if x0 is not None else 0,
+                       float(rtol), int(maxit), mem, stats)
+    if rc != OK and (rc != -4 or raise_on_noconv):
+        _check(rc)
+    return x, [stats[k] for k in range(nrhs)]

@@ -1,0 +1,37 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every declared entry point (no GPU)."""
+import ctypes
+import os
+import re
+
+from paper_2207_07488_gb300 import build as B
+from paper_2207_07488_gb300 import spnet
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "spnet.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*int\s+([a-z_0-9]+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("build_network_operator", "setup_preconditioner", "pcg_solve", "spnet_assemble"):
+        assert must in names
+    assert set(names) == set(spnet.EXPORTED)
+
+
+def test_library_loads_and_exports_every_symbol():
+    B.build()
+    lib = ctypes.CDLL(B.LIB)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_library_reports_errors_without_a_gpu():
+    lib = spnet.load()
+    # a null operator is rejected by argument checks before any device call
+    rc = lib.setup_preconditioner(None, 0.5, None, None, ctypes.byref(ctypes.c_void_p()))
+    assert rc == -1
+    assert "null operator" in spnet.last_error()
