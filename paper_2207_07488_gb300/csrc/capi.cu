@@ -97,7 +97,8 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
       (rc = pc->mem.get(&pc->vtmp, N)) || (rc = pc->mem.get(&pc->w, pc->sum_s > 0 ? pc->sum_s : 1)) ||
       (rc = pc->mem.get(&pc->rc, pc->m0 > 0 ? pc->m0 : 1)) ||
       (rc = pc->mem.get(&pc->zc, pc->m0 > 0 ? pc->m0 : 1)) ||
-      (rc = pc->mem.get(&pc->partial, 5 * pc->G)) || (rc = pc->mem.get(&pc->scal, 1)))
+      (rc = pc->mem.get(&pc->partial, 5 * pc->G)) || (rc = pc->mem.get(&pc->scal, 1)) ||
+      (rc = pc->mem.get(&pc->epart, (size_t)pc->n_elem * pc->nc * pc->ndof)))
     return bail(rc);
   cudaMemsetAsync(pc->scal, 0, sizeof(Scal), s);
   cudaEventRecord(e1, s);
@@ -116,6 +117,7 @@ extern "C" {
 int spnet_assemble(int model, int64_t n_nodes, int64_t n_edges, const int64_t* edges,
                    const double* coef, const double* dirs, int mem, void* stream, int64_t* row_ptr,
                    int32_t* col, double* val, int64_t cap_nnz, int64_t* nnz_out) {
+  cudaGetLastError();  // start from a clean error state
   if (!edges && n_edges > 0) return fail(SPNET_ERR_BAD_INPUT, "spnet_assemble: null edges");
   if (!row_ptr || !col || !val) return fail(SPNET_ERR_BAD_INPUT, "spnet_assemble: null output");
   return spnet::assemble(model, n_nodes, n_edges, edges, coef, dirs, mem, (cudaStream_t)stream,
@@ -126,6 +128,7 @@ int build_network_operator(int dim, int ndof, int64_t n_nodes, const double* coo
                            const int64_t* row_ptr, const int32_t* col_idx, const double* vals,
                            int64_t n_dirichlet, const int64_t* dirichlet_dofs,
                            const double* domain_hi, int mem, void* stream, spnet_op_t* out) {
+  cudaGetLastError();  // start from a clean error state
   if (!out || !coords || !row_ptr || !col_idx || !vals || !domain_hi || (n_dirichlet > 0 && !dirichlet_dofs))
     return fail(SPNET_ERR_BAD_INPUT, "build_network_operator: null argument");
   if (mem != SPNET_MEM_HOST && mem != SPNET_MEM_DEVICE)
@@ -139,6 +142,7 @@ int build_network_operator(int dim, int ndof, int64_t n_nodes, const double* coo
 
 int setup_preconditioner(spnet_op_t op, double H, const int* gamma_faces, const spnet_options* opts,
                          spnet_pc_t* out) {
+  cudaGetLastError();  // start from a clean error state
   if (!out) return fail(SPNET_ERR_BAD_INPUT, "setup_preconditioner: null output");
   spnet_pc_s* pc = nullptr;
   int rc = setup_impl(op, H, gamma_faces, opts, &pc);
@@ -148,6 +152,7 @@ int setup_preconditioner(spnet_op_t op, double H, const int* gamma_faces, const 
 
 int pcg_solve(spnet_op_t op, spnet_pc_t pc, int nrhs, const double* f, const double* g, double* x,
               int use_x0, double rtol, int maxit, int mem, spnet_stats* stats) {
+  cudaGetLastError();  // start from a clean error state
   if (!op || !pc || pc->op != op) return fail(SPNET_ERR_BAD_INPUT, "pcg_solve: operator/preconditioner mismatch");
   if (nrhs < 0 || !f || !x || (op->n_dir > 0 && !g)) return fail(SPNET_ERR_BAD_INPUT, "pcg_solve: null argument");
   if (!(rtol > 0.0) || maxit < 0) return fail(SPNET_ERR_BAD_INPUT, "pcg_solve: rtol must be > 0, maxit >= 0");
@@ -157,18 +162,29 @@ int pcg_solve(spnet_op_t op, spnet_pc_t pc, int nrhs, const double* f, const dou
 }
 
 int spnet_op_destroy(spnet_op_t op) {
+  cudaGetLastError();  // start from a clean error state
   if (!op) return SPNET_OK;
   if (op->refcount > 0) return fail(SPNET_ERR_BAD_INPUT, "spnet_op_destroy: preconditioners still alive");
   cudaStream_t s = op->stream;
   op->mem.free_all();
   cudaStreamSynchronize(s);
+  if (op->own_stream) cudaStreamDestroy(s);
   delete op;
   return SPNET_OK;
 }
 
 int spnet_pc_destroy(spnet_pc_t pc) {
+  cudaGetLastError();  // start from a clean error state
   if (!pc) return SPNET_OK;
   cudaStream_t s = pc->op->stream;
+  cudaStreamSynchronize(s);
+  if (pc->graph_exec) cudaGraphExecDestroy(pc->graph_exec);
+  if (pc->side) {
+    cudaStreamSynchronize(pc->side);
+    cudaStreamDestroy(pc->side);
+  }
+  if (pc->ev_fork) cudaEventDestroy(pc->ev_fork);
+  if (pc->ev_join) cudaEventDestroy(pc->ev_join);
   pc->mem.free_all();
   cudaStreamSynchronize(s);
   pc->op->refcount--;
@@ -186,6 +202,7 @@ int spnet_last_error(char* buf, size_t len) {
 }
 
 int spnet_op_get_info(spnet_op_t op, spnet_op_info* info) {
+  cudaGetLastError();  // start from a clean error state
   if (!op || !info) return fail(SPNET_ERR_BAD_INPUT, "spnet_op_get_info: null argument");
   *info = spnet_op_info{};
   info->n_dof = op->n_dof;
@@ -199,6 +216,7 @@ int spnet_op_get_info(spnet_op_t op, spnet_op_info* info) {
 }
 
 int spnet_pc_get_info(spnet_pc_t pc, spnet_pc_info* info) {
+  cudaGetLastError();  // start from a clean error state
   if (!pc || !info) return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_get_info: null argument");
   *info = spnet_pc_info{};
   for (int a = 0; a < 3; ++a) info->nH[a] = pc->nH[a];
@@ -246,6 +264,7 @@ static int with_free_vectors(spnet_pc_s* pc, const double* in, int64_t nin, doub
 }
 
 int spnet_spmv(spnet_op_t op, const double* x, double* y, int mem) {
+  cudaGetLastError();  // start from a clean error state
   if (!op || !x || !y) return fail(SPNET_ERR_BAD_INPUT, "spnet_spmv: null argument");
   cudaStream_t s = op->stream;
   DevArena tmp;
@@ -275,20 +294,19 @@ static int apply_all(spnet_pc_s* pc, const double* r, double* z) { return pc_app
 static int apply_star_term(spnet_pc_s* pc, const double* r, double* z) { return pc_apply_free(pc, r, z, 2); }
 
 int spnet_pc_apply(spnet_pc_t pc, const double* r, double* z, int mem) {
+  cudaGetLastError();  // start from a clean error state
   if (!pc || !r || !z) return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_apply: null argument");
   return with_free_vectors(pc, r, pc->N, z, pc->N, mem, apply_all);
 }
 
 int spnet_pc_stars(spnet_pc_t pc, const double* r, double* z, int mem) {
+  cudaGetLastError();  // start from a clean error state
   if (!pc || !r || !z) return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_stars: null argument");
   return with_free_vectors(pc, r, pc->N, z, pc->N, mem, apply_star_term);
 }
 
 static int restrict_fn(spnet_pc_s* pc, const double* r, double* rc) {
-  cudaStream_t s = pc->op->stream;
-  to_pc(pc, r, pc->vtmp);
-  if (pc->m0 > 0) launch_restrict(pc, pc->vtmp, rc, nullptr, s);
-  return SPNET_OK;
+  return pc_restrict_free(pc, r, rc);
 }
 
 static int coarse_fn(spnet_pc_s* pc, const double* rc, double* zc) {
@@ -300,27 +318,31 @@ static int prolong_fn(spnet_pc_s* pc, const double* zc, double* z) {
   cudaStream_t s = pc->op->stream;
   if (pc->m0 > 0)
     SPNET_CUDA_TRY(cudaMemcpyAsync(pc->zc, zc, sizeof(double) * pc->m0, cudaMemcpyDeviceToDevice, s));
-  launch_combine(pc, pc->vtmp, pc->z, 1, 0, 0, nullptr, s);
+  launch_combine(pc, pc->vtmp, pc->z, 1, 0, 0, s);
   from_pc(pc, pc->z, z);
   return SPNET_OK;
 }
 
 int spnet_pc_restrict(spnet_pc_t pc, const double* r, double* rc, int mem) {
+  cudaGetLastError();  // start from a clean error state
   if (!pc || !r || !rc) return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_restrict: null argument");
   return with_free_vectors(pc, r, pc->N, rc, pc->m0, mem, restrict_fn);
 }
 
 int spnet_pc_coarse(spnet_pc_t pc, const double* rc, double* zc, int mem) {
+  cudaGetLastError();  // start from a clean error state
   if (!pc || !rc || !zc) return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_coarse: null argument");
   return with_free_vectors(pc, rc, pc->m0, zc, pc->m0, mem, coarse_fn);
 }
 
 int spnet_pc_prolong(spnet_pc_t pc, const double* zc, double* z, int mem) {
+  cudaGetLastError();  // start from a clean error state
   if (!pc || !zc || !z) return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_prolong: null argument");
   return with_free_vectors(pc, zc, pc->m0, z, pc->N, mem, prolong_fn);
 }
 
 int spnet_pc_export(spnet_pc_t pc, int what, void* host_buf, size_t bytes) {
+  cudaGetLastError();  // start from a clean error state
   if (!pc || !host_buf) return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_export: null argument");
   cudaStream_t s = pc->op->stream;
   size_t need = 0;
@@ -343,17 +365,20 @@ int spnet_pc_export(spnet_pc_t pc, int what, void* host_buf, size_t bytes) {
 }
 
 int spnet_launch_count(int64_t* count) {
+  cudaGetLastError();  // start from a clean error state
   if (!count) return fail(SPNET_ERR_BAD_INPUT, "spnet_launch_count: null argument");
   *count = (int64_t)launch_count();
   return SPNET_OK;
 }
 
 int spnet_profile_enable(int on) {
+  cudaGetLastError();  // start from a clean error state
   profile_enable(on);
   return SPNET_OK;
 }
 
 int spnet_profile_read(int kernel, int64_t* launches, double* total_ms) {
+  cudaGetLastError();  // start from a clean error state
   if (kernel < 0 || kernel >= KID_COUNT || !launches || !total_ms)
     return fail(SPNET_ERR_BAD_INPUT, "spnet_profile_read: bad argument");
   long long n = 0;
@@ -365,6 +390,7 @@ int spnet_profile_read(int kernel, int64_t* launches, double* total_ms) {
 }
 
 int spnet_profile_reset(void) {
+  cudaGetLastError();  // start from a clean error state
   profile_reset();
   return SPNET_OK;
 }

@@ -22,23 +22,24 @@ template <class T>
 __global__ void k_pivot_inverse(T* Z, int64_t m0, int k0, int kb, double* P, int* flags) {
   __shared__ double D[NB][NB + 1];
   __shared__ double col[NB], row[NB];
-  __shared__ double piv;
+  __shared__ double ipiv;
   const int i = threadIdx.y, j = threadIdx.x;
   if (i < kb && j < kb) D[i][j] = (double)Z[(int64_t)(k0 + i) * m0 + (k0 + j)];
   __syncthreads();
   for (int p = 0; p < kb; ++p) {
     if (i == 0 && j == 0) {
-      piv = D[p][p];
+      double piv = D[p][p];
       if (!(piv > 0.0)) {
         atomicOr(flags, FLAG_COARSE_SPD);
         piv = 1.0;
       }
+      ipiv = 1.0 / piv;
     }
     if (i == 0 && j < kb) row[j] = D[p][j];
     if (j == 0 && i < kb) col[i] = D[i][p];
     __syncthreads();
     if (i < kb && j < kb) {
-      const double ip = 1.0 / piv;
+      const double ip = ipiv;
       if (i != p && j != p) D[i][j] -= col[i] * row[j] * ip;
       else if (i == p && j == p) D[i][j] = -ip;
       else if (i == p) D[i][j] = row[j] * ip;
@@ -51,65 +52,107 @@ __global__ void k_pivot_inverse(T* Z, int64_t m0, int k0, int kb, double* P, int
 
 // R = Z[k0:k0+kb, :] (copy of the pivot rows), Tm = P R
 template <class T>
-__global__ void k_panel(const T* Z, int64_t m0, int k0, int kb, const double* P, T* R, T* Tm) {
+__global__ void __launch_bounds__(256) k_panel(const T* Z, int64_t m0, int k0, int kb, const double* P,
+                                               T* R, T* Tm) {
+  __shared__ T sP[NB][NB];
+  for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
+    const int t = q / NB, u = q % NB;
+    sP[t][u] = (t < kb && u < kb) ? (T)P[t * NB + u] : (T)0;
+  }
+  __syncthreads();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < m0;
        c += (int64_t)gridDim.x * blockDim.x) {
     T col[NB];
-    for (int t = 0; t < kb; ++t) col[t] = Z[(int64_t)(k0 + t) * m0 + c];
-    for (int t = 0; t < kb; ++t) R[(int64_t)t * m0 + c] = col[t];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) col[t] = t < kb ? Z[(int64_t)(k0 + t) * m0 + c] : (T)0;
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+      if (t < kb) R[(int64_t)t * m0 + c] = col[t];
+#pragma unroll 4
     for (int t = 0; t < kb; ++t) {
       T acc = 0;
-      for (int u = 0; u < kb; ++u) acc += (T)P[t * NB + u] * col[u];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) acc += sP[t][u] * col[u];
       Tm[(int64_t)t * m0 + c] = acc;
     }
   }
 }
 
-// the rank-kb sweep update of every entry (64x64 tiles, 4x4 per thread)
-template <class T>
+// the rank-kb sweep update: tiles of TB x TB entries, (TB/16)^2 per thread; only
+// tiles on or above the block diagonal are computed, each writes itself and its
+// mirror image (the swept matrix stays symmetric)
+template <class T, int TB>
 __global__ void __launch_bounds__(256) k_sweep(T* Z, int64_t m0, int k0, int kb, const double* P,
                                                const T* __restrict__ R, const T* __restrict__ Tm) {
-  __shared__ T sR[NB][64];
-  __shared__ T sT[NB][64];
-  const int64_t i0 = (int64_t)blockIdx.y * 64, j0 = (int64_t)blockIdx.x * 64;
+  constexpr int RT = TB / 16;  // register tile
+  extern __shared__ __align__(16) char sm_raw[];
+  T (*sR)[TB] = reinterpret_cast<T (*)[TB]>(sm_raw);
+  T (*sT)[TB] = reinterpret_cast<T (*)[TB]>(sm_raw + sizeof(T) * NB * TB);
+  T (*sO)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(sm_raw + 2 * sizeof(T) * NB * TB);
+  // map the linear block index to an upper-triangular tile (bi <= bj)
+  const int nt = (int)((m0 + TB - 1) / TB);
+  int rem = blockIdx.x, bi = 0;
+  while (rem >= nt - bi) {
+    rem -= nt - bi;
+    ++bi;
+  }
+  const int bj = bi + rem;
+  const int64_t i0 = (int64_t)bi * TB, j0 = (int64_t)bj * TB;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  for (int q = threadIdx.x; q < NB * 64; q += 256) {
-    int t = q / 64, c = q % 64;
+  for (int q = threadIdx.x; q < NB * TB; q += 256) {
+    const int t = q / TB, c = q % TB;
     sR[t][c] = (t < kb && i0 + c < m0) ? R[(int64_t)t * m0 + i0 + c] : (T)0;
     sT[t][c] = (t < kb && j0 + c < m0) ? Tm[(int64_t)t * m0 + j0 + c] : (T)0;
   }
   __syncthreads();
-  T acc[4][4];
+  T acc[RT][RT];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RT; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+    for (int b = 0; b < RT; ++b) acc[a][b] = 0;
   for (int t = 0; t < kb; ++t) {
-    T ri[4], tj[4];
+    T ri[RT], tj[RT];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) ri[a] = sR[t][ty * 4 + a];
+    for (int a = 0; a < RT; ++a) ri[a] = sR[t][ty + 16 * a];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) tj[b] = sT[t][tx * 4 + b];
+    for (int b = 0; b < RT; ++b) tj[b] = sT[t][tx + 16 * b];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < RT; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] += ri[a] * tj[b];
+      for (int b = 0; b < RT; ++b) acc[a][b] += ri[a] * tj[b];
   }
+  // new values of the tile (i, j) in shared memory
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int64_t i = i0 + ty * 4 + a;
-    if (i >= m0) continue;
+  for (int a = 0; a < RT; ++a) {
+    const int li = ty + 16 * a;
+    const int64_t i = i0 + li;
     const bool iK = i >= k0 && i < k0 + kb;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int64_t j = j0 + tx * 4 + b;
-      if (j >= m0) continue;
-      const bool jK = j >= k0 && j < k0 + kb;
-      T* zz = &Z[i * m0 + j];
-      if (!iK && !jK) *zz -= acc[a][b];
-      else if (iK && jK) *zz = (T)(-P[(i - k0) * NB + (j - k0)]);
-      else if (iK) *zz = sT[i - k0][tx * 4 + b];
-      else *zz = Tm[(j - k0) * m0 + i];  // A_iK P = (P A_Ki)^T by symmetry
+    for (int b = 0; b < RT; ++b) {
+      const int lj = tx + 16 * b;
+      const int64_t j = j0 + lj;
+      T v = 0;
+      if (i < m0 && j < m0) {
+        const bool jK = j >= k0 && j < k0 + kb;
+        if (!iK && !jK) v = Z[i * m0 + j] - acc[a][b];
+        else if (iK && jK) v = (T)(-P[(i - k0) * NB + (j - k0)]);
+        else if (iK) v = sT[i - k0][lj];
+        else v = Tm[(j - k0) * m0 + i];  // A_iK P = (P A_Ki)^T by symmetry
+      }
+      sO[li][lj] = v;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < TB * TB; q += 256) {
+    const int li = q / TB, lj = q % TB;
+    const int64_t i = i0 + li, j = j0 + lj;
+    if (i < m0 && j < m0) Z[i * m0 + j] = sO[li][lj];
+  }
+  if (bi != bj) {
+    for (int q = threadIdx.x; q < TB * TB; q += 256) {
+      const int lj = q / TB, li = q % TB;  // write the mirror tile row by row
+      const int64_t i = i0 + li, j = j0 + lj;
+      if (i < m0 && j < m0) Z[j * m0 + i] = sO[li][lj];
     }
   }
 }
@@ -145,7 +188,18 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
   note_launch();
   k_negate_from<T><<<grid, 256, 0, s>>>(A0, Z, m0 * m0, 0);
   SPNET_CUDA_TRY(cudaMemsetAsync(pc->op->dflags, 0, sizeof(int), s));
-  dim3 tiles((unsigned)((m0 + 63) / 64), (unsigned)((m0 + 63) / 64));
+  constexpr int TB = sizeof(T) == 4 ? 128 : 64;
+  const int nt = (int)((m0 + TB - 1) / TB);
+  const unsigned tiles = (unsigned)(nt * (nt + 1) / 2);
+  const size_t smem = sizeof(T) * (2 * NB * TB + TB * (TB + 1));
+  static bool attr_set[64] = {};  // per device and instantiation; the size depends only on T
+  int dev = 0;
+  SPNET_CUDA_TRY(cudaGetDevice(&dev));
+  dev &= 63;
+  if (!attr_set[dev]) {
+    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_sweep<T, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set[dev] = true;
+  }
   for (int k0 = 0; k0 < m0; k0 += NB) {
     const int kb = (int)((m0 - k0) < NB ? (m0 - k0) : NB);
     note_launch();
@@ -154,7 +208,7 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
     k_panel<T><<<(unsigned)((m0 + 255) / 256), 256, 0, s>>>(Z, m0, k0, kb, P, R, Tm);
     note_launch();
     ProfScope ps(KID_SWEEP, s);
-    k_sweep<T><<<tiles, 256, 0, s>>>(Z, m0, k0, kb, P, R, Tm);
+    k_sweep<T, TB><<<tiles, 256, smem, s>>>(Z, m0, k0, kb, P, R, Tm);
   }
   note_launch();
   k_negate_from<T><<<grid, 256, 0, s>>>(A0, Z, m0 * m0, 1);

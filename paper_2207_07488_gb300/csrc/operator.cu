@@ -201,31 +201,14 @@ int choose_spmv_lanes(const Csr& A) {
   return 32;
 }
 
-int build_operator(int dim, int ndof, int64_t n_nodes, const double* coords, const int64_t* row_ptr,
-                   const int32_t* col_idx, const double* vals, int64_t n_dir, const int64_t* dir,
-                   const double* domain_hi, int mem, cudaStream_t s, spnet_op_s** out) {
-  if (dim < 2 || dim > 3) return fail(SPNET_ERR_BAD_INPUT, "build_network_operator: dim must be 2 or 3");
-  if (ndof != 1 && ndof != 3) return fail(SPNET_ERR_BAD_INPUT, "build_network_operator: ndof must be 1 or 3");
-  if (n_nodes <= 0 || n_dir < 0) return fail(SPNET_ERR_BAD_INPUT, "build_network_operator: bad sizes");
-  if (n_nodes * ndof >= ((int64_t)1 << 31))
-    return fail(SPNET_ERR_UNSUPPORTED, "build_network_operator: more than 2^31 dofs");
-  for (int a = 0; a < dim; ++a)
-    if (!(domain_hi[a] > 0.0)) return fail(SPNET_ERR_BAD_INPUT, "build_network_operator: domain side <= 0");
-  spnet_op_s* op = new spnet_op_s();
-  op->dim = dim;
-  op->ndof = ndof;
-  op->n_nodes = n_nodes;
-  op->n_dof = n_nodes * ndof;
-  op->n_dir = n_dir;
-  op->stream = s;
-  op->mem.stream = s;
-  for (int a = 0; a < dim; ++a) op->domain[a] = domain_hi[a];
-  auto bail = [&](int rc) {
-    op->mem.free_all();
-    cudaStreamSynchronize(s);
-    delete op;
-    return rc;
-  };
+// everything after the handle exists; temporary buffers are released (on the
+// operator's stream) before the caller decides whether to keep the handle
+static int build_operator_fill(spnet_op_s* op, const double* coords, const int64_t* row_ptr,
+                               const int32_t* col_idx, const double* vals, const int64_t* dir,
+                               int mem) {
+  const int dim = op->dim;
+  const int64_t n_nodes = op->n_nodes, n_dir = op->n_dir;
+  cudaStream_t s = op->stream;
   DevArena tmp;
   tmp.stream = s;
   struct Guard {
@@ -240,24 +223,24 @@ int build_operator(int dim, int ndof, int64_t n_nodes, const double* coords, con
   } else {
     if (cudaMemcpyAsync(&nnz, row_ptr + nd, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
-      return bail(fail(SPNET_ERR_CUDA, "build_network_operator: reading nnz"));
+      return (fail(SPNET_ERR_CUDA, "build_network_operator: reading nnz"));
   }
-  if (nnz < 0 || nnz >= ((int64_t)1 << 31)) return bail(fail(SPNET_ERR_UNSUPPORTED, "nnz out of range"));
+  if (nnz < 0 || nnz >= ((int64_t)1 << 31)) return (fail(SPNET_ERR_UNSUPPORTED, "nnz out of range"));
   int64_t *d_ptr = nullptr;
   int32_t* d_col = nullptr;
   double* d_val = nullptr;
   if ((rc = tmp.get(&d_ptr, nd + 1)) || (rc = tmp.get(&d_col, nnz)) || (rc = tmp.get(&d_val, nnz)))
-    return bail(rc);
+    return rc;
   if ((rc = copy_in(row_ptr, d_ptr, sizeof(int64_t) * (nd + 1), mem, s)) ||
       (rc = copy_in(col_idx, d_col, sizeof(int32_t) * nnz, mem, s)) ||
       (rc = copy_in(vals, d_val, sizeof(double) * nnz, mem, s)))
-    return bail(rc);
+    return rc;
   if ((rc = op->mem.get(&op->coords, n_nodes * dim)) || (rc = op->mem.get(&op->dflags, 1)) ||
       (rc = op->mem.get(&op->dir_dofs, n_dir)) || (rc = op->mem.get(&op->free_of, nd)))
-    return bail(rc);
+    return rc;
   if ((rc = copy_in(coords, op->coords, sizeof(double) * n_nodes * dim, mem, s)) ||
       (rc = copy_in(dir, op->dir_dofs, sizeof(int64_t) * n_dir, mem, s)))
-    return bail(rc);
+    return rc;
   cudaMemsetAsync(op->dflags, 0, sizeof(int), s);
   int grid = 4 * num_sms();
   note_launch();
@@ -267,46 +250,85 @@ int build_operator(int dim, int ndof, int64_t n_nodes, const double* coords, con
                                       op->domain[2], op->dflags);
   int32_t* is_free = nullptr;
   int64_t* pos = nullptr;
-  if ((rc = tmp.get(&is_free, nd)) || (rc = tmp.get(&pos, nd + 1))) return bail(rc);
+  if ((rc = tmp.get(&is_free, nd)) || (rc = tmp.get(&pos, nd + 1))) return rc;
   // every dof starts free; the Dirichlet ones are then cleared
   cudaMemsetAsync(op->free_of, 0xff, sizeof(int64_t) * nd, s);
   fill_i32(is_free, nd, 1, s);
   note_launch();
   k_mark_dirichlet<<<grid, 256, 0, s>>>(n_dir, op->dir_dofs, nd, op->free_of, is_free, op->dflags);
-  if ((rc = check_flags(op->dflags, s, "build_network_operator"))) return bail(rc);
-  if ((rc = scan_exclusive(is_free, pos, nd, s, tmp))) return bail(rc);
+  if ((rc = check_flags(op->dflags, s, "build_network_operator"))) return rc;
+  if ((rc = scan_exclusive(is_free, pos, nd, s, tmp))) return rc;
   int64_t n_free = 0;
   cudaMemcpyAsync(&n_free, pos + nd, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   op->n_free = n_free;
-  if (n_free != nd - n_dir) return bail(fail(SPNET_ERR_BAD_INPUT, "duplicate Dirichlet dofs"));
-  if ((rc = op->mem.get(&op->free_dofs, n_free))) return bail(rc);
+  if (n_free != nd - n_dir) return (fail(SPNET_ERR_BAD_INPUT, "duplicate Dirichlet dofs"));
+  if ((rc = op->mem.get(&op->free_dofs, n_free))) return rc;
   note_launch();
   k_free_index<<<grid, 256, 0, s>>>(nd, is_free, pos, op->free_of, op->free_dofs);
   int32_t *len_ff = nullptr, *len_fd = nullptr;
-  if ((rc = tmp.get(&len_ff, n_free + 1)) || (rc = tmp.get(&len_fd, n_free + 1))) return bail(rc);
+  if ((rc = tmp.get(&len_ff, n_free + 1)) || (rc = tmp.get(&len_fd, n_free + 1))) return rc;
   note_launch();
   k_split_count<<<grid, 256, 0, s>>>(n_free, op->free_dofs, op->free_of, d_ptr, d_col, len_ff, len_fd);
   op->ff.n = op->fd.n = n_free;
   if ((rc = op->mem.get(&op->ff.ptr, n_free + 1)) || (rc = op->mem.get(&op->fd.ptr, n_free + 1)))
-    return bail(rc);
+    return rc;
   if ((rc = scan_exclusive(len_ff, op->ff.ptr, n_free, s, tmp)) ||
       (rc = scan_exclusive(len_fd, op->fd.ptr, n_free, s, tmp)))
-    return bail(rc);
+    return rc;
   cudaMemcpyAsync(&op->ff.nnz, op->ff.ptr + n_free, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&op->fd.nnz, op->fd.ptr + n_free, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   if ((rc = op->mem.get(&op->ff.col, op->ff.nnz)) || (rc = op->mem.get(&op->ff.val, op->ff.nnz)) ||
       (rc = op->mem.get(&op->fd.col, op->fd.nnz)) || (rc = op->mem.get(&op->fd.val, op->fd.nnz)))
-    return bail(rc);
+    return rc;
   note_launch();
   k_split_fill<<<grid, 256, 0, s>>>(n_free, op->free_dofs, op->free_of, d_ptr, d_col, d_val,
                                     op->ff.ptr, op->ff.col, op->ff.val, op->fd.ptr, op->fd.col,
                                     op->fd.val);
   note_launch();
   k_check_sym<<<grid, 256, 0, s>>>(n_free, op->ff.ptr, op->ff.col, op->ff.val, op->dflags);
-  if ((rc = check_flags(op->dflags, s, "build_network_operator"))) return bail(rc);
-  if (cudaGetLastError() != cudaSuccess) return bail(fail(SPNET_ERR_CUDA, "build_network_operator: launch failed"));
+  if ((rc = check_flags(op->dflags, s, "build_network_operator"))) return rc;
+  if (cudaGetLastError() != cudaSuccess) return (fail(SPNET_ERR_CUDA, "build_network_operator: launch failed"));
+  return SPNET_OK;
+}
+
+int build_operator(int dim, int ndof, int64_t n_nodes, const double* coords, const int64_t* row_ptr,
+                   const int32_t* col_idx, const double* vals, int64_t n_dir, const int64_t* dir,
+                   const double* domain_hi, int mem, cudaStream_t s, spnet_op_s** out) {
+  if (dim < 2 || dim > 3) return fail(SPNET_ERR_BAD_INPUT, "build_network_operator: dim must be 2 or 3");
+  if (ndof != 1 && ndof != 3) return fail(SPNET_ERR_BAD_INPUT, "build_network_operator: ndof must be 1 or 3");
+  if (n_nodes <= 0 || n_dir < 0) return fail(SPNET_ERR_BAD_INPUT, "build_network_operator: bad sizes");
+  if (n_nodes * ndof >= ((int64_t)1 << 31))
+    return fail(SPNET_ERR_UNSUPPORTED, "build_network_operator: more than 2^31 dofs");
+  for (int a = 0; a < dim; ++a)
+    if (!(domain_hi[a] > 0.0)) return fail(SPNET_ERR_BAD_INPUT, "build_network_operator: domain side <= 0");
+  spnet_op_s* op = new spnet_op_s();
+  if (s == 0) {
+    // the legacy default stream cannot be captured into CUDA graphs: work on a
+    // private stream instead (every call synchronises it before returning)
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      delete op;
+      return fail(SPNET_ERR_CUDA, "build_network_operator: cannot create a stream");
+    }
+    op->own_stream = true;
+  }
+  op->dim = dim;
+  op->ndof = ndof;
+  op->n_nodes = n_nodes;
+  op->n_dof = n_nodes * ndof;
+  op->n_dir = n_dir;
+  op->stream = s;
+  op->mem.stream = s;
+  for (int a = 0; a < dim; ++a) op->domain[a] = domain_hi[a];
+  const int rc = build_operator_fill(op, coords, row_ptr, col_idx, vals, dir, mem);
+  if (rc != SPNET_OK) {
+    op->mem.free_all();
+    cudaStreamSynchronize(s);
+    if (op->own_stream) cudaStreamDestroy(s);
+    delete op;
+    return rc;
+  }
   *out = op;
   return SPNET_OK;
 }

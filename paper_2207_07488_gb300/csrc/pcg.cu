@@ -1,39 +1,30 @@
 // Preconditioned conjugate gradients (Section 4.2) on the free dofs in pc
 // order, and the restriction / combination steps of B (Section 4.1).
 //
-// Each iteration is a fixed sequence of kernels:
-//   spmv      q = A p, partial (p, q)
-//   update    alpha = (r, z)/(p, q); x += alpha p; r -= alpha q; partial |r|^2
-//   restrict  stop test |r| <= rtol |b| (sets `done`), r_c = R_0 r
-//   stars     w_j = A_j^{-1} E_j^T r for every star
-//   coarse    z_c = A_0^{-1} r_c
-//   combine   z = R_0^T z_c + sum_j E_j w_j, partial (r, z) [and (r, z_old)]
-//   direction beta; p = z + beta p
-// Every kernel returns at once when `done` is set, so the host may launch
-// several iterations ahead and read the state only now and then.  Partial
-// sums use a fixed grid and are reduced in a fixed order by every block:
-// results are bitwise reproducible.  Scalars live on the device; a value a
-// kernel publishes is read only by later kernels.
+// One iteration is six kernels; the star solves run on a second stream beside
+// the restriction and the coarse solve:
+//   spmv_dir  p = z + beta p;  q = A z + beta q  (= A p);  (p, q) -> alpha
+//   update    x += alpha p; r -= alpha q; |r|^2 -> stop test; per element the
+//             Q1-weighted sums of r at its 2^d corners
+//   restrict  r_c = R_0 r from the element sums         | stars  w_j = A_j^{-1} E_j^T r
+//   coarse    z_c = A_0^{-1} r_c                        |
+//   combine   z = R_0^T z_c + sum_j E_j w_j; (r, z) [and (r, z_old)] -> beta
+// Each reduction is finished by the last block of its kernel (fixed order:
+// bitwise reproducible), which publishes the scalar for the next kernel.
+// Every kernel returns at once when `done` is set, so chunks of iterations
+// are captured once in a CUDA graph and replayed; the host reads the state
+// only between chunks.
 #include <cmath>
 
 #include "spnet_internal.cuh"
 
 namespace spnet {
 
-__device__ __forceinline__ double block_reduce_partials(const double* partial, int G, double* sh) {
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < G; i += 32) s += partial[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) sh[0] = s;
-  }
-  __syncthreads();
-  double v = sh[0];
-  __syncthreads();
-  return v;
-}
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
-__device__ __forceinline__ void block_write_partial(double v, double* out, double* sh) {
+// block sum of one value per thread into out[blockIdx.x]; fixed order
+__device__ __forceinline__ void block_partial(double v, double* out, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
@@ -45,8 +36,29 @@ __device__ __forceinline__ void block_write_partial(double v, double* out, doubl
   __syncthreads();
 }
 
-#define GRID_STRIDE(i, n) \
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+// true in the block that finishes last (its partials and everyone's are visible)
+__device__ __forceinline__ bool last_block(unsigned* cnt) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+// sum of n partials by one block in a fixed order (result valid in every thread)
+__device__ __forceinline__ double block_sum(const double* part, int n, double* sh) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += ((volatile const double*)part)[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  __syncthreads();
+  return t;
+}
 
 // b = f_I - K_ID g (Section 3), in pc order
 __global__ void k_build_rhs(int64_t N, const int32_t* perm, const int64_t* free_dofs, const double* f,
@@ -82,111 +94,178 @@ __global__ void k_expand(int64_t n_dof, const int64_t* free_of, const int32_t* i
   }
 }
 
-__global__ void k_dot_partial(int64_t N, const double* a, const double* b, double* partial) {
-  __shared__ double sh[32];
-  double s = 0.0;
-  GRID_STRIDE(i, N) s = fma(a[i], b[i], s);
-  block_write_partial(s, partial, sh);
-}
-
-__global__ void k_reduce_to(const double* partial, int G, double* out) {
-  __shared__ double sh[1];
-  double v = block_reduce_partials(partial, G, sh);
-  if (threadIdx.x == 0) *out = v;
-}
-
-// r = b - q, partial |r|^2
-__global__ void k_residual(int64_t N, const double* b, const double* q, double* r, double* partial) {
+// r = b - q and |r|^2 (or |b|^2 when q is null), finished by the last block
+__global__ void k_residual(int64_t N, const double* b, const double* q, double* r, double* partial,
+                           double* out, unsigned* cnt) {
   __shared__ double sh[32];
   double s = 0.0;
   GRID_STRIDE(i, N) {
-    double v = b[i] - q[i];
-    r[i] = v;
+    double v = q ? b[i] - q[i] : b[i];
+    if (r) r[i] = v;
     s = fma(v, v, s);
   }
-  block_write_partial(s, partial, sh);
+  block_partial(s, partial, sh);
+  if (last_block(cnt)) {
+    double t = block_sum(partial, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      *out = t;
+      *cnt = 0;
+    }
+  }
 }
 
-__global__ void k_update_xr(int64_t N, double* x, double* r, const double* p, const double* q,
-                            const double* part_pq, double* part_rr, int G, Scal* sc) {
+// ---------------------------------------------------------------------------
+// spmv_dir: p = z + beta p, q = A z + beta q, partial (p, q); last block: alpha
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(256) k_spmv_dir(int64_t n, const int64_t* __restrict__ ptr,
+                                                  const int32_t* __restrict__ col,
+                                                  const double* __restrict__ val,
+                                                  const double* __restrict__ z, double* __restrict__ p,
+                                                  double* __restrict__ q, double* partial, Scal* sc) {
   __shared__ double sh[32];
   if (sc->done) return;
-  const double pq = block_reduce_partials(part_pq, G, sh);
-  const double rz = sc->rz_old;  // (r, z) published by the previous direction update
-  const double alpha = rz / pq;
-  double s = 0.0;
-  GRID_STRIDE(i, N) {
-    x[i] = fma(alpha, p[i], x[i]);
-    double v = fma(-alpha, q[i], r[i]);
-    r[i] = v;
-    s = fma(v, v, s);
+  const double beta = sc->beta;
+  constexpr int RPW = 32 / L;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % L;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double dot = 0.0;
+  for (int64_t base = gwarp * RPW; base < n; base += nwarps * RPW) {
+    const int64_t row = base + lane / L;
+    const bool valid = row < n;
+    double s = 0.0;
+    if (valid) {
+      const int64_t a = ptr[row], b = ptr[row + 1];
+      for (int64_t k = a + sub; k < b; k += L) s = fma(val[k], __ldg(&z[col[k]]), s);
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, L);
+    if (valid && sub == 0) {
+      double pn, qn;
+      if (beta == 0.0) {
+        pn = z[row];
+        qn = s;
+      } else {
+        pn = fma(beta, p[row], z[row]);
+        qn = fma(beta, q[row], s);
+      }
+      p[row] = pn;
+      q[row] = qn;
+      dot = fma(pn, qn, dot);
+    }
   }
-  block_write_partial(s, part_rr, sh);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    sc->pq = pq;
-    sc->alpha = alpha;
-    sc->rz = rz;
-    sc->iter += 1;
+  block_partial(dot, partial, sh);
+  if (last_block(&sc->cnt[0])) {
+    double pq = block_sum(partial, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      sc->pq = pq;
+      sc->alpha = sc->rz / pq;
+      sc->cnt[0] = 0;
+    }
   }
 }
 
-// r_c = R_0 r; one warp per mesh node; optionally the stop test first
-__global__ void k_restrict(int n_mesh, Mesh m, int ndof, int64_t N, const int32_t* elem_ptr,
-                           const int8_t* comp_of, const double* q1w, const int32_t* cidx,
-                           const double* r, double* rc, Scal* sc, const double* part_rr, int G,
-                           double tol2_rel, int maxit) {
-  __shared__ double sh[1];
-  if (sc) {
-    if (sc->done) return;
-    const double rr = block_reduce_partials(part_rr, G, sh);
-    const bool stop = sqrt(rr) <= tol2_rel * sqrt(sc->bb) || sc->iter >= maxit;
-    if (stop) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
-        sc->rr = rr;
-        sc->done = 1;
-      }
-      return;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc->rr = rr;
-  }
+// ---------------------------------------------------------------------------
+// update (one warp per element): x += alpha p, r -= alpha q (mode 0) or r as is
+// (mode 1); |r|^2; corner sums E[e][c][a] = sum_{p in e, comp a} phi_c(p) r_p.
+// Last block: |r|^2 and, in mode 0, the iteration count and the stop test.
+// ---------------------------------------------------------------------------
+template <int NC, int ND>
+__global__ void __launch_bounds__(256) k_update(int n_elem, int64_t N, const int32_t* __restrict__ elem_ptr,
+                                                const int8_t* __restrict__ comp_of,
+                                                const double* __restrict__ q1w, double* __restrict__ x,
+                                                double* __restrict__ r, const double* __restrict__ p,
+                                                const double* __restrict__ q, double* __restrict__ epart,
+                                                double* partial, Scal* sc, int mode) {
+  __shared__ double sh[32];
+  if (mode == 0 && sc->done) return;
+  const double alpha = mode == 0 ? sc->alpha : 0.0;
   const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_mesh; k += nw) {
-    bool any = false;
-    for (int a = 0; a < ndof; ++a) any |= cidx[k * ndof + a] >= 0;
-    if (!any) continue;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double rr = 0.0;
+  for (int64_t e = gwarp; e < n_elem; e += nwarps) {
+    double acc[NC * ND];
+#pragma unroll
+    for (int t = 0; t < NC * ND; ++t) acc[t] = 0.0;
+    const int a0 = elem_ptr[e], a1 = elem_ptr[e + 1];
+    for (int i = a0 + lane; i < a1; i += 32) {
+      double v;
+      if (mode == 0) {
+        x[i] = fma(alpha, p[i], x[i]);
+        v = fma(-alpha, q[i], r[i]);
+        r[i] = v;
+      } else {
+        v = r[i];
+      }
+      rr = fma(v, v, rr);
+      const int a = ND == 1 ? 0 : comp_of[i];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const double wv = q1w[(int64_t)c * N + i] * v;
+        if (ND == 1) {
+          acc[c] += wv;
+        } else {
+#pragma unroll
+          for (int b = 0; b < ND; ++b)
+            if (b == a) acc[c * ND + b] += wv;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NC * ND; ++t) {
+      double v = acc[t];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) epart[e * (NC * ND) + t] = v;
+    }
+  }
+  block_partial(rr, partial, sh);
+  if (last_block(&sc->cnt[1])) {
+    double t = block_sum(partial, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      sc->rr = t;
+      if (mode == 0) {
+        sc->iter += 1;
+        if (sqrt(t) <= sc->rtol * sqrt(sc->bb) || sc->iter >= sc->maxit) sc->done = 1;
+      }
+      sc->cnt[1] = 0;
+    }
+  }
+}
+
+// r_c = R_0 r from the corner sums of the elements around each mesh node
+__global__ void k_restrict(int n_mesh, Mesh m, int ndof, const double* __restrict__ epart,
+                           const int32_t* __restrict__ cidx, double* __restrict__ rc, const int* done) {
+  if (done && *done) return;
+  GRID_STRIDE(ka, (int64_t)n_mesh * ndof) {
+    const int ci = cidx[ka];
+    if (ci < 0) continue;
+    const int k = (int)(ka / ndof), a = (int)(ka % ndof);
     int km[3];
-    mesh_multi(m, (int)k, km);
-    double acc[3] = {0.0, 0.0, 0.0};
+    mesh_multi(m, k, km);
+    double s = 0.0;
     for (int cp = 0; cp < m.nc; ++cp) {
-      int e = elem_around(m, km, cp);
+      const int e = elem_around(m, km, cp);
       if (e < 0) continue;
       const int c = (m.nc - 1) - cp;  // corner of e at mesh node k
-      const double* wc = q1w + (int64_t)c * N;
-      for (int p = elem_ptr[e] + lane; p < elem_ptr[e + 1]; p += 32) {
-        double v = wc[p] * r[p];
-        if (ndof == 1) acc[0] += v;
-        else acc[comp_of[p]] += v;
-      }
+      s += epart[((int64_t)e * m.nc + c) * ndof + a];
     }
-    for (int a = 0; a < ndof; ++a) {
-      double v = acc[a];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      int ci = cidx[k * ndof + a];
-      if (lane == 0 && ci >= 0) rc[ci] = v;
-    }
+    rc[ci] = s;
   }
 }
 
-// z = [R_0^T z_c] + [sum_j E_j w_j]; partial (r, z) and (r, z_old)
-__global__ void k_combine(int64_t N, Mesh m, int ndof, const int32_t* elem_of, const int8_t* comp_of,
-                          const int32_t* elem_ptr, const double* q1w, const int32_t* cidx,
-                          const double* zc, const int32_t* elem_star_off, const int32_t* star_of_mesh,
-                          const int64_t* star_ptr, const double* w, const double* r, double* z,
-                          double* part_rz, double* part_rzo, int with_coarse, int with_stars,
-                          const int* done) {
+// z = [R_0^T z_c] + [sum_j E_j w_j]; partials (r, z) and (r, z_old); last block: beta
+__global__ void __launch_bounds__(256) k_combine(int64_t N, Mesh m, int ndof, const int32_t* elem_of,
+                                                 const int8_t* comp_of, const int32_t* elem_ptr,
+                                                 const double* q1w, const int32_t* cidx, const double* zc,
+                                                 const int32_t* elem_star_off, const int32_t* star_of_mesh,
+                                                 const int64_t* star_ptr, const double* w, const double* r,
+                                                 double* z, double* part1, double* part2, int with_coarse,
+                                                 int with_stars, Scal* sc, int flexible, int first) {
   __shared__ double sh[32];
-  if (done && *done) return;
+  if (sc && sc->done) return;
   double s1 = 0.0, s2 = 0.0;
   GRID_STRIDE(p, N) {
     const int e = elem_of[p];
@@ -207,103 +286,151 @@ __global__ void k_combine(int64_t N, Mesh m, int ndof, const int32_t* elem_of, c
         v += w[star_ptr[st] + so + off_e];
       }
     }
-    if (part_rz) {
+    if (sc) {
       s1 = fma(r[p], v, s1);
-      if (part_rzo) s2 = fma(r[p], z[p], s2);
+      s2 = fma(r[p], z[p], s2);
     }
     z[p] = v;
   }
-  if (part_rz) {
-    block_write_partial(s1, part_rz, sh);
-    if (part_rzo) block_write_partial(s2, part_rzo, sh);
-  }
-}
-
-// beta and p = z + beta p
-__global__ void k_direction(int64_t N, const double* z, double* p, const double* part_rz,
-                            const double* part_rzo, int G, int flexible, int first, Scal* sc) {
-  __shared__ double sh[1];
-  if (sc->done) return;
-  const double rz_new = block_reduce_partials(part_rz, G, sh);
-  double beta = 0.0;
-  if (!first) {
-    const double rz = sc->rz;
-    if (flexible) {
-      const double rzo = block_reduce_partials(part_rzo, G, sh);
-      beta = (rz_new - rzo) / rz;
-    } else {
-      beta = rz_new / rz;
+  if (!sc) return;
+  block_partial(s1, part1, sh);
+  block_partial(s2, part2, sh);
+  if (last_block(&sc->cnt[2])) {
+    const double rz_new = block_sum(part1, gridDim.x, sh);
+    const double rzo = block_sum(part2, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      double beta = 0.0;
+      if (!first) beta = flexible ? (rz_new - rzo) / sc->rz : rz_new / sc->rz;
+      sc->beta = beta;
+      sc->rz = rz_new;
+      sc->cnt[2] = 0;
     }
   }
-  GRID_STRIDE(i, N) p[i] = first ? z[i] : fma(beta, p[i], z[i]);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    sc->beta = beta;
-    sc->rz_old = rz_new;
+}
+
+template <int NC, int ND>
+static void launch_update_t(spnet_pc_s* pc, double* x, double* r, const double* p, const double* q,
+                            Scal* sc, int mode, cudaStream_t s) {
+  k_update<NC, ND><<<pc->G, 256, 0, s>>>(pc->n_elem, pc->N, pc->elem_ptr, pc->comp_of, pc->q1w, x, r,
+                                        p, q, pc->epart, pc->partial + pc->G, sc, mode);
+}
+
+static void launch_update(spnet_pc_s* pc, double* x, double* r, const double* p, const double* q,
+                          Scal* sc, int mode, cudaStream_t s) {
+  note_launch();
+  ProfScope ps(KID_UPDATE, s);
+  if (pc->nc == 4 && pc->ndof == 1) launch_update_t<4, 1>(pc, x, r, p, q, sc, mode, s);
+  else if (pc->nc == 8 && pc->ndof == 1) launch_update_t<8, 1>(pc, x, r, p, q, sc, mode, s);
+  else if (pc->nc == 4) launch_update_t<4, 3>(pc, x, r, p, q, sc, mode, s);
+  else launch_update_t<8, 3>(pc, x, r, p, q, sc, mode, s);
+}
+
+static void launch_spmv_dir(spnet_pc_s* pc, cudaStream_t s) {
+  note_launch();
+  ProfScope ps(KID_SPMV, s);
+  const Csr& A = pc->K;
+  const int G = pc->G;
+  switch (pc->spmv_lanes) {
+    case 1: k_spmv_dir<1><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, pc->partial, pc->scal); break;
+    case 2: k_spmv_dir<2><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, pc->partial, pc->scal); break;
+    case 4: k_spmv_dir<4><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, pc->partial, pc->scal); break;
+    case 8: k_spmv_dir<8><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, pc->partial, pc->scal); break;
+    case 16: k_spmv_dir<16><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, pc->partial, pc->scal); break;
+    default: k_spmv_dir<32><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, pc->partial, pc->scal); break;
   }
 }
 
-__global__ void k_copy(int64_t N, const double* a, double* b) {
-  GRID_STRIDE(i, N) b[i] = a[i];
-}
-
-void launch_restrict(spnet_pc_s* pc, const double* r, double* rc, const int* done, cudaStream_t s) {
-  (void)done;
+void launch_restrict(spnet_pc_s* pc, double* rc, const int* done, cudaStream_t s) {
   if (pc->m0 == 0) return;
-  int blocks = (pc->n_mesh + 7) / 8;
   note_launch();
-  k_restrict<<<blocks, 256, 0, s>>>(pc->n_mesh, mesh_of_pc(pc), pc->ndof, pc->N, pc->elem_ptr,
-                                    pc->comp_of, pc->q1w, pc->cidx, r, rc, nullptr, nullptr, 0, 0.0, 0);
+  ProfScope ps(KID_RESTRICT, s);
+  const int64_t n = (int64_t)pc->n_mesh * pc->ndof;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > pc->G) blocks = pc->G;
+  k_restrict<<<blocks, 256, 0, s>>>(pc->n_mesh, mesh_of_pc(pc), pc->ndof, pc->epart, pc->cidx, rc, done);
 }
 
+// dots: 0 none, 1 PCG step (beta from the previous rz), 2 PCG start (beta = 0)
 void launch_combine(spnet_pc_s* pc, const double* r, double* z, int with_coarse, int with_stars,
-                    int with_dots, const int* done, cudaStream_t s) {
-  double* prz = with_dots ? pc->partial + 2 * pc->G : nullptr;
-  double* przo = (with_dots && pc->flexible) ? pc->partial + 3 * pc->G : nullptr;
+                    int dots, cudaStream_t s) {
   note_launch();
   ProfScope ps(KID_COMBINE, s);
-  k_combine<<<pc->G, RED_BLOCK, 0, s>>>(pc->N, mesh_of_pc(pc), pc->ndof, pc->elem_of, pc->comp_of,
-                                        pc->elem_ptr, pc->q1w, pc->cidx, pc->zc, pc->elem_star_off,
-                                        pc->star_of_mesh, pc->star_ptr, pc->w, r, z, prz, przo,
-                                        with_coarse && pc->m0 > 0, with_stars && pc->S > 0, done);
+  k_combine<<<pc->G, 256, 0, s>>>(pc->N, mesh_of_pc(pc), pc->ndof, pc->elem_of, pc->comp_of,
+                                  pc->elem_ptr, pc->q1w, pc->cidx, pc->zc, pc->elem_star_off,
+                                  pc->star_of_mesh, pc->star_ptr, pc->w, r, z, pc->partial + 2 * pc->G,
+                                  pc->partial + 3 * pc->G, with_coarse && pc->m0 > 0,
+                                  with_stars && pc->S > 0, dots ? pc->scal : nullptr, pc->flexible,
+                                  dots == 2 ? 1 : 0);
 }
 
-// z = B r (pc order), without the stop test
-static void precond(spnet_pc_s* pc, const double* r, double* z, int with_dots, const int* done,
-                    cudaStream_t s) {
-  if (pc->m0 > 0) {
-    launch_restrict(pc, r, pc->rc, done, s);
-    launch_coarse_apply(pc, pc->rc, pc->zc, done, s);
+// z = B r for a vector r already in pc order (corner sums of r computed here)
+static void precond_any(spnet_pc_s* pc, double* r, double* z, int with_coarse, int with_stars, int dots,
+                        cudaStream_t s) {
+  if (with_coarse && pc->m0 > 0) {
+    launch_update(pc, nullptr, r, nullptr, nullptr, pc->scal, 1, s);
+    launch_restrict(pc, pc->rc, nullptr, s);
+    launch_coarse_apply(pc, pc->rc, pc->zc, nullptr, s);
   }
-  launch_star_solve(pc, r, done, s);
-  launch_combine(pc, r, z, 1, 1, with_dots, done, s);
+  if (with_stars) launch_star_solve(pc, r, nullptr, s);
+  launch_combine(pc, r, z, with_coarse, with_stars, dots, s);
 }
 
-// one PCG iteration (see the file comment)
-static void iteration(spnet_pc_s* pc, double rtol, int maxit, cudaStream_t s) {
-  const int G = pc->G;
-  int* done = &pc->scal->done;
-  launch_spmv(pc->K, pc->p, pc->q, pc->partial, G, pc->spmv_lanes, done, s);
-  note_launch();
-  {
-  ProfScope ps(KID_UPDATE, s);
-  k_update_xr<<<G, RED_BLOCK, 0, s>>>(pc->N, pc->x, pc->r, pc->p, pc->q, pc->partial,
-                                      pc->partial + G, G, pc->scal);
+// one PCG iteration; the star solves go to the side stream when `side` is set
+static void iteration(spnet_pc_s* pc, cudaStream_t s, cudaStream_t side) {
+  const int* done = &pc->scal->done;
+  launch_spmv_dir(pc, s);
+  launch_update(pc, pc->x, pc->r, pc->p, pc->q, pc->scal, 0, s);
+  if (side) {
+    cudaEventRecord(pc->ev_fork, s);
+    cudaStreamWaitEvent(side, pc->ev_fork, 0);
+    launch_star_solve(pc, pc->r, done, side);
+    cudaEventRecord(pc->ev_join, side);
+  } else {
+    launch_star_solve(pc, pc->r, done, s);
   }
-  {
-    ProfScope ps(KID_RESTRICT, s);
-    int blocks = pc->m0 > 0 ? (pc->n_mesh + 7) / 8 : 1;
-    note_launch();
-    k_restrict<<<blocks, 256, 0, s>>>(pc->m0 > 0 ? pc->n_mesh : 0, mesh_of_pc(pc), pc->ndof, pc->N,
-                                      pc->elem_ptr, pc->comp_of, pc->q1w, pc->cidx, pc->r, pc->rc,
-                                      pc->scal, pc->partial + G, G, rtol, maxit);
+  launch_restrict(pc, pc->rc, done, s);
+  launch_coarse_apply(pc, pc->rc, pc->zc, done, s);
+  if (side) cudaStreamWaitEvent(s, pc->ev_join, 0);
+  launch_combine(pc, pc->r, pc->z, 1, 1, 1, s);
+}
+
+constexpr int CHUNK = 8;
+
+// the chunk of iterations as a CUDA graph (captured once per preconditioner)
+static int chunk_graph(spnet_pc_s* pc, cudaStream_t s) {
+  if (pc->graph_exec) return SPNET_OK;
+  if (!pc->side) {
+    SPNET_CUDA_TRY(cudaStreamCreateWithFlags(&pc->side, cudaStreamNonBlocking));
+    SPNET_CUDA_TRY(cudaEventCreateWithFlags(&pc->ev_fork, cudaEventDisableTiming));
+    SPNET_CUDA_TRY(cudaEventCreateWithFlags(&pc->ev_join, cudaEventDisableTiming));
   }
-  if (pc->m0 > 0) launch_coarse_apply(pc, pc->rc, pc->zc, done, s);
-  launch_star_solve(pc, pc->r, done, s);
-  launch_combine(pc, pc->r, pc->z, 1, 1, 1, done, s);
-  note_launch();
-  ProfScope ps(KID_DIRECTION, s);
-  k_direction<<<G, RED_BLOCK, 0, s>>>(pc->N, pc->z, pc->p, pc->partial + 2 * G, pc->partial + 3 * G,
-                                      G, pc->flexible, 0, pc->scal);
+  cudaGraph_t g = nullptr;
+  SPNET_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  const long long before = launch_count();
+  for (int it = 0; it < CHUNK; ++it) iteration(pc, s, pc->side);
+  pc->graph_launches = (int)(launch_count() - before);
+  add_launches(-pc->graph_launches);  // captured, not launched
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess) return fail(SPNET_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&pc->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    pc->graph_exec = nullptr;
+    return fail(SPNET_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  return SPNET_OK;
+}
+
+static int run_chunk(spnet_pc_s* pc, cudaStream_t s) {
+  if (profiling_on()) {
+    // eager launches so that every kernel can be timed with its own events
+    for (int it = 0; it < CHUNK; ++it) iteration(pc, s, nullptr);
+    return SPNET_OK;
+  }
+  SPNET_TRY(chunk_graph(pc, s));
+  add_launches(pc->graph_launches);
+  SPNET_CUDA_TRY(cudaGraphLaunch(pc->graph_exec, s));
+  return SPNET_OK;
 }
 
 void to_pc(spnet_pc_s* pc, const double* free_vec, double* pc_vec) {
@@ -377,23 +504,21 @@ int export_item(spnet_pc_s* pc, int what, void* host_buf) {
 
 int pc_apply_free(spnet_pc_s* pc, const double* r_free, double* z_free, int which) {
   cudaStream_t s = pc->op->stream;
-  const int grid = pc->G;
-  note_launch();
-  k_to_pc<<<grid, 256, 0, s>>>(pc->N, pc->perm, r_free, pc->vtmp);
-  if (which == 0) {
-    precond(pc, pc->vtmp, pc->z, 0, nullptr, s);
-  } else if (which == 1) {  // coarse term only
-    if (pc->m0 > 0) {
-      launch_restrict(pc, pc->vtmp, pc->rc, nullptr, s);
-      launch_coarse_apply(pc, pc->rc, pc->zc, nullptr, s);
-    }
-    launch_combine(pc, pc->vtmp, pc->z, 1, 0, 0, nullptr, s);
-  } else {  // star term only
-    launch_star_solve(pc, pc->vtmp, nullptr, s);
-    launch_combine(pc, pc->vtmp, pc->z, 0, 1, 0, nullptr, s);
-  }
-  note_launch();
-  k_from_pc<<<grid, 256, 0, s>>>(pc->N, pc->perm, pc->z, z_free);
+  to_pc(pc, r_free, pc->vtmp);
+  if (which == 0) precond_any(pc, pc->vtmp, pc->z, 1, 1, 0, s);
+  else if (which == 1) precond_any(pc, pc->vtmp, pc->z, 1, 0, 0, s);
+  else precond_any(pc, pc->vtmp, pc->z, 0, 1, 0, s);
+  from_pc(pc, pc->z, z_free);
+  SPNET_CUDA_TRY(cudaGetLastError());
+  return SPNET_OK;
+}
+
+int pc_restrict_free(spnet_pc_s* pc, const double* r_free, double* rc) {
+  cudaStream_t s = pc->op->stream;
+  to_pc(pc, r_free, pc->vtmp);
+  if (pc->m0 == 0) return SPNET_OK;
+  launch_update(pc, nullptr, pc->vtmp, nullptr, nullptr, pc->scal, 1, s);
+  launch_restrict(pc, rc, nullptr, s);
   SPNET_CUDA_TRY(cudaGetLastError());
   return SPNET_OK;
 }
@@ -427,20 +552,21 @@ int pcg_run(spnet_op_s* op, spnet_pc_s* pc, int nrhs, const double* f, const dou
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int worst = SPNET_OK;
-  const int chunk = 8;
+  unsigned* cnt3 = &pc->scal->cnt[3];
   for (int k = 0; k < nrhs; ++k) {
     const double* fk = df + (int64_t)k * nd;
     const double* gk = dg + (int64_t)k * ndir;
     double* xk = dx + (int64_t)k * nd;
     cudaEventRecord(e0, s);
-    SPNET_CUDA_TRY(cudaMemsetAsync(pc->scal, 0, sizeof(Scal), s));
+    Scal init{};
+    init.rtol = rtol;
+    init.maxit = maxit;
+    SPNET_CUDA_TRY(cudaMemcpyAsync(pc->scal, &init, sizeof(Scal), cudaMemcpyHostToDevice, s));
     note_launch();
     k_build_rhs<<<G, 256, 0, s>>>(N, pc->perm, op->free_dofs, fk, op->fd.ptr, op->fd.col, op->fd.val,
                                   gk, pc->b);
     note_launch();
-    k_dot_partial<<<G, RED_BLOCK, 0, s>>>(N, pc->b, pc->b, pc->partial);
-    note_launch();
-    k_reduce_to<<<1, 32, 0, s>>>(pc->partial, G, &pc->scal->bb);
+    k_residual<<<G, 256, 0, s>>>(N, pc->b, nullptr, nullptr, pc->partial, &pc->scal->bb, cnt3);
     if (use_x0) {
       note_launch();
       k_x0_from_dofs<<<G, 256, 0, s>>>(N, pc->perm, op->free_dofs, xk, pc->x);
@@ -452,22 +578,17 @@ int pcg_run(spnet_op_s* op, spnet_pc_s* pc, int nrhs, const double* f, const dou
     int restarts = 0;
     Scal h{};
     for (;;) {
-      // (re)start: r = b - A x, z = B r, p = z
+      // (re)start: r = b - A x, z = B r, beta = 0
       note_launch();
-      k_residual<<<G, RED_BLOCK, 0, s>>>(N, pc->b, pc->q, pc->r, pc->partial + G);
-      note_launch();
-      k_reduce_to<<<1, 32, 0, s>>>(pc->partial + G, G, &pc->scal->rr);
+      k_residual<<<G, 256, 0, s>>>(N, pc->b, pc->q, pc->r, pc->partial, &pc->scal->rr, cnt3);
       SPNET_CUDA_TRY(cudaMemcpyAsync(&h, pc->scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
       SPNET_CUDA_TRY(cudaStreamSynchronize(s));
       const double tol = rtol * sqrt(h.bb);
       if (h.bb == 0.0) break;
       if (sqrt(h.rr) > tol && h.iter < maxit) {
-        precond(pc, pc->r, pc->z, 1, nullptr, s);
-        note_launch();
-        k_direction<<<G, RED_BLOCK, 0, s>>>(N, pc->z, pc->p, pc->partial + 2 * G, pc->partial + 3 * G,
-                                            G, pc->flexible, 1, pc->scal);
+        precond_any(pc, pc->r, pc->z, 1, 1, 2, s);  // z = B r, rz = (r, z), beta = 0
         for (;;) {
-          for (int it = 0; it < chunk; ++it) iteration(pc, rtol, maxit, s);
+          SPNET_TRY(run_chunk(pc, s));
           SPNET_CUDA_TRY(cudaMemcpyAsync(&h, pc->scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
           SPNET_CUDA_TRY(cudaStreamSynchronize(s));
           if (h.done) break;
@@ -476,9 +597,7 @@ int pcg_run(spnet_op_s* op, spnet_pc_s* pc, int nrhs, const double* f, const dou
       // recompute the residual in FP64
       launch_spmv(pc->K, pc->x, pc->q, nullptr, G, pc->spmv_lanes, nullptr, s);
       note_launch();
-      k_residual<<<G, RED_BLOCK, 0, s>>>(N, pc->b, pc->q, pc->vtmp, pc->partial + 4 * G);
-      note_launch();
-      k_reduce_to<<<1, 32, 0, s>>>(pc->partial + 4 * G, G, &pc->scal->rr_true);
+      k_residual<<<G, 256, 0, s>>>(N, pc->b, pc->q, pc->vtmp, pc->partial, &pc->scal->rr_true, cnt3);
       SPNET_CUDA_TRY(cudaMemcpyAsync(&h, pc->scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
       SPNET_CUDA_TRY(cudaStreamSynchronize(s));
       const double rel = sqrt(h.rr_true) / sqrt(h.bb);
@@ -486,6 +605,7 @@ int pcg_run(spnet_op_s* op, spnet_pc_s* pc, int nrhs, const double* f, const dou
       ++restarts;
       int zero = 0;
       SPNET_CUDA_TRY(cudaMemcpyAsync(&pc->scal->done, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+      SPNET_CUDA_TRY(cudaStreamSynchronize(s));
     }
     if (h.bb == 0.0) SPNET_CUDA_TRY(cudaMemsetAsync(pc->x, 0, sizeof(double) * N, s));
     note_launch();

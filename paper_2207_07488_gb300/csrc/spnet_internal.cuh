@@ -78,10 +78,12 @@ struct Csr {
   double* val = nullptr;
 };
 
+// PCG scalars on the device; each field has one writer per kernel (the last
+// block of the kernel that finishes its reduction)
 struct Scal {
-  double rz, rz_old, pq, rr, bb, alpha, beta, rz_flex;
-  double rr_true;
-  int iter, done, restarts, pad;
+  double rz, pq, rr, bb, alpha, beta, rr_true, rtol;
+  int maxit, iter, done, restarts;
+  unsigned cnt[4];  // arrival counters of the last-block reductions
 };
 
 }  // namespace spnet
@@ -91,6 +93,7 @@ struct spnet_op_s {
   int64_t n_nodes = 0, n_dof = 0, n_free = 0, n_dir = 0;
   double domain[3] = {1, 1, 1};
   cudaStream_t stream = 0;
+  bool own_stream = false;      // created by the library (the caller passed stream 0)
   spnet::DevArena mem;
   double* coords = nullptr;     // [n_nodes*dim]
   int64_t* dir_dofs = nullptr;  // [n_dir]
@@ -138,11 +141,17 @@ struct spnet_pc_s {
   int32_t* star_n = nullptr;       // [S]
   int32_t* star_lev = nullptr;     // [S]
   int32_t* star_nnz = nullptr;     // [S]
+  int solve_spw = 0;               // shared-memory bytes per warp of the star solve
   // work vectors (pc order)
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *b = nullptr;
   double *w = nullptr, *rc = nullptr, *zc = nullptr, *partial = nullptr, *vtmp = nullptr;
   void* ybuf = nullptr;
+  double* epart = nullptr;         // [n_elem*nc*ndof] Q1-weighted corner sums of r
   spnet::Scal* scal = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;  // a chunk of PCG iterations
+  cudaStream_t side = nullptr;     // second stream of the graph (star solves)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int graph_launches = 0;
   int G = 0;         // reduction grid
   int spmv_lanes = 1;
   double setup_ms = 0;
@@ -213,7 +222,9 @@ enum KernelId {
   KID_STAR_SYMBOLIC, KID_STAR_NUMERIC, KID_SWEEP, KID_GALERKIN, KID_COUNT
 };
 void note_launch();
+void add_launches(long long n);
 long long launch_count();
+bool profiling_on();
 struct ProfScope {
   int id;
   cudaStream_t s;
@@ -253,9 +264,10 @@ void launch_coarse_apply(spnet_pc_s* pc, const double* rc, double* zc, const int
                          cudaStream_t s);
 
 // pcg.cu
-void launch_restrict(spnet_pc_s* pc, const double* r, double* rc, const int* done, cudaStream_t s);
+void launch_restrict(spnet_pc_s* pc, double* rc, const int* done, cudaStream_t s);
 void launch_combine(spnet_pc_s* pc, const double* r, double* z, int with_coarse, int with_stars,
-                    int with_dots, const int* done, cudaStream_t s);
+                    int dots, cudaStream_t s);
+int pc_restrict_free(spnet_pc_s* pc, const double* r_free, double* rc);
 int pc_apply_free(spnet_pc_s* pc, const double* r_free_dev, double* z_free_dev, int which);
 void to_pc(spnet_pc_s* pc, const double* free_vec, double* pc_vec);
 void from_pc(spnet_pc_s* pc, const double* pc_vec, double* free_vec);

@@ -28,30 +28,37 @@ constexpr int SWITCH_DEG = 24;   // minimum degree above which the rest is dense
 constexpr int CORE_MAX = 256;    // largest dense block handled
 constexpr int CORE_ENTRIES = CORE_MAX * (CORE_MAX - 1) / 2;
 
+// A star's blob: a compact "solve section" (all the triangular solves read)
+// followed by a set-up section.  Values of the solve section are FP64 or FP32
+// (vbytes); the set-up section holds the column->row entry map and, for FP32
+// solves, the FP64 factor computed first.
 struct BlobLayout {
-  int64_t gidx, perm, lvl, colptr, colidx, rowptr, rowidx, c2r, v64, v32, total;
+  int64_t gidx, rowptr, colptr, lvl, perm, rowidx, colidx, rowval, colval, invd, solve;
+  int64_t c2r, v64, total;
 };
 
 __host__ __device__ inline int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline BlobLayout blob_layout(int n, int nlev, int nnz) {
+__host__ __device__ inline BlobLayout blob_layout(int n, int nlev, int nnz, int vbytes) {
   BlobLayout L;
   int64_t o = 16;  // header: n, nlev, nnz, 0
-  L.gidx = o;  o += 4ll * n;
-  L.perm = o;  o += 2ll * n;
-  L.lvl = o;   o += 2ll * (nlev + 1);
-  o = align_up(o, 4);
-  L.colptr = o; o += 4ll * (n + 1);
-  L.colidx = o; o += 2ll * nnz;
-  o = align_up(o, 4);
+  L.gidx = o;   o += 4ll * n;
   L.rowptr = o; o += 4ll * (n + 1);
+  L.colptr = o; o += 4ll * (n + 1);
+  L.lvl = o;    o += 2ll * (nlev + 1);
+  L.perm = o;   o += 2ll * n;
   L.rowidx = o; o += 2ll * nnz;
-  o = align_up(o, 4);
-  L.c2r = o;   o += 4ll * nnz;
+  L.colidx = o; o += 2ll * nnz;
   o = align_up(o, 8);
-  L.v64 = o;   o += 8ll * (2ll * nnz + n);   // col values, row values, 1/L_vv
-  o = align_up(o, 4);
-  L.v32 = o;   o += 4ll * (2ll * nnz + n);
+  L.rowval = o; o += (int64_t)vbytes * nnz;
+  L.colval = o; o += (int64_t)vbytes * nnz;
+  L.invd = o;   o += (int64_t)vbytes * n;
+  L.solve = align_up(o, 16);
+  o = L.solve;
+  L.c2r = o;    o += 4ll * nnz;
+  o = align_up(o, 8);
+  L.v64 = vbytes == 8 ? L.rowval : o;       // FP64 row values, col values, 1/L_vv
+  if (vbytes != 8) o += 8ll * (2ll * nnz + n);
   L.total = align_up(o, 16);
   return L;
 }
@@ -77,6 +84,7 @@ struct StarArgs {
   int32_t* star_nnz;
   int* flags;
   int* next;
+  int vbytes;
 };
 
 struct Scratch {
@@ -374,7 +382,7 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
     for (int t = lane; t < n; t += 32) W.rcnt[t] = 0;
     __syncwarp();
     // place the blob
-    const BlobLayout L = blob_layout(n, nlev, ncol);
+    const BlobLayout L = blob_layout(n, nlev, ncol, A.vbytes);
     unsigned long long off = 0;
     if (lane == 0) off = atomicAdd(A.pool_top, (unsigned long long)L.total);
     off = __shfl_sync(FULL, off, 0);
@@ -440,18 +448,16 @@ __device__ inline double k_entry(const int64_t* kptr, const int32_t* kcol, const
   return 0.0;
 }
 
-__global__ void __launch_bounds__(128) k_star_numeric(int S, const char* __restrict__ pool0,
-                                                      char* pool, const int64_t* star_off,
+__global__ void __launch_bounds__(128) k_star_numeric(int S, char* pool, const int64_t* star_off,
                                                       const int64_t* kptr, const int32_t* kcol,
-                                                      const double* kval, int* flags) {
+                                                      const double* kval, int vbytes, int* flags) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  (void)pool0;
   for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
     char* blob = pool + star_off[s];
     const int32_t* hdr = (const int32_t*)blob;
     const int n = hdr[0], nlev = hdr[1], nnz = hdr[2];
-    const BlobLayout L = blob_layout(n, nlev, nnz);
+    const BlobLayout L = blob_layout(n, nlev, nnz, vbytes);
     const int32_t* gidx = (const int32_t*)(blob + L.gidx);
     const uint16_t* lvl = (const uint16_t*)(blob + L.lvl);
     const uint32_t* colptr = (const uint32_t*)(blob + L.colptr);
@@ -459,9 +465,9 @@ __global__ void __launch_bounds__(128) k_star_numeric(int S, const char* __restr
     const uint32_t* rowptr = (const uint32_t*)(blob + L.rowptr);
     const uint16_t* rowidx = (const uint16_t*)(blob + L.rowidx);
     const int32_t* c2r = (const int32_t*)(blob + L.c2r);
-    double* colv = (double*)(blob + L.v64);
-    double* rowv = colv + nnz;
-    double* invd = rowv + nnz;
+    double* rowv = (double*)(blob + L.v64);
+    double* colv = rowv + nnz;
+    double* invd = colv + nnz;
     bool bad = false;
     for (int l = 0; l < nlev; ++l) {
       for (int v = lvl[l] + lane; v < (int)lvl[l + 1]; v += 32) {
@@ -500,9 +506,22 @@ __global__ void __launch_bounds__(128) k_star_numeric(int S, const char* __restr
       __syncwarp();
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, FLAG_NOT_SPD);
-    float* c32 = (float*)(blob + L.v32);
-    for (int q = lane; q < 2 * nnz + n; q += 32) c32[q] = (float)colv[q];
+    if (vbytes == 4) {
+      float* r32 = (float*)(blob + L.rowval);
+      for (int q = lane; q < 2 * nnz + n; q += 32) r32[q] = (float)rowv[q];
+    }
   }
+}
+
+__global__ void k_solve_need(int S, const char* pool, const int64_t* star_off, int vbytes, int* mx) {
+  int m = 0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
+    const int32_t* hdr = (const int32_t*)(pool + star_off[s]);
+    const BlobLayout L = blob_layout(hdr[0], hdr[1], hdr[2], vbytes);
+    int need = (int)(L.solve + align_up((int64_t)vbytes * hdr[0], 16));
+    m = max(m, need);
+  }
+  atomicMax(mx, m);
 }
 
 // ---------------------------------------------------------------------------
@@ -510,31 +529,47 @@ __global__ void __launch_bounds__(128) k_star_numeric(int S, const char* __restr
 // w_j in the star's element-concatenated order
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(256) k_star_solve(int S, const char* __restrict__ pool,
+__global__ void __launch_bounds__(128) k_star_solve(int S, const char* __restrict__ pool,
                                                     const int64_t* __restrict__ star_off,
                                                     const int64_t* __restrict__ star_ptr,
                                                     const double* __restrict__ r, T* ybuf,
-                                                    double* __restrict__ w, const int* done) {
+                                                    double* __restrict__ w, int spw, const int* done) {
+  extern __shared__ __align__(16) char smem[];
   if (done && *done) return;
   const int lane = threadIdx.x & 31;
+  char* mine = smem + (threadIdx.x >> 5) * spw;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
     const char* blob = pool + star_off[s];
-    const int32_t* hdr = (const int32_t*)blob;
-    const int n = hdr[0], nlev = hdr[1], nnz = hdr[2];
-    const BlobLayout L = blob_layout(n, nlev, nnz);
-    const int32_t* gidx = (const int32_t*)(blob + L.gidx);
-    const uint16_t* perm = (const uint16_t*)(blob + L.perm);
-    const uint16_t* lvl = (const uint16_t*)(blob + L.lvl);
-    const uint32_t* colptr = (const uint32_t*)(blob + L.colptr);
-    const uint16_t* colidx = (const uint16_t*)(blob + L.colidx);
-    const uint32_t* rowptr = (const uint32_t*)(blob + L.rowptr);
-    const uint16_t* rowidx = (const uint16_t*)(blob + L.rowidx);
-    const T* colv = (const T*)(blob + (sizeof(T) == 8 ? L.v64 : L.v32));
-    const T* rowv = colv + nnz;
-    const T* invd = rowv + nnz;
+    const int4 h = *(const int4*)blob;
+    const int n = h.x, nlev = h.y, nnz = h.z;
+    const BlobLayout L = blob_layout(n, nlev, nnz, (int)sizeof(T));
     const int64_t base = star_ptr[s];
-    T* y = ybuf + base;
+    const char* src;
+    T* y;
+    if (L.solve + align_up((int64_t)sizeof(T) * n, 16) <= spw) {
+      // stage the solve section in shared memory (16-byte vector copies)
+      const int4* g4 = (const int4*)blob;
+      int4* s4 = (int4*)mine;
+      const int n4 = (int)(L.solve >> 4);
+      for (int q = lane; q < n4; q += 32) s4[q] = __ldg(&g4[q]);
+      src = mine;
+      y = (T*)(mine + L.solve);
+      __syncwarp();
+    } else {
+      src = blob;
+      y = ybuf + base;
+    }
+    const int32_t* gidx = (const int32_t*)(src + L.gidx);
+    const uint16_t* perm = (const uint16_t*)(src + L.perm);
+    const uint16_t* lvl = (const uint16_t*)(src + L.lvl);
+    const uint32_t* colptr = (const uint32_t*)(src + L.colptr);
+    const uint16_t* colidx = (const uint16_t*)(src + L.colidx);
+    const uint32_t* rowptr = (const uint32_t*)(src + L.rowptr);
+    const uint16_t* rowidx = (const uint16_t*)(src + L.rowidx);
+    const T* rowv = (const T*)(src + L.rowval);
+    const T* colv = (const T*)(src + L.colval);
+    const T* invd = (const T*)(src + L.invd);
     for (int pos = lane; pos < n; pos += 32) y[pos] = (T)r[gidx[pos]];
     __syncwarp();
     for (int l = 0; l < nlev; ++l) {
@@ -560,16 +595,17 @@ __global__ void __launch_bounds__(256) k_star_solve(int S, const char* __restric
 
 void launch_star_solve(spnet_pc_s* pc, const double* r, const int* done, cudaStream_t s) {
   if (pc->S == 0) return;
-  const int warps_per_block = 8;
-  int blocks = (pc->S + warps_per_block - 1) / warps_per_block;
+  const int wpb = 4;
+  const int spw = pc->solve_spw;
+  int blocks = (pc->S + wpb - 1) / wpb;
   note_launch();
   ProfScope ps(KID_STARS, s);
   if (pc->precision == SPNET_PREC_FP64)
-    k_star_solve<double><<<blocks, 32 * warps_per_block, 0, s>>>(
-        pc->S, pc->pool, pc->star_off, pc->star_ptr, r, (double*)pc->ybuf, pc->w, done);
+    k_star_solve<double><<<blocks, 32 * wpb, (size_t)spw * wpb, s>>>(
+        pc->S, pc->pool, pc->star_off, pc->star_ptr, r, (double*)pc->ybuf, pc->w, spw, done);
   else
-    k_star_solve<float><<<blocks, 32 * warps_per_block, 0, s>>>(
-        pc->S, pc->pool, pc->star_off, pc->star_ptr, r, (float*)pc->ybuf, pc->w, done);
+    k_star_solve<float><<<blocks, 32 * wpb, (size_t)spw * wpb, s>>>(
+        pc->S, pc->pool, pc->star_off, pc->star_ptr, r, (float*)pc->ybuf, pc->w, spw, done);
 }
 
 int pc_factor_stars(spnet_pc_s* pc) {
@@ -630,6 +666,7 @@ int pc_factor_stars(spnet_pc_s* pc) {
     A.star_nnz = pc->star_nnz;
     A.flags = flags;
     A.next = counters;
+    A.vbytes = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
     note_launch();
     ProfScope ps(KID_STAR_SYMBOLIC, s);
     k_star_symbolic<<<(unsigned)(warps / 4), 128, 0, s>>>(A);
@@ -653,8 +690,9 @@ int pc_factor_stars(spnet_pc_s* pc) {
   int blocks = (pc->S + 3) / 4;
   note_launch();
   ProfScope ps(KID_STAR_NUMERIC, s);
-  k_star_numeric<<<blocks, 128, 0, s>>>(pc->S, pc->pool, pc->pool, pc->star_off, pc->K.ptr,
-                                         pc->K.col, pc->K.val, flags);
+  const int vbytes = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
+  k_star_numeric<<<blocks, 128, 0, s>>>(pc->S, pc->pool, pc->star_off, pc->K.ptr, pc->K.col,
+                                         pc->K.val, vbytes, flags);
   SPNET_CUDA_TRY(cudaGetLastError());
   SPNET_TRY(check_flags(flags, s, "setup_preconditioner (star factorisation)"));
   // statistics
@@ -670,8 +708,35 @@ int pc_factor_stars(spnet_pc_s* pc) {
     pc->total_levels += lev[i];
     pc->max_levels = lev[i] > pc->max_levels ? lev[i] : pc->max_levels;
   }
-  // local solve buffers
-  SPNET_TRY(pc->mem.alloc(&pc->ybuf, (size_t)pc->sum_s * (pc->precision == SPNET_PREC_FP64 ? 8 : 4)));
+  // local solve buffers (used by stars that do not fit the shared-memory stage)
+  SPNET_TRY(pc->mem.alloc(&pc->ybuf, (size_t)pc->sum_s * vbytes));
+  // shared memory per warp: the largest star's solve section and vector, capped
+  {
+    int* mx = counters;
+    SPNET_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(int), s));
+    note_launch();
+    k_solve_need<<<(pc->S + 255) / 256, 256, 0, s>>>(pc->S, pc->pool, pc->star_off, vbytes, mx);
+    int need = 0;
+    SPNET_CUDA_TRY(cudaMemcpyAsync(&need, mx, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+    const int cap = 48 * 1024;
+    pc->solve_spw = (int)align_up(need < cap ? need : cap, 16);
+    // the kernel attribute is process-wide: allow the largest stage any
+    // preconditioner may ask for (4 warps x cap)
+    static bool attr_set[64][2] = {};
+    int dev = 0;
+    SPNET_CUDA_TRY(cudaGetDevice(&dev));
+    dev &= 63;
+    const int bytes = 4 * cap;
+    if (vbytes == 8 && !attr_set[dev][1]) {
+      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+      attr_set[dev][1] = true;
+    }
+    if (vbytes == 4 && !attr_set[dev][0]) {
+      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+      attr_set[dev][0] = true;
+    }
+  }
   return SPNET_OK;
 }
 

@@ -77,6 +77,8 @@ static long long g_prof_n[KID_COUNT];
 static double g_prof_ms[KID_COUNT];
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+bool profiling_on() { return g_prof_on.load(std::memory_order_relaxed) != 0; }
 long long launch_count() { return g_launches.load(); }
 
 ProfScope::ProfScope(int id_, cudaStream_t s_) : id(id_), s(s_) {

@@ -218,6 +218,9 @@ class Operator:
         vl, m4, k4 = _arg(val, np.float64)
         dd, m5, k5 = _arg(dirichlet_dofs, np.int64)
         mem = _same_mem(m1, m2, m3, m4, m5)
+        if mem == MEM_DEVICE:
+            import torch
+            torch.cuda.current_stream(k1.device).synchronize()
         dom = np.ascontiguousarray(domain, dtype=np.float64)
         n_nodes = int(np.asarray(coords.shape)[0])
         nd = 0 if dirichlet_dofs is None else int(len(dirichlet_dofs))
@@ -253,6 +256,7 @@ class Operator:
         if mem == MEM_DEVICE:
             import torch
             y = torch.empty_like(keep)
+            torch.cuda.current_stream(keep.device).synchronize()
             _check(self._lib.spnet_spmv(self.handle, xp, C.c_void_p(y.data_ptr()), mem))
             return y
         y = np.zeros(self.info.n_free)
@@ -296,6 +300,7 @@ class Preconditioner:
         if mem == MEM_DEVICE:
             import torch
             out = torch.zeros(max(n_out, 1), dtype=torch.float64, device=keep.device)[:n_out]
+            torch.cuda.current_stream(keep.device).synchronize()
             _check(fn(self.handle, vp, C.c_void_p(out.data_ptr()), mem))
             return out
         out = np.zeros(n_out)
@@ -365,6 +370,9 @@ def pcg_solve(op: Operator, pc: Preconditioner, f, g, x0=None, rtol=1e-8, maxit=
             x = x0.to(torch.float64).clone().contiguous()
         else:
             x = torch.zeros(tuple(f.shape), dtype=torch.float64, device=kf.device)
+        # torch filled x and may have produced f, g on its current stream; the
+        # library works on the operator's stream
+        torch.cuda.current_stream(kf.device).synchronize()
         xp = C.c_void_p(x.data_ptr())
     else:
         x = np.zeros(tuple(f.shape)) if x0 is None else np.array(x0, dtype=np.float64)
