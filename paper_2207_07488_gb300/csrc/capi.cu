@@ -86,6 +86,7 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
     if ((rc = pc->mem.alloc((void**)&A0, bytes))) return bail(rc);
     if ((rc = pc_galerkin(pc, A0))) return bail(rc);
     if ((rc = pc_coarse_invert(pc, A0))) return bail(rc);
+    if ((rc = coarse_gemv_prepare(pc))) return bail(rc);
     if (pc->m0 <= A0_KEEP) pc->A0 = A0;
     else pc->mem.release(A0);
   }

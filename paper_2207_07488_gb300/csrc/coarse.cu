@@ -19,12 +19,12 @@ constexpr int NB = 32;
 
 // invert the SPD pivot block D = Z[k0.., k0..] (kb x kb) into P (FP64 arithmetic)
 template <class T>
-__global__ void k_pivot_inverse(T* Z, int64_t m0, int k0, int kb, double* P, int* flags) {
+__global__ void k_pivot_inverse(T* Z, int64_t ld, int k0, int kb, double* P, int* flags) {
   __shared__ double D[NB][NB + 1];
   __shared__ double col[NB], row[NB];
   __shared__ double ipiv;
   const int i = threadIdx.y, j = threadIdx.x;
-  if (i < kb && j < kb) D[i][j] = (double)Z[(int64_t)(k0 + i) * m0 + (k0 + j)];
+  if (i < kb && j < kb) D[i][j] = (double)Z[(int64_t)(k0 + i) * ld + (k0 + j)];
   __syncthreads();
   for (int p = 0; p < kb; ++p) {
     if (i == 0 && j == 0) {
@@ -52,8 +52,8 @@ __global__ void k_pivot_inverse(T* Z, int64_t m0, int k0, int kb, double* P, int
 
 // R = Z[k0:k0+kb, :] (copy of the pivot rows), Tm = P R
 template <class T>
-__global__ void __launch_bounds__(256) k_panel(const T* Z, int64_t m0, int k0, int kb, const double* P,
-                                               T* R, T* Tm) {
+__global__ void __launch_bounds__(256) k_panel(const T* Z, int64_t m0, int64_t ld, int k0, int kb,
+                                               const double* P, T* R, T* Tm) {
   __shared__ T sP[NB][NB];
   for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
     const int t = q / NB, u = q % NB;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) k_panel(const T* Z, int64_t m0, int k0, i
        c += (int64_t)gridDim.x * blockDim.x) {
     T col[NB];
 #pragma unroll
-    for (int t = 0; t < NB; ++t) col[t] = t < kb ? Z[(int64_t)(k0 + t) * m0 + c] : (T)0;
+    for (int t = 0; t < NB; ++t) col[t] = t < kb ? Z[(int64_t)(k0 + t) * ld + c] : (T)0;
 #pragma unroll
     for (int t = 0; t < NB; ++t)
       if (t < kb) R[(int64_t)t * m0 + c] = col[t];
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_panel(const T* Z, int64_t m0, int k0, i
 // tiles on or above the block diagonal are computed, each writes itself and its
 // mirror image (the swept matrix stays symmetric)
 template <class T, int TB>
-__global__ void __launch_bounds__(256) k_sweep(T* Z, int64_t m0, int k0, int kb, const double* P,
+__global__ void __launch_bounds__(256) k_sweep(T* Z, int64_t m0, int64_t ld, int k0, int kb, const double* P,
                                                const T* __restrict__ R, const T* __restrict__ Tm) {
   constexpr int RT = TB / 16;  // register tile
   extern __shared__ __align__(16) char sm_raw[];
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_sweep(T* Z, int64_t m0, int k0, int kb,
       T v = 0;
       if (i < m0 && j < m0) {
         const bool jK = j >= k0 && j < k0 + kb;
-        if (!iK && !jK) v = Z[i * m0 + j] - acc[a][b];
+        if (!iK && !jK) v = Z[i * ld + j] - acc[a][b];
         else if (iK && jK) v = (T)(-P[(i - k0) * NB + (j - k0)]);
         else if (iK) v = sT[i - k0][lj];
         else v = Tm[(j - k0) * m0 + i];  // A_iK P = (P A_Ki)^T by symmetry
@@ -146,22 +146,24 @@ __global__ void __launch_bounds__(256) k_sweep(T* Z, int64_t m0, int k0, int kb,
   for (int q = threadIdx.x; q < TB * TB; q += 256) {
     const int li = q / TB, lj = q % TB;
     const int64_t i = i0 + li, j = j0 + lj;
-    if (i < m0 && j < m0) Z[i * m0 + j] = sO[li][lj];
+    if (i < m0 && j < m0) Z[i * ld + j] = sO[li][lj];
   }
   if (bi != bj) {
     for (int q = threadIdx.x; q < TB * TB; q += 256) {
       const int lj = q / TB, li = q % TB;  // write the mirror tile row by row
       const int64_t i = i0 + li, j = j0 + lj;
-      if (i < m0 && j < m0) Z[j * m0 + i] = sO[li][lj];
+      if (i < m0 && j < m0) Z[j * ld + i] = sO[li][lj];
     }
   }
 }
 
+// mode 0: Z = A0 (rows padded to ld with zeros); mode 1: Z = -Z
 template <class T>
-__global__ void k_negate_from(const double* A0, T* Z, int64_t n, int mode) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+__global__ void k_negate_from(const double* A0, T* Z, int64_t m0, int64_t ld, int mode) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m0 * ld;
        q += (int64_t)gridDim.x * blockDim.x) {
-    if (mode == 0) Z[q] = (T)A0[q];
+    const int64_t i = q / ld, j = q % ld;
+    if (mode == 0) Z[q] = j < m0 ? (T)A0[i * m0 + j] : (T)0;
     else Z[q] = -Z[q];
   }
 }
@@ -176,9 +178,12 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
     DevArena& a;
     ~Guard() { a.free_all(); }
   } guard{tmp};
+  // rows padded to 16 bytes so that the coarse product can load them as vectors
+  const int64_t ld = (m0 + (16 / (int64_t)sizeof(T)) - 1) / (16 / (int64_t)sizeof(T)) * (16 / (int64_t)sizeof(T));
   T* Z = nullptr;
-  SPNET_TRY(pc->mem.get(&Z, m0 * m0));
+  SPNET_TRY(pc->mem.get(&Z, m0 * ld));
   pc->Z = Z;
+  pc->ldz = ld;
   double* P = nullptr;
   T *R = nullptr, *Tm = nullptr;
   SPNET_TRY(tmp.get(&P, NB * NB));
@@ -186,7 +191,7 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
   SPNET_TRY(tmp.get(&Tm, NB * m0));
   const int grid = 4 * num_sms();
   note_launch();
-  k_negate_from<T><<<grid, 256, 0, s>>>(A0, Z, m0 * m0, 0);
+  k_negate_from<T><<<grid, 256, 0, s>>>(A0, Z, m0, ld, 0);
   SPNET_CUDA_TRY(cudaMemsetAsync(pc->op->dflags, 0, sizeof(int), s));
   constexpr int TB = sizeof(T) == 4 ? 128 : 64;
   const int nt = (int)((m0 + TB - 1) / TB);
@@ -203,15 +208,15 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
   for (int k0 = 0; k0 < m0; k0 += NB) {
     const int kb = (int)((m0 - k0) < NB ? (m0 - k0) : NB);
     note_launch();
-    k_pivot_inverse<T><<<1, dim3(NB, NB), 0, s>>>(Z, m0, k0, kb, P, pc->op->dflags);
+    k_pivot_inverse<T><<<1, dim3(NB, NB), 0, s>>>(Z, ld, k0, kb, P, pc->op->dflags);
     note_launch();
-    k_panel<T><<<(unsigned)((m0 + 255) / 256), 256, 0, s>>>(Z, m0, k0, kb, P, R, Tm);
+    k_panel<T><<<(unsigned)((m0 + 255) / 256), 256, 0, s>>>(Z, m0, ld, k0, kb, P, R, Tm);
     note_launch();
     ProfScope ps(KID_SWEEP, s);
-    k_sweep<T, TB><<<tiles, 256, smem, s>>>(Z, m0, k0, kb, P, R, Tm);
+    k_sweep<T, TB><<<tiles, 256, smem, s>>>(Z, m0, ld, k0, kb, P, R, Tm);
   }
   note_launch();
-  k_negate_from<T><<<grid, 256, 0, s>>>(A0, Z, m0 * m0, 1);
+  k_negate_from<T><<<grid, 256, 0, s>>>(A0, Z, m0, ld, 1);
   SPNET_CUDA_TRY(cudaGetLastError());
   return check_flags(pc->op->dflags, s, "setup_preconditioner (coarse matrix)");
 }
@@ -222,18 +227,29 @@ int pc_coarse_invert(spnet_pc_s* pc, double* A0) {
   return invert_impl<float>(pc, A0);
 }
 
-// z_c = Z r_c: one warp per row
-template <class T>
-__global__ void __launch_bounds__(256) k_coarse_gemv(const T* __restrict__ Z, int64_t m0,
+// z_c = Z r_c: r_c staged in shared memory, one warp per row, 16-byte loads of Z
+template <class T, class V>
+__global__ void __launch_bounds__(256) k_coarse_gemv(const T* __restrict__ Z, int64_t m0, int64_t ld,
                                                      const double* __restrict__ rc,
                                                      double* __restrict__ zc, const int* done) {
+  extern __shared__ __align__(16) char sm_raw[];
+  T* srv = reinterpret_cast<T*>(sm_raw);
   if (done && *done) return;
+  for (int64_t c = threadIdx.x; c < ld; c += blockDim.x) srv[c] = c < m0 ? (T)rc[c] : (T)0;
+  __syncthreads();
+  constexpr int VW = sizeof(V) / sizeof(T);
   const int lane = threadIdx.x & 31;
+  const int64_t nv = ld / VW;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < m0; row += nw) {
-    const T* zr = Z + row * m0;
+    const V* zr = reinterpret_cast<const V*>(Z + row * ld);
     T acc = 0;
-    for (int64_t c = lane; c < m0; c += 32) acc += zr[c] * (T)__ldg(&rc[c]);
+    for (int64_t c = lane; c < nv; c += 32) {
+      const V z = __ldg(&zr[c]);
+      const T* zz = reinterpret_cast<const T*>(&z);
+#pragma unroll
+      for (int u = 0; u < VW; ++u) acc += zz[u] * srv[c * VW + u];
+    }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) zc[row] = (double)acc;
   }
@@ -242,14 +258,32 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(const T* __restrict__ Z, in
 void launch_coarse_apply(spnet_pc_s* pc, const double* rc, double* zc, const int* done,
                          cudaStream_t s) {
   if (pc->m0 == 0) return;
-  int blocks = (int)((pc->m0 + 7) / 8);
-  if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
+  int blocks = 2 * num_sms();
+  const int64_t rows_blocks = (pc->m0 + 7) / 8;
+  if (blocks > rows_blocks) blocks = (int)rows_blocks;
+  const size_t vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
+  const size_t smem = vb * (size_t)pc->ldz;
   note_launch();
   ProfScope ps(KID_COARSE, s);
   if (pc->precision == SPNET_PREC_FP64)
-    k_coarse_gemv<double><<<blocks, 256, 0, s>>>((const double*)pc->Z, pc->m0, rc, zc, done);
+    k_coarse_gemv<double, double2><<<blocks, 256, smem, s>>>((const double*)pc->Z, pc->m0, pc->ldz, rc, zc, done);
   else
-    k_coarse_gemv<float><<<blocks, 256, 0, s>>>((const float*)pc->Z, pc->m0, rc, zc, done);
+    k_coarse_gemv<float, float4><<<blocks, 256, smem, s>>>((const float*)pc->Z, pc->m0, pc->ldz, rc, zc, done);
+}
+
+int coarse_gemv_prepare(spnet_pc_s* pc) {
+  if (pc->m0 == 0) return SPNET_OK;
+  const size_t vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
+  const size_t smem = vb * (size_t)pc->ldz;
+  if (smem > 220 * 1024)
+    return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: coarse space too large for the staged product");
+  if (smem > 48 * 1024) {
+    if (pc->precision == SPNET_PREC_FP64)
+      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    else
+      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv<float, float4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  return SPNET_OK;
 }
 
 }  // namespace spnet

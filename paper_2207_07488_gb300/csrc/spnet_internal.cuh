@@ -126,7 +126,8 @@ struct spnet_pc_s {
   // coarse space
   int m0 = 0;
   int32_t* cidx = nullptr;     // [n_mesh*ndof]
-  void* Z = nullptr;           // [m0*m0] A_0^{-1} (float or double by precision)
+  void* Z = nullptr;           // [m0*ldz] A_0^{-1} (float or double by precision), rows padded
+  int64_t ldz = 0;
   double* A0 = nullptr;        // [m0*m0] copy of A_0 if m0 <= A0_KEEP
   // stars
   int S = 0, max_star = 0, max_levels = 0;
@@ -260,6 +261,7 @@ void launch_star_solve(spnet_pc_s* pc, const double* r, const int* done, cudaStr
 
 // coarse.cu
 int pc_coarse_invert(spnet_pc_s* pc, double* A0_dense);
+int coarse_gemv_prepare(spnet_pc_s* pc);
 void launch_coarse_apply(spnet_pc_s* pc, const double* rc, double* zc, const int* done,
                          cudaStream_t s);
 
