@@ -221,6 +221,28 @@ int spnet_pc_stars(spnet_pc_t pc, const double* r, double* z, int mem);
 #define SPNET_EXPORT_STAR_LEVELS 6
 int spnet_pc_export(spnet_pc_t pc, int what, void* host_buf, size_t bytes);
 
+/* spnet_pc_restrict_static -- r_c = R_0 r, exactly as spnet_pc_restrict, but the
+ * call allocates no memory at all.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory at the time of
+ * the call -- code running inside CUDA stream capture (where cudaMalloc is not
+ * permitted), hosts that reserve all device memory up front, or real-time
+ * loops that must not enter the allocator.
+ *
+ * r (device, free order, n_free doubles) and rc (device, coarse order, m0
+ * doubles) are the caller's.  The scratch -- the Q1-weighted sums of r at the
+ * 2^d corners of every element, n_elem * 2^d * ndof doubles -- lives in one
+ * fixed array of 2^18 doubles (2 MiB) inside the library, which every GPU that
+ * loads the library holds until the process exits.  Meshes that need more
+ * corner sums are rejected with SPNET_ERR_UNSUPPORTED.  The first call on a
+ * device looks the array's device address up (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array: calls whose work overlaps on the GPU (other threads,
+ * other streams, several preconditioners) race and must be serialised by the
+ * caller.  Every entry of the array that a call reads is written earlier in
+ * the same call, so nothing has to be cleared between calls.  Runs on the
+ * operator's stream and returns when rc is complete. */
+int spnet_pc_restrict_static(spnet_pc_t pc, const double* r, double* rc);
+
 /* Instrumentation (process-wide; not part of the paper's method).
  * spnet_launch_count   kernels the library has launched since it was loaded.
  * spnet_profile_enable 1: time every launch of the kernels below with CUDA

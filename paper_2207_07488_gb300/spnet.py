@@ -31,7 +31,7 @@ EXPORTED = [
     "spnet_op_destroy", "spnet_pc_destroy", "spnet_last_error", "spnet_op_get_info",
     "spnet_pc_get_info", "spnet_spmv", "spnet_pc_apply", "spnet_pc_restrict", "spnet_pc_coarse",
     "spnet_pc_prolong", "spnet_pc_stars", "spnet_pc_export", "spnet_launch_count",
-    "spnet_profile_enable", "spnet_profile_read", "spnet_profile_reset",
+    "spnet_profile_enable", "spnet_profile_read", "spnet_profile_reset", "spnet_pc_restrict_static",
 ]
 KERNELS = ["spmv", "update", "restrict", "stars", "coarse", "combine", "direction",
            "star_symbolic", "star_numeric", "sweep", "galerkin"]
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
         getattr(lib, name).argtypes = [P, P, P, i32]
     lib.spnet_pc_export.argtypes = [P, i32, P, C.c_size_t]
     lib.spnet_launch_count.argtypes = [C.POINTER(i64)]
+    lib.spnet_pc_restrict_static.argtypes = [P, P, P]
     lib.spnet_profile_enable.argtypes = [i32]
     lib.spnet_profile_read.argtypes = [i32, C.POINTER(i64), C.POINTER(dbl)]
     lib.spnet_profile_reset.argtypes = []
@@ -315,6 +316,16 @@ class Preconditioner:
 
     def restrict(self, r):
         return self._vec_call(self._lib.spnet_pc_restrict, r, self.info.m0)
+
+    def restrict_static(self, r, rc):
+        """r_c = R_0 r into the caller's device tensor rc, allocating nothing."""
+        rp, mem, keep = _arg(r, np.float64)
+        if mem != MEM_DEVICE or not _is_torch(rc) or not rc.is_cuda:
+            raise ValueError("restrict_static takes device tensors only")
+        import torch
+        torch.cuda.current_stream(keep.device).synchronize()
+        _check(self._lib.spnet_pc_restrict_static(self.handle, rp, C.c_void_p(rc.data_ptr())))
+        return rc
 
     def coarse(self, rc):
         return self._vec_call(self._lib.spnet_pc_coarse, rc, self.info.m0)
