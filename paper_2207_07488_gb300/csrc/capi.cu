@@ -91,6 +91,7 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
     else pc->mem.release(A0);
   }
   if ((rc = pc_factor_stars(pc))) return bail(rc);
+  if ((rc = pc_elem_tables(pc))) return bail(rc);
   // work vectors
   const int64_t N = pc->N;
   if ((rc = pc->mem.get(&pc->x, N)) || (rc = pc->mem.get(&pc->r, N)) || (rc = pc->mem.get(&pc->p, N)) ||

@@ -1,7 +1,7 @@
 // The coarse solve z_c = A_0^{-1} r_c of P_0 (Section 4.1, eq. defPj).
 //
 // A_0 (m0 x m0, SPD) is inverted once at set-up by block Gauss-Jordan sweeps
-// (pivot blocks of 32): sweeping pivot block K maps
+// (pivot blocks of 64): sweeping pivot block K maps
 //   A_ij -> A_ij - A_iK P A_Kj,  A_iK -> A_iK P,  A_Kj -> P A_Kj,  A_KK -> -P
 // with P = A_KK^{-1}; after sweeping every block the matrix holds -A^{-1}.
 // For an SPD matrix the pivot blocks are Schur complements, hence SPD, so no
@@ -15,50 +15,66 @@
 
 namespace spnet {
 
-constexpr int NB = 32;
+constexpr int NB = 64;  // pivot block
 
-// invert the SPD pivot block D = Z[k0.., k0..] (kb x kb) into P (FP64 arithmetic)
+// invert the SPD pivot block D = Z[k0.., k0..] (kb x kb) into P by scalar sweeps
+// in the arithmetic of T; 1024 threads, 2 x 2 entries each
 template <class T>
-__global__ void k_pivot_inverse(T* Z, int64_t ld, int k0, int kb, double* P, int* flags) {
-  __shared__ double D[NB][NB + 1];
-  __shared__ double col[NB], row[NB];
-  __shared__ double ipiv;
-  const int i = threadIdx.y, j = threadIdx.x;
-  if (i < kb && j < kb) D[i][j] = (double)Z[(int64_t)(k0 + i) * ld + (k0 + j)];
+__global__ void __launch_bounds__(1024) k_pivot_inverse(T* Z, int64_t ld, int k0, int kb, T* P, int* flags) {
+  __shared__ T D[NB][NB + 1];
+  __shared__ T col[NB], row[NB];
+  __shared__ T ipiv;
+  const int tj = threadIdx.x, ti = threadIdx.y;  // 32 x 32
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int i = ti + 32 * a, j = tj + 32 * b;
+      D[i][j] = (i < kb && j < kb) ? Z[(int64_t)(k0 + i) * ld + (k0 + j)] : (T)0;
+    }
   __syncthreads();
   for (int p = 0; p < kb; ++p) {
-    if (i == 0 && j == 0) {
-      double piv = D[p][p];
-      if (!(piv > 0.0)) {
+    if (ti == 0 && tj == 0) {
+      T piv = D[p][p];
+      if (!(piv > (T)0)) {
         atomicOr(flags, FLAG_COARSE_SPD);
-        piv = 1.0;
+        piv = (T)1;
       }
-      ipiv = 1.0 / piv;
+      ipiv = (T)1 / piv;
     }
-    if (i == 0 && j < kb) row[j] = D[p][j];
-    if (j == 0 && i < kb) col[i] = D[i][p];
+    if (ti == 0) {
+      row[tj] = D[p][tj];
+      row[tj + 32] = D[p][tj + 32];
+    }
+    if (tj == 0) {
+      col[ti] = D[ti][p];
+      col[ti + 32] = D[ti + 32][p];
+    }
     __syncthreads();
-    if (i < kb && j < kb) {
-      const double ip = ipiv;
-      if (i != p && j != p) D[i][j] -= col[i] * row[j] * ip;
-      else if (i == p && j == p) D[i][j] = -ip;
-      else if (i == p) D[i][j] = row[j] * ip;
-      else D[i][j] = col[i] * ip;
-    }
+    const T ip = ipiv;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        const int i = ti + 32 * a, j = tj + 32 * b;
+        if (i < kb && j < kb) {
+          if (i != p && j != p) D[i][j] -= col[i] * row[j] * ip;
+          else if (i == p && j == p) D[i][j] = -ip;
+          else if (i == p) D[i][j] = row[j] * ip;
+          else D[i][j] = col[i] * ip;
+        }
+      }
     __syncthreads();
   }
-  if (i < kb && j < kb) P[i * NB + j] = -D[i][j];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int i = ti + 32 * a, j = tj + 32 * b;
+      P[i * NB + j] = (i < kb && j < kb) ? -D[i][j] : (T)0;
+    }
 }
 
 // R = Z[k0:k0+kb, :] (copy of the pivot rows), Tm = P R
 template <class T>
-__global__ void __launch_bounds__(256) k_panel(const T* Z, int64_t m0, int64_t ld, int k0, int kb,
-                                               const double* P, T* R, T* Tm) {
+__global__ void __launch_bounds__(128) k_panel(const T* Z, int64_t m0, int64_t ld, int k0, int kb,
+                                               const T* P, T* R, T* Tm) {
   __shared__ T sP[NB][NB];
-  for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) {
-    const int t = q / NB, u = q % NB;
-    sP[t][u] = (t < kb && u < kb) ? (T)P[t * NB + u] : (T)0;
-  }
+  for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) sP[q / NB][q % NB] = P[q];
   __syncthreads();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < m0;
        c += (int64_t)gridDim.x * blockDim.x) {
@@ -68,7 +84,6 @@ __global__ void __launch_bounds__(256) k_panel(const T* Z, int64_t m0, int64_t l
 #pragma unroll
     for (int t = 0; t < NB; ++t)
       if (t < kb) R[(int64_t)t * m0 + c] = col[t];
-#pragma unroll 4
     for (int t = 0; t < kb; ++t) {
       T acc = 0;
 #pragma unroll
@@ -78,17 +93,27 @@ __global__ void __launch_bounds__(256) k_panel(const T* Z, int64_t m0, int64_t l
   }
 }
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::);
+}
+
 // the rank-kb sweep update: tiles of TB x TB entries, (TB/16)^2 per thread; only
 // tiles on or above the block diagonal are computed, each writes itself and its
-// mirror image (the swept matrix stays symmetric)
+// mirror image (the swept matrix stays symmetric).  The tile's old values are
+// copied to shared memory asynchronously while the update is computed.
 template <class T, int TB>
-__global__ void __launch_bounds__(256) k_sweep(T* Z, int64_t m0, int64_t ld, int k0, int kb, const double* P,
+__global__ void __launch_bounds__(256) k_sweep(T* Z, int64_t m0, int64_t ld, int k0, int kb, const T* P,
                                                const T* __restrict__ R, const T* __restrict__ Tm) {
-  constexpr int RT = TB / 16;  // register tile
+  constexpr int RT = TB / 16;       // register tile
+  constexpr int SO = TB + 16 / sizeof(T);  // padded row of the staged tile (16-byte aligned)
   extern __shared__ __align__(16) char sm_raw[];
   T (*sR)[TB] = reinterpret_cast<T (*)[TB]>(sm_raw);
   T (*sT)[TB] = reinterpret_cast<T (*)[TB]>(sm_raw + sizeof(T) * NB * TB);
-  T (*sO)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(sm_raw + 2 * sizeof(T) * NB * TB);
+  T (*sO)[SO] = reinterpret_cast<T (*)[SO]>(sm_raw + 2 * sizeof(T) * NB * TB);
   // map the linear block index to an upper-triangular tile (bi <= bj)
   const int nt = (int)((m0 + TB - 1) / TB);
   int rem = blockIdx.x, bi = 0;
@@ -99,6 +124,13 @@ __global__ void __launch_bounds__(256) k_sweep(T* Z, int64_t m0, int64_t ld, int
   const int bj = bi + rem;
   const int64_t i0 = (int64_t)bi * TB, j0 = (int64_t)bj * TB;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  // old tile values -> sO (16-byte chunks; rows are 16-byte aligned, ld padded)
+  constexpr int CH = TB * sizeof(T) / 16;  // chunks per tile row
+  for (int q = threadIdx.x; q < TB * CH; q += 256) {
+    const int li = q / CH, ch = q % CH;
+    const int64_t i = i0 + li, j = j0 + ch * (16 / sizeof(T));
+    if (i < m0 && j < ld) cp_async16(&sO[li][ch * (16 / sizeof(T))], &Z[i * ld + j]);
+  }
   for (int q = threadIdx.x; q < NB * TB; q += 256) {
     const int t = q / TB, c = q % TB;
     sR[t][c] = (t < kb && i0 + c < m0) ? R[(int64_t)t * m0 + i0 + c] : (T)0;
@@ -121,7 +153,9 @@ __global__ void __launch_bounds__(256) k_sweep(T* Z, int64_t m0, int64_t ld, int
 #pragma unroll
       for (int b = 0; b < RT; ++b) acc[a][b] += ri[a] * tj[b];
   }
-  // new values of the tile (i, j) in shared memory
+  cp_async_wait_all();
+  __syncthreads();
+  // new values of the tile (i, j), in place in shared memory
 #pragma unroll
   for (int a = 0; a < RT; ++a) {
     const int li = ty + 16 * a;
@@ -134,14 +168,19 @@ __global__ void __launch_bounds__(256) k_sweep(T* Z, int64_t m0, int64_t ld, int
       T v = 0;
       if (i < m0 && j < m0) {
         const bool jK = j >= k0 && j < k0 + kb;
-        if (!iK && !jK) v = Z[i * ld + j] - acc[a][b];
-        else if (iK && jK) v = (T)(-P[(i - k0) * NB + (j - k0)]);
+        if (!iK && !jK) v = sO[li][lj] - acc[a][b];
+        else if (iK && jK) v = -P[(i - k0) * NB + (j - k0)];
         else if (iK) v = sT[i - k0][lj];
         else v = Tm[(j - k0) * m0 + i];  // A_iK P = (P A_Ki)^T by symmetry
       }
-      sO[li][lj] = v;
+      acc[a][b] = v;
     }
   }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < RT; ++a)
+#pragma unroll
+    for (int b = 0; b < RT; ++b) sO[ty + 16 * a][tx + 16 * b] = acc[a][b];
   __syncthreads();
   for (int q = threadIdx.x; q < TB * TB; q += 256) {
     const int li = q / TB, lj = q % TB;
@@ -184,8 +223,7 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
   SPNET_TRY(pc->mem.get(&Z, m0 * ld));
   pc->Z = Z;
   pc->ldz = ld;
-  double* P = nullptr;
-  T *R = nullptr, *Tm = nullptr;
+  T *P = nullptr, *R = nullptr, *Tm = nullptr;
   SPNET_TRY(tmp.get(&P, NB * NB));
   SPNET_TRY(tmp.get(&R, NB * m0));
   SPNET_TRY(tmp.get(&Tm, NB * m0));
@@ -196,7 +234,7 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
   constexpr int TB = sizeof(T) == 4 ? 128 : 64;
   const int nt = (int)((m0 + TB - 1) / TB);
   const unsigned tiles = (unsigned)(nt * (nt + 1) / 2);
-  const size_t smem = sizeof(T) * (2 * NB * TB + TB * (TB + 1));
+  const size_t smem = sizeof(T) * (2 * NB * TB + TB * (TB + 16 / sizeof(T)));
   static bool attr_set[64] = {};  // per device and instantiation; the size depends only on T
   int dev = 0;
   SPNET_CUDA_TRY(cudaGetDevice(&dev));
@@ -208,9 +246,9 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
   for (int k0 = 0; k0 < m0; k0 += NB) {
     const int kb = (int)((m0 - k0) < NB ? (m0 - k0) : NB);
     note_launch();
-    k_pivot_inverse<T><<<1, dim3(NB, NB), 0, s>>>(Z, ld, k0, kb, P, pc->op->dflags);
+    k_pivot_inverse<T><<<1, dim3(32, 32), 0, s>>>(Z, ld, k0, kb, P, pc->op->dflags);
     note_launch();
-    k_panel<T><<<(unsigned)((m0 + 255) / 256), 256, 0, s>>>(Z, m0, ld, k0, kb, P, R, Tm);
+    k_panel<T><<<(unsigned)((m0 + 127) / 128), 128, 0, s>>>(Z, m0, ld, k0, kb, P, R, Tm);
     note_launch();
     ProfScope ps(KID_SWEEP, s);
     k_sweep<T, TB><<<tiles, 256, smem, s>>>(Z, m0, ld, k0, kb, P, R, Tm);

@@ -256,41 +256,62 @@ __global__ void k_restrict(int n_mesh, Mesh m, int ndof, const double* __restric
   }
 }
 
-// z = [R_0^T z_c] + [sum_j E_j w_j]; partials (r, z) and (r, z_old); last block: beta
-__global__ void __launch_bounds__(256) k_combine(int64_t N, Mesh m, int ndof, const int32_t* elem_of,
-                                                 const int8_t* comp_of, const int32_t* elem_ptr,
-                                                 const double* q1w, const int32_t* cidx, const double* zc,
-                                                 const int32_t* elem_star_off, const int32_t* star_of_mesh,
-                                                 const int64_t* star_ptr, const double* w, const double* r,
-                                                 double* z, double* part1, double* part2, int with_coarse,
+// z = [R_0^T z_c] + [sum_j E_j w_j], one warp per element: the element's
+// coarse values z_c at its corners and the bases of its entries in the star
+// results are loaded once and held in registers; partials (r, z) and
+// (r, z_old); last block: beta
+template <int NC, int ND>
+__global__ void __launch_bounds__(256) k_combine(int n_elem, int64_t N, const int32_t* __restrict__ elem_ptr,
+                                                 const int8_t* __restrict__ comp_of,
+                                                 const double* __restrict__ q1w,
+                                                 const int32_t* __restrict__ ecoarse,
+                                                 const int64_t* __restrict__ estar,
+                                                 const double* __restrict__ zc, const double* __restrict__ w,
+                                                 const double* __restrict__ r, double* __restrict__ z,
+                                                 double* part1, double* part2, int with_coarse,
                                                  int with_stars, Scal* sc, int flexible, int first) {
   __shared__ double sh[32];
   if (sc && sc->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double s1 = 0.0, s2 = 0.0;
-  GRID_STRIDE(p, N) {
-    const int e = elem_of[p];
-    const int a = ndof == 1 ? 0 : comp_of[p];
-    double v = 0.0;
-    if (with_coarse) {
-      for (int c = 0; c < m.nc; ++c) {
-        int ci = cidx[(int64_t)mesh_of(m, e, c) * ndof + a];
-        if (ci >= 0) v = fma(q1w[(int64_t)c * N + p], zc[ci], v);
+  for (int64_t e = gwarp; e < n_elem; e += nwarps) {
+    double zl = 0.0;
+    long long sl = -1;
+    if (lane < NC * ND && with_coarse) {
+      const int ci = ecoarse[e * (NC * ND) + lane];
+      if (ci >= 0) zl = zc[ci];
+    }
+    if (lane < NC && with_stars) sl = estar[e * NC + lane];
+    double zcv[NC * ND];
+    long long sb[NC];
+#pragma unroll
+    for (int t = 0; t < NC * ND; ++t) zcv[t] = __shfl_sync(0xffffffffu, zl, t);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) sb[c] = __shfl_sync(0xffffffffu, sl, c);
+    const int a0 = elem_ptr[e], a1 = elem_ptr[e + 1];
+    for (int i = a0 + lane; i < a1; i += 32) {
+      const int a = ND == 1 ? 0 : comp_of[i];
+      double v = 0.0;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        double zv = zcv[c * ND];
+#pragma unroll
+        for (int b = 1; b < ND; ++b)
+          if (b == a) zv = zcv[c * ND + b];
+        v = fma(q1w[(int64_t)c * N + i], zv, v);
       }
-    }
-    if (with_stars) {
-      const int off_e = (int)(p - elem_ptr[e]);
-      for (int c = 0; c < m.nc; ++c) {
-        int so = elem_star_off[(int64_t)e * m.nc + c];
-        if (so < 0) continue;
-        int st = star_of_mesh[mesh_of(m, e, c)];
-        v += w[star_ptr[st] + so + off_e];
+      const int off = i - a0;
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (sb[c] >= 0) v += w[sb[c] + off];
+      if (sc) {
+        s1 = fma(r[i], v, s1);
+        s2 = fma(r[i], z[i], s2);
       }
+      z[i] = v;
     }
-    if (sc) {
-      s1 = fma(r[p], v, s1);
-      s2 = fma(r[p], z[p], s2);
-    }
-    z[p] = v;
   }
   if (!sc) return;
   block_partial(s1, part1, sh);
@@ -306,6 +327,32 @@ __global__ void __launch_bounds__(256) k_combine(int64_t N, Mesh m, int ndof, co
       sc->cnt[2] = 0;
     }
   }
+}
+
+// per element and corner: the coarse index (per component) and the base of the
+// element's entries in the star at that corner (-1 where there is none)
+__global__ void k_elem_tables(int n_elem, Mesh m, int ndof, const int32_t* cidx, const int32_t* elem_star_off,
+                              const int32_t* star_of_mesh, const int64_t* star_ptr, int32_t* ecoarse,
+                              int64_t* estar) {
+  GRID_STRIDE(e, (int64_t)n_elem) {
+    for (int c = 0; c < m.nc; ++c) {
+      const int k = mesh_of(m, (int)e, c);
+      for (int a = 0; a < ndof; ++a) ecoarse[(e * m.nc + c) * ndof + a] = cidx[(int64_t)k * ndof + a];
+      const int so = elem_star_off[e * m.nc + c];
+      estar[e * m.nc + c] = so < 0 ? -1 : star_ptr[star_of_mesh[k]] + so;
+    }
+  }
+}
+
+int pc_elem_tables(spnet_pc_s* pc) {
+  cudaStream_t s = pc->op->stream;
+  SPNET_TRY(pc->mem.get(&pc->ecoarse, (size_t)pc->n_elem * pc->nc * pc->ndof));
+  SPNET_TRY(pc->mem.get(&pc->estar, (size_t)pc->n_elem * pc->nc));
+  note_launch();
+  k_elem_tables<<<4 * num_sms(), 256, 0, s>>>(pc->n_elem, mesh_of_pc(pc), pc->ndof, pc->cidx, pc->elem_star_off,
+                                              pc->star_of_mesh, pc->star_ptr, pc->ecoarse, pc->estar);
+  SPNET_CUDA_TRY(cudaGetLastError());
+  return SPNET_OK;
 }
 
 template <int NC, int ND>
@@ -350,17 +397,25 @@ void launch_restrict(spnet_pc_s* pc, double* rc, const int* done, cudaStream_t s
   k_restrict<<<blocks, 256, 0, s>>>(pc->n_mesh, mesh_of_pc(pc), pc->ndof, pc->epart, pc->cidx, rc, done);
 }
 
+template <int NC, int ND>
+static void launch_combine_t(spnet_pc_s* pc, const double* r, double* z, int with_coarse, int with_stars,
+                             int dots, cudaStream_t s) {
+  k_combine<NC, ND><<<pc->G, 256, 0, s>>>(pc->n_elem, pc->N, pc->elem_ptr, pc->comp_of, pc->q1w, pc->ecoarse,
+                                         pc->estar, pc->zc, pc->w, r, z, pc->partial + 2 * pc->G,
+                                         pc->partial + 3 * pc->G, with_coarse && pc->m0 > 0,
+                                         with_stars && pc->S > 0, dots ? pc->scal : nullptr, pc->flexible,
+                                         dots == 2 ? 1 : 0);
+}
+
 // dots: 0 none, 1 PCG step (beta from the previous rz), 2 PCG start (beta = 0)
 void launch_combine(spnet_pc_s* pc, const double* r, double* z, int with_coarse, int with_stars,
                     int dots, cudaStream_t s) {
   note_launch();
   ProfScope ps(KID_COMBINE, s);
-  k_combine<<<pc->G, 256, 0, s>>>(pc->N, mesh_of_pc(pc), pc->ndof, pc->elem_of, pc->comp_of,
-                                  pc->elem_ptr, pc->q1w, pc->cidx, pc->zc, pc->elem_star_off,
-                                  pc->star_of_mesh, pc->star_ptr, pc->w, r, z, pc->partial + 2 * pc->G,
-                                  pc->partial + 3 * pc->G, with_coarse && pc->m0 > 0,
-                                  with_stars && pc->S > 0, dots ? pc->scal : nullptr, pc->flexible,
-                                  dots == 2 ? 1 : 0);
+  if (pc->nc == 4 && pc->ndof == 1) launch_combine_t<4, 1>(pc, r, z, with_coarse, with_stars, dots, s);
+  else if (pc->nc == 8 && pc->ndof == 1) launch_combine_t<8, 1>(pc, r, z, with_coarse, with_stars, dots, s);
+  else if (pc->nc == 4) launch_combine_t<4, 3>(pc, r, z, with_coarse, with_stars, dots, s);
+  else launch_combine_t<8, 3>(pc, r, z, with_coarse, with_stars, dots, s);
 }
 
 // z = B r for a vector r already in pc order (corner sums of r computed here)

@@ -142,12 +142,19 @@ struct spnet_pc_s {
   int32_t* star_n = nullptr;       // [S]
   int32_t* star_lev = nullptr;     // [S]
   int32_t* star_nnz = nullptr;     // [S]
-  int solve_spw = 0;               // shared-memory bytes per warp of the star solve
+  char* spool = nullptr;           // packed per-star solve sections, star order
+  int64_t spool_bytes = 0;
+  int64_t* soff = nullptr;         // [S+1] byte offsets of the sections
+  int32_t* blk_star = nullptr;     // [solve_blocks+1] first star of each solve block
+  uint8_t* blk_global = nullptr;   // [solve_blocks] 1: the block's star is solved from global memory
+  int solve_blocks = 0;
   // work vectors (pc order)
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *b = nullptr;
   double *w = nullptr, *rc = nullptr, *zc = nullptr, *partial = nullptr, *vtmp = nullptr;
   void* ybuf = nullptr;
   double* epart = nullptr;         // [n_elem*nc*ndof] Q1-weighted corner sums of r
+  int32_t* ecoarse = nullptr;      // [n_elem*nc*ndof] coarse index at each corner (-1: none)
+  int64_t* estar = nullptr;        // [n_elem*nc] base of the element's entries in w (-1: no star)
   spnet::Scal* scal = nullptr;
   cudaGraphExec_t graph_exec = nullptr;  // a chunk of PCG iterations
   cudaStream_t side = nullptr;     // second stream of the graph (star solves)
@@ -270,6 +277,7 @@ void launch_restrict(spnet_pc_s* pc, double* rc, const int* done, cudaStream_t s
 void launch_combine(spnet_pc_s* pc, const double* r, double* z, int with_coarse, int with_stars,
                     int dots, cudaStream_t s);
 int pc_restrict_free(spnet_pc_s* pc, const double* r_free, double* rc);
+int pc_elem_tables(spnet_pc_s* pc);
 int pc_apply_free(spnet_pc_s* pc, const double* r_free_dev, double* z_free_dev, int which);
 void to_pc(spnet_pc_s* pc, const double* free_vec, double* pc_vec);
 void from_pc(spnet_pc_s* pc, const double* pc_vec, double* free_vec);

@@ -513,99 +513,301 @@ __global__ void __launch_bounds__(128) k_star_numeric(int S, char* pool, const i
   }
 }
 
-__global__ void k_solve_need(int S, const char* pool, const int64_t* star_off, int vbytes, int* mx) {
-  int m = 0;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
-    const int32_t* hdr = (const int32_t*)(pool + star_off[s]);
-    const BlobLayout L = blob_layout(hdr[0], hdr[1], hdr[2], vbytes);
-    int need = (int)(L.solve + align_up((int64_t)vbytes * hdr[0], 16));
-    m = max(m, need);
-  }
-  atomicMax(mx, m);
+// ---------------------------------------------------------------------------
+// The solve works on compact per-star sections packed in star order:
+//   header (80 B): n, nlev, nnz, pointer bytes; base of the star in w; the pc
+//                  index of the first dof and the local offset of each of the
+//                  star's 2^d elements
+//   lvl [nlev+1] u16, perm [n] u16, rowptr/colptr [n+1] (u16, or u32 when
+//   nnz > 65535), rowidx/colidx [nnz] u16, then (8-byte aligned) row values,
+//   column values and 1/L_vv in the solve precision; padded to 16 bytes.
+// Stars are grouped into blocks whose sections and vectors fit a shared-memory
+// budget; a block copies its contiguous sections into shared memory with
+// 16-byte loads and each warp then solves one star there: every level step
+// reads shared memory only.
+// ---------------------------------------------------------------------------
+constexpr int SOLVE_WPB = 12;                  // warps (stars) per block
+constexpr int SOLVE_BUDGET = 110 * 1024;       // shared memory per block
+constexpr int SEC_HDR = 80;
+
+struct SecLayout {
+  int64_t lvl, perm, rowptr, colptr, rowidx, colidx, rowval, colval, invd, total;
+};
+
+__host__ __device__ inline SecLayout sec_layout(int n, int nlev, int nnz, int vb) {
+  SecLayout L;
+  const int pw = nnz > 65535 ? 4 : 2;
+  int64_t o = SEC_HDR;
+  L.lvl = o;    o += 2ll * (nlev + 1);
+  L.perm = o;   o += 2ll * n;
+  o = align_up(o, pw);
+  L.rowptr = o; o += (int64_t)pw * (n + 1);
+  L.colptr = o; o += (int64_t)pw * (n + 1);
+  L.rowidx = o; o += 2ll * nnz;
+  L.colidx = o; o += 2ll * nnz;
+  o = align_up(o, 8);
+  L.rowval = o; o += (int64_t)vb * nnz;
+  L.colval = o; o += (int64_t)vb * nnz;
+  L.invd = o;   o += (int64_t)vb * n;
+  L.total = align_up(o, 16);
+  return L;
 }
 
-// ---------------------------------------------------------------------------
-// the solve: gather r over the star, forward and backward level sweeps, write
-// w_j in the star's element-concatenated order
-// ---------------------------------------------------------------------------
+__global__ void k_sec_sizes(int S, const char* pool, const int64_t* star_off, int vb, int64_t* sz,
+                            int32_t* yb) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
+    const int32_t* h = (const int32_t*)(pool + star_off[s]);
+    sz[s] = sec_layout(h[0], h[1], h[2], vb).total;
+    yb[s] = (int32_t)align_up((int64_t)vb * h[0], 16);
+  }
+}
+
+// warp per star: setup blob (FP64) -> compact section (vb-byte values)
 template <class T>
-__global__ void __launch_bounds__(128) k_star_solve(int S, const char* __restrict__ pool,
-                                                    const int64_t* __restrict__ star_off,
-                                                    const int64_t* __restrict__ star_ptr,
-                                                    const double* __restrict__ r, T* ybuf,
-                                                    double* __restrict__ w, int spw, const int* done) {
-  extern __shared__ __align__(16) char smem[];
-  if (done && *done) return;
+__global__ void k_sec_pack(int S, Mesh m, const char* pool, const int64_t* star_off,
+                           const int32_t* star_mesh, const int32_t* elem_ptr, const int64_t* star_ptr,
+                           char* spool, const int64_t* soff) {
   const int lane = threadIdx.x & 31;
-  char* mine = smem + (threadIdx.x >> 5) * spw;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
     const char* blob = pool + star_off[s];
-    const int4 h = *(const int4*)blob;
-    const int n = h.x, nlev = h.y, nnz = h.z;
-    const BlobLayout L = blob_layout(n, nlev, nnz, (int)sizeof(T));
-    const int64_t base = star_ptr[s];
-    const char* src;
-    T* y;
-    if (L.solve + align_up((int64_t)sizeof(T) * n, 16) <= spw) {
-      // stage the solve section in shared memory (16-byte vector copies)
-      const int4* g4 = (const int4*)blob;
-      int4* s4 = (int4*)mine;
-      const int n4 = (int)(L.solve >> 4);
-      for (int q = lane; q < n4; q += 32) s4[q] = __ldg(&g4[q]);
-      src = mine;
-      y = (T*)(mine + L.solve);
-      __syncwarp();
+    const int32_t* hb = (const int32_t*)blob;
+    const int n = hb[0], nlev = hb[1], nnz = hb[2];
+    const BlobLayout B = blob_layout(n, nlev, nnz, 8);
+    const SecLayout L = sec_layout(n, nlev, nnz, sizeof(T));
+    char* sec = spool + soff[s];
+    if (lane == 0) {
+      int32_t* h = (int32_t*)sec;
+      h[0] = n;
+      h[1] = nlev;
+      h[2] = nnz;
+      h[3] = nnz > 65535 ? 4 : 2;
+      *(int64_t*)(sec + 16) = star_ptr[s];
+      int32_t* es = (int32_t*)(sec + 24);
+      uint16_t* eo = (uint16_t*)(sec + 56);
+      const StarElems se = star_elems(m, star_mesh[s], elem_ptr);
+      for (int cp = 0; cp < 8; ++cp) es[cp] = (cp < m.nc && se.e[cp] >= 0) ? elem_ptr[se.e[cp]] : -1;
+      for (int cp = 0; cp <= 8; ++cp) eo[cp] = (uint16_t)(cp <= m.nc ? se.off[cp < m.nc ? cp : m.nc] : n);
+    }
+    const uint16_t* lvl = (const uint16_t*)(blob + B.lvl);
+    const uint16_t* perm = (const uint16_t*)(blob + B.perm);
+    const uint32_t* rowptr = (const uint32_t*)(blob + B.rowptr);
+    const uint32_t* colptr = (const uint32_t*)(blob + B.colptr);
+    const uint16_t* rowidx = (const uint16_t*)(blob + B.rowidx);
+    const uint16_t* colidx = (const uint16_t*)(blob + B.colidx);
+    const double* v64 = (const double*)(blob + B.v64);  // row values, column values, 1/L_vv
+    for (int q = lane; q <= nlev; q += 32) ((uint16_t*)(sec + L.lvl))[q] = lvl[q];
+    for (int q = lane; q < n; q += 32) ((uint16_t*)(sec + L.perm))[q] = perm[q];
+    if (nnz > 65535) {
+      for (int q = lane; q <= n; q += 32) {
+        ((uint32_t*)(sec + L.rowptr))[q] = rowptr[q];
+        ((uint32_t*)(sec + L.colptr))[q] = colptr[q];
+      }
     } else {
-      src = blob;
-      y = ybuf + base;
-    }
-    const int32_t* gidx = (const int32_t*)(src + L.gidx);
-    const uint16_t* perm = (const uint16_t*)(src + L.perm);
-    const uint16_t* lvl = (const uint16_t*)(src + L.lvl);
-    const uint32_t* colptr = (const uint32_t*)(src + L.colptr);
-    const uint16_t* colidx = (const uint16_t*)(src + L.colidx);
-    const uint32_t* rowptr = (const uint32_t*)(src + L.rowptr);
-    const uint16_t* rowidx = (const uint16_t*)(src + L.rowidx);
-    const T* rowv = (const T*)(src + L.rowval);
-    const T* colv = (const T*)(src + L.colval);
-    const T* invd = (const T*)(src + L.invd);
-    for (int pos = lane; pos < n; pos += 32) y[pos] = (T)r[gidx[pos]];
-    __syncwarp();
-    for (int l = 0; l < nlev; ++l) {
-      for (int v = lvl[l] + lane; v < (int)lvl[l + 1]; v += 32) {
-        T acc = y[v];
-        for (uint32_t q = rowptr[v]; q < rowptr[v + 1]; ++q) acc -= rowv[q] * y[rowidx[q]];
-        y[v] = acc * invd[v];
+      for (int q = lane; q <= n; q += 32) {
+        ((uint16_t*)(sec + L.rowptr))[q] = (uint16_t)rowptr[q];
+        ((uint16_t*)(sec + L.colptr))[q] = (uint16_t)colptr[q];
       }
-      __syncwarp();
     }
-    for (int l = nlev - 1; l >= 0; --l) {
-      for (int v = lvl[l] + lane; v < (int)lvl[l + 1]; v += 32) {
-        T acc = y[v];
-        for (uint32_t q = colptr[v]; q < colptr[v + 1]; ++q) acc -= colv[q] * y[colidx[q]];
-        y[v] = acc * invd[v];
+    for (int q = lane; q < nnz; q += 32) {
+      ((uint16_t*)(sec + L.rowidx))[q] = rowidx[q];
+      ((uint16_t*)(sec + L.colidx))[q] = colidx[q];
+    }
+    T* vals = (T*)(sec + L.rowval);  // rowval, colval, invd are contiguous
+    for (int q = lane; q < 2 * nnz + n; q += 32) vals[q] = (T)v64[q];
+  }
+}
+
+template <class T, class PT>
+__device__ __forceinline__ void solve_section(const char* sec, T* y, const double* __restrict__ r,
+                                              double* __restrict__ w, int lane) {
+  const int32_t* h = (const int32_t*)sec;
+  const int n = h[0], nlev = h[1], nnz = h[2];
+  const SecLayout L = sec_layout(n, nlev, nnz, sizeof(T));
+  const int64_t base = *(const int64_t*)(sec + 16);
+  const int32_t* es = (const int32_t*)(sec + 24);
+  const uint16_t* eo = (const uint16_t*)(sec + 56);
+  const uint16_t* lvl = (const uint16_t*)(sec + L.lvl);
+  const uint16_t* perm = (const uint16_t*)(sec + L.perm);
+  const PT* rowptr = (const PT*)(sec + L.rowptr);
+  const PT* colptr = (const PT*)(sec + L.colptr);
+  const uint16_t* rowidx = (const uint16_t*)(sec + L.rowidx);
+  const uint16_t* colidx = (const uint16_t*)(sec + L.colidx);
+  const T* rowv = (const T*)(sec + L.rowval);
+  const T* colv = (const T*)(sec + L.colval);
+  const T* invd = (const T*)(sec + L.invd);
+  // gather r over the star: position -> element-concatenated index -> pc index
+  constexpr int GU = 4;
+  for (int p0 = 0; p0 < n; p0 += 32 * GU) {
+    double rv[GU];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const int pos = p0 + u * 32 + lane;
+      rv[u] = 0.0;
+      if (pos < n) {
+        const int t = perm[pos];
+        int cp = 0;
+#pragma unroll
+        for (int c = 1; c < 8; ++c)
+          if (t >= (int)eo[c] && es[c] >= 0) cp = c;
+        rv[u] = __ldg(&r[es[cp] + (t - (int)eo[cp])]);
       }
-      __syncwarp();
     }
-    for (int pos = lane; pos < n; pos += 32) w[base + perm[pos]] = (double)y[pos];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const int pos = p0 + u * 32 + lane;
+      if (pos < n) y[pos] = (T)rv[u];
+    }
+  }
+  __syncwarp();
+  for (int l = 0; l < nlev; ++l) {
+    const int v1 = lvl[l + 1];
+    for (int v = lvl[l] + lane; v < v1; v += 32) {
+      T acc = y[v];
+      const int q1 = rowptr[v + 1];
+      for (int q = rowptr[v]; q < q1; ++q) acc -= rowv[q] * y[rowidx[q]];
+      y[v] = acc * invd[v];
+    }
     __syncwarp();
+  }
+  for (int l = nlev - 1; l >= 0; --l) {
+    const int v1 = lvl[l + 1];
+    for (int v = lvl[l] + lane; v < v1; v += 32) {
+      T acc = y[v];
+      const int q1 = colptr[v + 1];
+      for (int q = colptr[v]; q < q1; ++q) acc -= colv[q] * y[colidx[q]];
+      y[v] = acc * invd[v];
+    }
+    __syncwarp();
+  }
+  for (int pos = lane; pos < n; pos += 32) w[base + perm[pos]] = (double)y[pos];
+}
+
+// block b solves stars blk[b] .. blk[b+1]-1; a block flagged "global" (one star
+// too large for the budget) reads its section from global memory and keeps y
+// in the global scratch
+template <class T>
+__global__ void __launch_bounds__(SOLVE_WPB * 32) k_star_solve(const int32_t* __restrict__ blk,
+                                                                const uint8_t* __restrict__ blk_global,
+                                                                const char* __restrict__ spool,
+                                                                const int64_t* __restrict__ soff,
+                                                                const int64_t* __restrict__ star_ptr,
+                                                                const double* __restrict__ r,
+                                                                double* __restrict__ w, T* ybuf,
+                                                                const int* done) {
+  extern __shared__ int4 smem4[];
+  if (done && *done) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int s0 = blk[blockIdx.x], s1 = blk[blockIdx.x + 1];
+  const int64_t g0 = soff[s0], g1 = soff[s1];
+  if (blk_global[blockIdx.x]) {
+    for (int s = s0 + wid; s < s1; s += SOLVE_WPB) {
+      const char* sec = spool + soff[s];
+      const int nnz = ((const int32_t*)sec)[2];
+      T* y = ybuf + star_ptr[s];
+      if (nnz > 65535) solve_section<T, uint32_t>(sec, y, r, w, lane);
+      else solve_section<T, uint16_t>(sec, y, r, w, lane);
+    }
+    return;
+  }
+  const int n4 = (int)((g1 - g0) >> 4);
+  const int4* src = (const int4*)(spool + g0);
+  for (int q = threadIdx.x; q < n4; q += blockDim.x) smem4[q] = __ldg(&src[q]);
+  __syncthreads();
+  const char* sm = (const char*)smem4;
+  for (int s = s0 + wid; s < s1; s += SOLVE_WPB) {
+    // y of this star after all sections, behind the vectors of the block's earlier stars
+    int64_t yo = g1 - g0;
+    for (int t = s0; t < s; ++t) yo += align_up((int64_t)sizeof(T) * ((const int32_t*)(sm + (soff[t] - g0)))[0], 16);
+    const char* sec = sm + (soff[s] - g0);
+    const int nnz = ((const int32_t*)sec)[2];
+    T* y = (T*)(sm + yo);
+    if (nnz > 65535) solve_section<T, uint32_t>(sec, y, r, w, lane);
+    else solve_section<T, uint16_t>(sec, y, r, w, lane);
   }
 }
 
 void launch_star_solve(spnet_pc_s* pc, const double* r, const int* done, cudaStream_t s) {
   if (pc->S == 0) return;
-  const int wpb = 4;
-  const int spw = pc->solve_spw;
-  int blocks = (pc->S + wpb - 1) / wpb;
   note_launch();
   ProfScope ps(KID_STARS, s);
   if (pc->precision == SPNET_PREC_FP64)
-    k_star_solve<double><<<blocks, 32 * wpb, (size_t)spw * wpb, s>>>(
-        pc->S, pc->pool, pc->star_off, pc->star_ptr, r, (double*)pc->ybuf, pc->w, spw, done);
+    k_star_solve<double><<<pc->solve_blocks, SOLVE_WPB * 32, SOLVE_BUDGET, s>>>(
+        pc->blk_star, pc->blk_global, pc->spool, pc->soff, pc->star_ptr, r, pc->w, (double*)pc->ybuf, done);
   else
-    k_star_solve<float><<<blocks, 32 * wpb, (size_t)spw * wpb, s>>>(
-        pc->S, pc->pool, pc->star_off, pc->star_ptr, r, (float*)pc->ybuf, pc->w, spw, done);
+    k_star_solve<float><<<pc->solve_blocks, SOLVE_WPB * 32, SOLVE_BUDGET, s>>>(
+        pc->blk_star, pc->blk_global, pc->spool, pc->soff, pc->star_ptr, r, pc->w, (float*)pc->ybuf, done);
+}
+
+// compact sections in star order, grouped into blocks by the shared-memory budget
+static int pack_sections(spnet_pc_s* pc, DevArena& tmp) {
+  cudaStream_t s = pc->op->stream;
+  const int S = pc->S;
+  const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
+  int64_t* sz = nullptr;
+  int32_t* yb = nullptr;
+  SPNET_TRY(tmp.get(&sz, S + 1));
+  SPNET_TRY(tmp.get(&yb, S));
+  SPNET_TRY(pc->mem.get(&pc->soff, S + 1));
+  note_launch();
+  k_sec_sizes<<<(S + 255) / 256, 256, 0, s>>>(S, pc->pool, pc->star_off, vb, sz, yb);
+  SPNET_TRY(scan_exclusive64(sz, pc->soff, S, s, tmp));
+  std::vector<int64_t> hoff(S + 1);
+  std::vector<int32_t> hyb(S);
+  SPNET_CUDA_TRY(cudaMemcpyAsync(hoff.data(), pc->soff, sizeof(int64_t) * (S + 1), cudaMemcpyDeviceToHost, s));
+  SPNET_CUDA_TRY(cudaMemcpyAsync(hyb.data(), yb, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, s));
+  SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+  pc->spool_bytes = hoff[S];
+  SPNET_TRY(pc->mem.get(&pc->spool, hoff[S] > 0 ? hoff[S] : 16));
+  note_launch();
+  if (vb == 8)
+    k_sec_pack<double><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_mesh,
+                                                   pc->elem_ptr, pc->star_ptr, pc->spool, pc->soff);
+  else
+    k_sec_pack<float><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_mesh,
+                                                  pc->elem_ptr, pc->star_ptr, pc->spool, pc->soff);
+  // greedy grouping in star order
+  std::vector<int32_t> blk;
+  std::vector<uint8_t> glob;
+  int st = 0;
+  while (st < S) {
+    int e = st;
+    int64_t bytes = 0;
+    while (e < S && e - st < SOLVE_WPB) {
+      const int64_t add = (hoff[e + 1] - hoff[e]) + hyb[e];
+      if (bytes + add > SOLVE_BUDGET) break;
+      bytes += add;
+      ++e;
+    }
+    blk.push_back(st);
+    if (e == st) {  // one star beyond the budget: solved from global memory
+      glob.push_back(1);
+      e = st + 1;
+    } else {
+      glob.push_back(0);
+    }
+    st = e;
+  }
+  blk.push_back(S);
+  pc->solve_blocks = (int)glob.size();
+  SPNET_TRY(pc->mem.get(&pc->blk_star, blk.size()));
+  SPNET_TRY(pc->mem.get(&pc->blk_global, glob.size()));
+  SPNET_CUDA_TRY(cudaMemcpyAsync(pc->blk_star, blk.data(), sizeof(int32_t) * blk.size(), cudaMemcpyHostToDevice, s));
+  SPNET_CUDA_TRY(cudaMemcpyAsync(pc->blk_global, glob.data(), glob.size(), cudaMemcpyHostToDevice, s));
+  SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+  static bool attr_set[64][2] = {};
+  int dev = 0;
+  SPNET_CUDA_TRY(cudaGetDevice(&dev));
+  dev &= 63;
+  if (vb == 8 && !attr_set[dev][1]) {
+    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_BUDGET));
+    attr_set[dev][1] = true;
+  }
+  if (vb == 4 && !attr_set[dev][0]) {
+    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_BUDGET));
+    attr_set[dev][0] = true;
+  }
+  return SPNET_OK;
 }
 
 int pc_factor_stars(spnet_pc_s* pc) {
@@ -666,7 +868,7 @@ int pc_factor_stars(spnet_pc_s* pc) {
     A.star_nnz = pc->star_nnz;
     A.flags = flags;
     A.next = counters;
-    A.vbytes = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
+    A.vbytes = 8;  // the set-up blobs keep FP64 values; the solve sections are packed later
     note_launch();
     ProfScope ps(KID_STAR_SYMBOLIC, s);
     k_star_symbolic<<<(unsigned)(warps / 4), 128, 0, s>>>(A);
@@ -690,9 +892,8 @@ int pc_factor_stars(spnet_pc_s* pc) {
   int blocks = (pc->S + 3) / 4;
   note_launch();
   ProfScope ps(KID_STAR_NUMERIC, s);
-  const int vbytes = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
   k_star_numeric<<<blocks, 128, 0, s>>>(pc->S, pc->pool, pc->star_off, pc->K.ptr, pc->K.col,
-                                         pc->K.val, vbytes, flags);
+                                         pc->K.val, 8, flags);
   SPNET_CUDA_TRY(cudaGetLastError());
   SPNET_TRY(check_flags(flags, s, "setup_preconditioner (star factorisation)"));
   // statistics
@@ -708,35 +909,13 @@ int pc_factor_stars(spnet_pc_s* pc) {
     pc->total_levels += lev[i];
     pc->max_levels = lev[i] > pc->max_levels ? lev[i] : pc->max_levels;
   }
-  // local solve buffers (used by stars that do not fit the shared-memory stage)
+  // vectors of stars solved from global memory, then the packed solve sections;
+  // the set-up blobs are released
+  const int vbytes = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
   SPNET_TRY(pc->mem.alloc(&pc->ybuf, (size_t)pc->sum_s * vbytes));
-  // shared memory per warp: the largest star's solve section and vector, capped
-  {
-    int* mx = counters;
-    SPNET_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(int), s));
-    note_launch();
-    k_solve_need<<<(pc->S + 255) / 256, 256, 0, s>>>(pc->S, pc->pool, pc->star_off, vbytes, mx);
-    int need = 0;
-    SPNET_CUDA_TRY(cudaMemcpyAsync(&need, mx, sizeof(int), cudaMemcpyDeviceToHost, s));
-    SPNET_CUDA_TRY(cudaStreamSynchronize(s));
-    const int cap = 48 * 1024;
-    pc->solve_spw = (int)align_up(need < cap ? need : cap, 16);
-    // the kernel attribute is process-wide: allow the largest stage any
-    // preconditioner may ask for (4 warps x cap)
-    static bool attr_set[64][2] = {};
-    int dev = 0;
-    SPNET_CUDA_TRY(cudaGetDevice(&dev));
-    dev &= 63;
-    const int bytes = 4 * cap;
-    if (vbytes == 8 && !attr_set[dev][1]) {
-      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-      attr_set[dev][1] = true;
-    }
-    if (vbytes == 4 && !attr_set[dev][0]) {
-      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-      attr_set[dev][0] = true;
-    }
-  }
+  SPNET_TRY(pack_sections(pc, tmp));
+  pc->mem.release(pc->pool);
+  pc->pool = nullptr;
   return SPNET_OK;
 }
 

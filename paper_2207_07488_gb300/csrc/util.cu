@@ -81,10 +81,25 @@ void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relax
 bool profiling_on() { return g_prof_on.load(std::memory_order_relaxed) != 0; }
 long long launch_count() { return g_launches.load(); }
 
+// events are created once and reused after every drain, so that recording
+// costs the host as little as possible and the GPU is not left waiting
+static std::vector<cudaEvent_t> g_ev_pool;
+static size_t g_ev_next = 0;
+
+static cudaEvent_t pool_event() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_ev_next == g_ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    g_ev_pool.push_back(e);
+  }
+  return g_ev_pool[g_ev_next++];
+}
+
 ProfScope::ProfScope(int id_, cudaStream_t s_) : id(id_), s(s_) {
   if (!g_prof_on.load(std::memory_order_relaxed)) return;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
+  a = pool_event();
+  b = pool_event();
   cudaEventRecord(a, s);
   active = true;
 }
@@ -113,9 +128,9 @@ static void profile_drain() {
     cudaEventElapsedTime(&ms, r.a, r.b);
     g_prof_n[r.id] += 1;
     g_prof_ms[r.id] += ms;
-    cudaEventDestroy(r.a);
-    cudaEventDestroy(r.b);
   }
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_prof_pending.empty()) g_ev_next = 0;
 }
 
 void profile_read(int id, long long* n, double* ms) {
