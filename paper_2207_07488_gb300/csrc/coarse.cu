@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemv(const T* __restrict__ Z, in
   for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < m0; row += nw) {
     const V* zr = reinterpret_cast<const V*>(Z + row * ld);
     T acc = 0;
+#pragma unroll 4
     for (int64_t c = lane; c < nv; c += 32) {
       const V z = __ldg(&zr[c]);
       const T* zz = reinterpret_cast<const T*>(&z);

@@ -167,6 +167,46 @@ __global__ void __launch_bounds__(256) k_spmv_dir(int64_t n, const int64_t* __re
   }
 }
 
+// Butterfly reduce-scatter of K per-lane values (K a power of two, K <= 32):
+// K-1 + log2(32/K) shuffles instead of 5K.  Afterwards lane L holds the warp
+// total of index rs_index<K>(L) if rs_writer<K>(L).  Fixed order: deterministic.
+template <int K>
+__device__ __forceinline__ double reduce_scatter(double (&v)[K], int lane) {
+#pragma unroll
+  for (int h = K / 2, bit = 16; h >= 1; h >>= 1, bit >>= 1) {
+    const bool upper = (lane & bit) != 0;
+#pragma unroll
+    for (int t = 0; t < h; ++t) {
+      const double send = upper ? v[t] : v[t + h];
+      const double recv = __shfl_xor_sync(0xffffffffu, send, bit);
+      v[t] = (upper ? v[t + h] : v[t]) + recv;
+    }
+  }
+  double s = v[0];
+#pragma unroll
+  for (int bit = 16 / K; bit >= 1; bit >>= 1) s += __shfl_xor_sync(0xffffffffu, s, bit);
+  return s;
+}
+
+template <int K>
+__device__ __forceinline__ int rs_index(int lane) {
+  int idx = 0;
+#pragma unroll
+  for (int h = K / 2, bit = 16; h >= 1; h >>= 1, bit >>= 1)
+    if (lane & bit) idx += h;
+  return idx;
+}
+
+template <int K>
+__device__ __forceinline__ bool rs_writer(int lane) {
+  return (lane & (32 / K - 1)) == 0;
+}
+
+template <int N>
+struct Pow2 {
+  static constexpr int value = N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
+};
+
 // ---------------------------------------------------------------------------
 // update (one warp per element): x += alpha p, r -= alpha q (mode 0) or r as is
 // (mode 1); |r|^2; corner sums E[e][c][a] = sum_{p in e, comp a} phi_c(p) r_p.
@@ -214,12 +254,13 @@ __global__ void __launch_bounds__(256) k_update(int n_elem, int64_t N, const int
         }
       }
     }
+    constexpr int K = Pow2<NC * ND>::value;
+    double red[K];
 #pragma unroll
-    for (int t = 0; t < NC * ND; ++t) {
-      double v = acc[t];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) epart[e * (NC * ND) + t] = v;
-    }
+    for (int t = 0; t < K; ++t) red[t] = t < NC * ND ? acc[t] : 0.0;
+    const double tot = reduce_scatter<K>(red, lane);
+    const int ti = rs_index<K>(lane);
+    if (rs_writer<K>(lane) && ti < NC * ND) epart[e * (NC * ND) + ti] = tot;
   }
   block_partial(rr, partial, sh);
   if (last_block(&sc->cnt[1])) {
@@ -292,7 +333,17 @@ __global__ void __launch_bounds__(256) k_combine(int n_elem, int64_t N, const in
     for (int c = 0; c < NC; ++c) sb[c] = __shfl_sync(0xffffffffu, sl, c);
     const int a0 = elem_ptr[e], a1 = elem_ptr[e + 1];
     for (int i = a0 + lane; i < a1; i += 32) {
+      // every load is issued before any is used (no loads under branches)
       const int a = ND == 1 ? 0 : comp_of[i];
+      const int off = i - a0;
+      double qv[NC], wv[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        qv[c] = __ldg(&q1w[(int64_t)c * N + i]);
+        wv[c] = __ldg(&w[sb[c] >= 0 ? sb[c] + off : 0]);
+      }
+      const double ri = sc ? __ldg(&r[i]) : 0.0;
+      const double zo = sc ? z[i] : 0.0;
       double v = 0.0;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -300,15 +351,13 @@ __global__ void __launch_bounds__(256) k_combine(int n_elem, int64_t N, const in
 #pragma unroll
         for (int b = 1; b < ND; ++b)
           if (b == a) zv = zcv[c * ND + b];
-        v = fma(q1w[(int64_t)c * N + i], zv, v);
+        v = fma(qv[c], zv, v);
       }
-      const int off = i - a0;
 #pragma unroll
-      for (int c = 0; c < NC; ++c)
-        if (sb[c] >= 0) v += w[sb[c] + off];
+      for (int c = 0; c < NC; ++c) v += sb[c] >= 0 ? wv[c] : 0.0;
       if (sc) {
-        s1 = fma(r[i], v, s1);
-        s2 = fma(r[i], z[i], s2);
+        s1 = fma(ri, v, s1);
+        s2 = fma(ri, zo, s2);
       }
       z[i] = v;
     }

@@ -74,7 +74,9 @@ struct StarArgs {
   const int32_t* kcol;
   const double* kval;
   char* scratch;
-  int64_t stride;  // scratch bytes per warp
+  int64_t stride;  // global scratch bytes per warp
+  int64_t hot;     // hot bytes per warp
+  int hot_in_smem; // 1: hot arrays in dynamic shared memory
   int nmax;
   char* pool;
   int64_t pool_cap;
@@ -100,29 +102,34 @@ struct Scratch {
   uint8_t* sel;      // [nmax]
 };
 
-__host__ __device__ inline int64_t scratch_bytes(int nmax) {
-  int64_t o = 0;
-  o += 2ll * nmax * CAP;
-  o += 2ll * ((int64_t)nmax * CAP + CORE_ENTRIES);
+// hot arrays (adjacency, degrees, states, selection), touched in every round:
+// in shared memory when they fit, else with the cold ones in global scratch
+__host__ __device__ inline int64_t hot_bytes(int nmax) {
+  return align_up(2ll * nmax * CAP, 16) + align_up(8ll * nmax, 16) + align_up((int64_t)nmax, 16);
+}
+
+__host__ __device__ inline int64_t cold_bytes(int nmax) {
+  int64_t o = 2ll * ((int64_t)nmax * CAP + CORE_ENTRIES);
   o = align_up(o, 8);
-  o += 4ll * nmax * 2 + 4ll * (nmax + 1) * 5 + nmax;
+  o += 4ll * (nmax + 1) * 6;
   return align_up(o, 256);
 }
 
-__device__ inline Scratch carve(char* base, int nmax) {
+__device__ inline Scratch carve(char* cold, char* hot, int nmax) {
   Scratch s;
   int64_t o = 0;
-  s.nbr = (uint16_t*)(base + o);    o += 2ll * nmax * CAP;
-  s.colent = (uint16_t*)(base + o); o += 2ll * ((int64_t)nmax * CAP + CORE_ENTRIES);
+  s.nbr = (uint16_t*)(hot + o);   o = align_up(o + 2ll * nmax * CAP, 16);
+  s.deg = (int32_t*)(hot + o);    o += 4ll * nmax;
+  s.state = (int32_t*)(hot + o);  o = align_up(o + 4ll * nmax, 16);
+  s.sel = (uint8_t*)(hot + o);
+  o = 0;
+  s.colent = (uint16_t*)(cold + o); o += 2ll * ((int64_t)nmax * CAP + CORE_ENTRIES);
   o = align_up(o, 8);
-  s.deg = (int32_t*)(base + o);      o += 4ll * nmax;
-  s.state = (int32_t*)(base + o);    o += 4ll * nmax;
-  s.posnode = (int32_t*)(base + o);  o += 4ll * (nmax + 1);
-  s.colstart = (int32_t*)(base + o); o += 4ll * (nmax + 1);
-  s.lvl = (int32_t*)(base + o);      o += 4ll * (nmax + 1);
-  s.rcnt = (int32_t*)(base + o);     o += 4ll * (nmax + 1);
-  s.rstart = (int32_t*)(base + o);   o += 4ll * (nmax + 1);
-  s.sel = (uint8_t*)(base + o);
+  s.posnode = (int32_t*)(cold + o);  o += 4ll * (nmax + 1);
+  s.colstart = (int32_t*)(cold + o); o += 4ll * (nmax + 1);
+  s.lvl = (int32_t*)(cold + o);      o += 4ll * (nmax + 1);
+  s.rcnt = (int32_t*)(cold + o);     o += 4ll * (nmax + 1);
+  s.rstart = (int32_t*)(cold + o);   o += 4ll * (nmax + 1);
   return s;
 }
 
@@ -205,9 +212,12 @@ __device__ inline void compact_all(const Scratch& W, int n, int lane) {
 }
 
 __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
+  extern __shared__ __align__(16) char sm_hot[];
   const int lane = threadIdx.x & 31;
   const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const Scratch W = carve(A.scratch + wg * A.stride, A.nmax);
+  char* cold = A.scratch + wg * A.stride;
+  char* hot = A.hot_in_smem ? sm_hot + (threadIdx.x >> 5) * A.hot : cold + cold_bytes(A.nmax);
+  const Scratch W = carve(cold, hot, A.nmax);
   const unsigned FULL = 0xffffffffu;
   for (;;) {
     int s = 0;
@@ -822,14 +832,30 @@ int pc_factor_stars(spnet_pc_s* pc) {
     ~Guard() { a.free_all(); }
   } guard{tmp};
   const int nmax = pc->max_star;
-  const int64_t stride = scratch_bytes(nmax);
-  // warps of the symbolic pass: bounded by the scratch budget (1 GiB) and by the star count
-  int64_t warps = (int64_t)8 * num_sms();
+  const int64_t hot = hot_bytes(nmax);
+  // hot arrays in shared memory when four warps' worth fit in 200 KiB, one
+  // block of four warps per SM at least; otherwise everything in global scratch
+  const int hot_in_smem = 4 * hot <= 200 * 1024 ? 1 : 0;
+  const int64_t stride = cold_bytes(nmax) + (hot_in_smem ? 0 : align_up(hot, 256));
+  int wpb_blocks = hot_in_smem ? (int)((200 * 1024) / (4 * hot)) : 4;  // blocks per SM
+  if (wpb_blocks < 1) wpb_blocks = 1;
+  if (wpb_blocks > 4) wpb_blocks = 4;
+  int64_t warps = (int64_t)4 * wpb_blocks * num_sms();
   int64_t budget = (int64_t)1 << 30;
   if (warps * stride > budget) warps = budget / stride;
   if (warps < 4) warps = 4;
   if (warps > pc->S) warps = pc->S;
   warps = (warps + 3) / 4 * 4;
+  if (hot_in_smem) {
+    static bool attr_set[64] = {};
+    int dev = 0;
+    SPNET_CUDA_TRY(cudaGetDevice(&dev));
+    dev &= 63;
+    if (!attr_set[dev]) {
+      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_symbolic, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr_set[dev] = true;
+    }
+  }
   char* scratch = nullptr;
   SPNET_TRY(tmp.get(&scratch, warps * stride));
   int* counters = nullptr;  // [0] next star, [2..3] pool top (u64)
@@ -859,6 +885,8 @@ int pc_factor_stars(spnet_pc_s* pc) {
     A.kval = pc->K.val;
     A.scratch = scratch;
     A.stride = stride;
+    A.hot = hot;
+    A.hot_in_smem = hot_in_smem;
     A.nmax = nmax;
     A.pool = pc->pool;
     A.pool_cap = cap;
@@ -871,7 +899,7 @@ int pc_factor_stars(spnet_pc_s* pc) {
     A.vbytes = 8;  // the set-up blobs keep FP64 values; the solve sections are packed later
     note_launch();
     ProfScope ps(KID_STAR_SYMBOLIC, s);
-    k_star_symbolic<<<(unsigned)(warps / 4), 128, 0, s>>>(A);
+    k_star_symbolic<<<(unsigned)(warps / 4), 128, hot_in_smem ? (size_t)(4 * hot) : 0, s>>>(A);
     SPNET_CUDA_TRY(cudaGetLastError());
     int h = 0;
     SPNET_CUDA_TRY(cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
