@@ -141,9 +141,9 @@ def kernel_bytes(op, pc, prec_bytes):
     return {
         # values + columns, row pointers (int64), x gathered once, y written
         "spmv": 12 * nnz + 8 * (n + 1) + 8 * n + 8 * n,
-        # factor structure and values, the gather of r and the scatter of w
-        "stars": (S * 16 + 4 * ss + 2 * ss + 2 * (lev + S) + 4 * (ss + S) * 2 + 2 * fnz * 2
-                  + prec_bytes * (2 * fnz + ss) + 8 * ss + 8 * ss),
+        # solve streams (headers, inverse permutations, entries), the gather of r
+        # over every star and the write of w
+        "stars": i.star_stream_bytes + 8 * ss + 8 * ss,
         "coarse": prec_bytes * i.m0 * i.m0 + 16 * i.m0,
         "restrict": n * (8 + 8 * nc) + 8 * i.m0,
         "combine": n * (8 + 8 * nc + 4 + 8 + 8 + 8) + 8 * ss,

@@ -104,7 +104,9 @@ typedef struct {
   int precision, star_set, flexible;
   double setup_ms;      /* device time of setup_preconditioner */
   int64_t device_bytes; /* device memory held by the preconditioner */
-  int64_t reserved[5];
+  int64_t star_stream_bytes; /* bytes one star solve reads from its solve streams
+                                (headers, inverse permutations, entries) */
+  int64_t reserved[4];
 } spnet_pc_info;
 
 /* spnet_assemble -- assemble K on all n_nodes*ndof dofs from an edge list.

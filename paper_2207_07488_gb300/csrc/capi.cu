@@ -236,6 +236,7 @@ int spnet_pc_get_info(spnet_pc_t pc, spnet_pc_info* info) {
   info->flexible = pc->flexible;
   info->setup_ms = pc->setup_ms;
   info->device_bytes = pc->mem.bytes;
+  info->star_stream_bytes = pc->stream_bytes;
   return SPNET_OK;
 }
 

@@ -167,46 +167,6 @@ __global__ void __launch_bounds__(256) k_spmv_dir(int64_t n, const int64_t* __re
   }
 }
 
-// Butterfly reduce-scatter of K per-lane values (K a power of two, K <= 32):
-// K-1 + log2(32/K) shuffles instead of 5K.  Afterwards lane L holds the warp
-// total of index rs_index<K>(L) if rs_writer<K>(L).  Fixed order: deterministic.
-template <int K>
-__device__ __forceinline__ double reduce_scatter(double (&v)[K], int lane) {
-#pragma unroll
-  for (int h = K / 2, bit = 16; h >= 1; h >>= 1, bit >>= 1) {
-    const bool upper = (lane & bit) != 0;
-#pragma unroll
-    for (int t = 0; t < h; ++t) {
-      const double send = upper ? v[t] : v[t + h];
-      const double recv = __shfl_xor_sync(0xffffffffu, send, bit);
-      v[t] = (upper ? v[t + h] : v[t]) + recv;
-    }
-  }
-  double s = v[0];
-#pragma unroll
-  for (int bit = 16 / K; bit >= 1; bit >>= 1) s += __shfl_xor_sync(0xffffffffu, s, bit);
-  return s;
-}
-
-template <int K>
-__device__ __forceinline__ int rs_index(int lane) {
-  int idx = 0;
-#pragma unroll
-  for (int h = K / 2, bit = 16; h >= 1; h >>= 1, bit >>= 1)
-    if (lane & bit) idx += h;
-  return idx;
-}
-
-template <int K>
-__device__ __forceinline__ bool rs_writer(int lane) {
-  return (lane & (32 / K - 1)) == 0;
-}
-
-template <int N>
-struct Pow2 {
-  static constexpr int value = N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
-};
-
 // ---------------------------------------------------------------------------
 // update (one warp per element): x += alpha p, r -= alpha q (mode 0) or r as is
 // (mode 1); |r|^2; corner sums E[e][c][a] = sum_{p in e, comp a} phi_c(p) r_p.

@@ -58,7 +58,8 @@ enum : int {
 struct DevArena {
   cudaStream_t stream = 0;
   std::vector<void*> ptrs;
-  int64_t bytes = 0;
+  std::vector<int64_t> sizes;
+  int64_t bytes = 0;  // bytes currently held
   int alloc(void** p, size_t n);
   template <class T>
   int get(T** p, size_t count) {
@@ -126,8 +127,12 @@ struct spnet_pc_s {
   // coarse space
   int m0 = 0;
   int32_t* cidx = nullptr;     // [n_mesh*ndof]
-  void* Z = nullptr;           // [m0*ldz] A_0^{-1} (float or double by precision), rows padded
+  void* Z = nullptr;           // [m0*ldz] A_0^{-1} during set-up (float or double by precision), rows padded
   int64_t ldz = 0;
+  void* ctiles = nullptr;      // upper CT x CT tiles of Z, packed (the product reads these)
+  void* cpart = nullptr;       // [nt*nt*CT] per row block and tile column: partial products
+  unsigned* ccnt = nullptr;    // [nt] parts written per row block (zero between applications)
+  int ctiles_n = 0;            // nt: tiles per dimension
   double* A0 = nullptr;        // [m0*m0] copy of A_0 if m0 <= A0_KEEP
   // stars
   int S = 0, max_star = 0, max_levels = 0;
@@ -142,16 +147,18 @@ struct spnet_pc_s {
   int32_t* star_n = nullptr;       // [S]
   int32_t* star_lev = nullptr;     // [S]
   int32_t* star_nnz = nullptr;     // [S]
-  char* spool = nullptr;           // packed per-star solve sections, star order
-  int64_t spool_bytes = 0;
-  int64_t* soff = nullptr;         // [S+1] byte offsets of the sections
-  int32_t* blk_star = nullptr;     // [solve_blocks+1] first star of each solve block
-  uint8_t* blk_global = nullptr;   // [solve_blocks] 1: the block's star is solved from global memory
-  int solve_blocks = 0;
+  // solve streams: per-star header (80 B), inverse permutation, entries
+  void* shdr = nullptr;            // [S] headers
+  uint16_t* iperm_star = nullptr;  // [sum_s] local index -> elimination position, at star_ptr
+  uint16_t* emeta = nullptr;       // [n_entries + chunk] column | flags
+  char* ecoef = nullptr;           // [n_entries + chunk] coefficients in the solve precision
+  int64_t n_entries = 0;
+  int64_t stream_bytes = 0;        // bytes one solve reads from the streams
+  int solve_wpb = 0;               // warps (stars) per block of the solve
+  size_t solve_smem = 0;           // its dynamic shared memory per block
   // work vectors (pc order)
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *b = nullptr;
   double *w = nullptr, *rc = nullptr, *zc = nullptr, *partial = nullptr, *vtmp = nullptr;
-  void* ybuf = nullptr;
   double* epart = nullptr;         // [n_elem*nc*ndof] Q1-weighted corner sums of r
   int32_t* ecoarse = nullptr;      // [n_elem*nc*ndof] coarse index at each corner (-1: none)
   int64_t* estar = nullptr;        // [n_elem*nc] base of the element's entries in w (-1: no star)
@@ -284,5 +291,45 @@ void from_pc(spnet_pc_s* pc, const double* pc_vec, double* free_vec);
 int export_item(spnet_pc_s* pc, int what, void* host_buf);
 int pcg_run(spnet_op_s* op, spnet_pc_s* pc, int nrhs, const double* f, const double* g, double* x,
             int use_x0, double rtol, int maxit, int mem, spnet_stats* stats);
+
+// Butterfly reduce-scatter of K per-lane values (K a power of two, K <= 32):
+// K-1 + log2(32/K) shuffles instead of 5K.  Afterwards lane L holds the warp
+// total of index rs_index<K>(L) if rs_writer<K>(L).  Fixed order: deterministic.
+template <int K, class T>
+__device__ __forceinline__ T reduce_scatter(T (&v)[K], int lane) {
+#pragma unroll
+  for (int h = K / 2, bit = 16; h >= 1; h >>= 1, bit >>= 1) {
+    const bool upper = (lane & bit) != 0;
+#pragma unroll
+    for (int t = 0; t < h; ++t) {
+      const T send = upper ? v[t] : v[t + h];
+      const T recv = __shfl_xor_sync(0xffffffffu, send, bit);
+      v[t] = (upper ? v[t + h] : v[t]) + recv;
+    }
+  }
+  T s = v[0];
+#pragma unroll
+  for (int bit = 16 / K; bit >= 1; bit >>= 1) s += __shfl_xor_sync(0xffffffffu, s, bit);
+  return s;
+}
+
+template <int K>
+__device__ __forceinline__ int rs_index(int lane) {
+  int idx = 0;
+#pragma unroll
+  for (int h = K / 2, bit = 16; h >= 1; h >>= 1, bit >>= 1)
+    if (lane & bit) idx += h;
+  return idx;
+}
+
+template <int K>
+__device__ __forceinline__ bool rs_writer(int lane) {
+  return (lane & (32 / K - 1)) == 0;
+}
+
+template <int N>
+struct Pow2 {
+  static constexpr int value = N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
+};
 
 }  // namespace spnet

@@ -524,59 +524,65 @@ __global__ void __launch_bounds__(128) k_star_numeric(int S, char* pool, const i
 }
 
 // ---------------------------------------------------------------------------
-// The solve works on compact per-star sections packed in star order:
-//   header (80 B): n, nlev, nnz, pointer bytes; base of the star in w; the pc
-//                  index of the first dof and the local offset of each of the
-//                  star's 2^d elements
-//   lvl [nlev+1] u16, perm [n] u16, rowptr/colptr [n+1] (u16, or u32 when
-//   nnz > 65535), rowidx/colidx [nnz] u16, then (8-byte aligned) row values,
-//   column values and 1/L_vv in the solve precision; padded to 16 bytes.
-// Stars are grouped into blocks whose sections and vectors fit a shared-memory
-// budget; a block copies its contiguous sections into shared memory with
-// 16-byte loads and each warp then solves one star there: every level step
-// reads shared memory only.
+// Solve streams.  Both triangular solves of a star are written as one stream of
+// entries (column, coefficient), level after level: the forward levels of
+// L y = r in elimination order, then the levels of L^T z = y in reverse.  A row
+// v of a level is a segment of consecutive entries
+//   forward:   (u, -L_vu / L_vv) for the u of row v, then (v, 1 / L_vv)
+//   backward:  (u, -L_uv / L_vv) for the u of column v, then (v, 1 / L_vv)
+// so that the new value is the segment's sum of coefficient * y[column], the
+// diagonal entry last: its column names the row written.  Rows of one level do
+// not read one another, so the sums of a level run in parallel and the update
+// is in place.  Entry metadata (u16): column (14 bits), SEG_END on a row's
+// last entry, LEVEL_END on a level's last entry.
+//
+// A warp solves one star.  It streams the entries through a ring in shared
+// memory (cp.async, RING_CH chunks of 64 entries in flight) and consumes them
+// 32 at a time: every lane multiplies one entry, a segmented shuffle scan sums
+// the segments in a fixed order (deterministic), and the last lane of each
+// segment writes its row.  A window stops at a level's end; a segment cut by
+// the window's end carries its partial sum into the next window.  Only the
+// star's vector (and its inverse permutation) stays in shared memory.
 // ---------------------------------------------------------------------------
-constexpr int SOLVE_WPB = 12;                  // warps (stars) per block
-constexpr int SOLVE_BUDGET = 110 * 1024;       // shared memory per block
-constexpr int SEC_HDR = 80;
+constexpr int STREAM_CHUNK = 64;                // entries per copy group
+constexpr int RING_CH = 4;                      // chunks in the ring
+constexpr int RING_E = STREAM_CHUNK * RING_CH;  // ring entries (power of two)
+constexpr int STREAM_MAX_N = 16383;             // star size the 14-bit columns address
+constexpr unsigned SEG_END = 0x4000u, LEVEL_END = 0x8000u, COL_MASK = 0x3fffu;
+constexpr int STREAM_SMEM = 200 * 1024;         // shared memory budget per block
 
-struct SecLayout {
-  int64_t lvl, perm, rowptr, colptr, rowidx, colidx, rowval, colval, invd, total;
+// per-star header of the solve, 80 bytes
+struct StarHdr {
+  int64_t eoff;   // first entry of the star's stream
+  int64_t wbase;  // first slot of the star in w (star_ptr)
+  int32_t n;      // dofs
+  int32_t ne;     // entries (forward + backward)
+  int32_t es[8];  // pc index of the first dof of each of the 2^d elements, -1 if absent
+  uint16_t eo[9]; // local offset of each element's dofs within the star
+  uint16_t pad[3];
 };
+static_assert(sizeof(StarHdr) == 80, "StarHdr layout");
 
-__host__ __device__ inline SecLayout sec_layout(int n, int nlev, int nnz, int vb) {
-  SecLayout L;
-  const int pw = nnz > 65535 ? 4 : 2;
-  int64_t o = SEC_HDR;
-  L.lvl = o;    o += 2ll * (nlev + 1);
-  L.perm = o;   o += 2ll * n;
-  o = align_up(o, pw);
-  L.rowptr = o; o += (int64_t)pw * (n + 1);
-  L.colptr = o; o += (int64_t)pw * (n + 1);
-  L.rowidx = o; o += 2ll * nnz;
-  L.colidx = o; o += 2ll * nnz;
-  o = align_up(o, 8);
-  L.rowval = o; o += (int64_t)vb * nnz;
-  L.colval = o; o += (int64_t)vb * nnz;
-  L.invd = o;   o += (int64_t)vb * n;
-  L.total = align_up(o, 16);
-  return L;
+// shared memory of one warp: ring (metadata, coefficients), y, inverse permutation, header
+__host__ __device__ inline int64_t stream_warp_bytes(int vb, int ymax) {
+  return align_up(2ll * RING_E, 16) + align_up((int64_t)vb * RING_E, 16) + align_up((int64_t)vb * ymax, 16) +
+         align_up(2ll * ymax, 16) + (int64_t)sizeof(StarHdr);
 }
 
-__global__ void k_sec_sizes(int S, const char* pool, const int64_t* star_off, int vb, int64_t* sz,
-                            int32_t* yb) {
+__global__ void k_stream_sizes(int S, const char* pool, const int64_t* star_off, int64_t* sz) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
     const int32_t* h = (const int32_t*)(pool + star_off[s]);
-    sz[s] = sec_layout(h[0], h[1], h[2], vb).total;
-    yb[s] = (int32_t)align_up((int64_t)vb * h[0], 16);
+    sz[s] = align_up(2ll * ((int64_t)h[0] + h[2]), 8);
   }
 }
 
-// warp per star: setup blob (FP64) -> compact section (vb-byte values)
+// warp per star: set-up blob (FP64 factor) -> header, inverse permutation, entry stream
 template <class T>
-__global__ void k_sec_pack(int S, Mesh m, const char* pool, const int64_t* star_off,
-                           const int32_t* star_mesh, const int32_t* elem_ptr, const int64_t* star_ptr,
-                           char* spool, const int64_t* soff) {
+__global__ void k_stream_pack(int S, Mesh m, const char* __restrict__ pool, const int64_t* __restrict__ star_off,
+                              const int32_t* __restrict__ star_mesh, const int32_t* __restrict__ elem_ptr,
+                              const int64_t* __restrict__ star_ptr, const int64_t* __restrict__ eoff,
+                              StarHdr* __restrict__ hdr, uint16_t* __restrict__ iperm,
+                              uint16_t* __restrict__ emeta, T* __restrict__ ecoef) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
@@ -584,247 +590,261 @@ __global__ void k_sec_pack(int S, Mesh m, const char* pool, const int64_t* star_
     const int32_t* hb = (const int32_t*)blob;
     const int n = hb[0], nlev = hb[1], nnz = hb[2];
     const BlobLayout B = blob_layout(n, nlev, nnz, 8);
-    const SecLayout L = sec_layout(n, nlev, nnz, sizeof(T));
-    char* sec = spool + soff[s];
-    if (lane == 0) {
-      int32_t* h = (int32_t*)sec;
-      h[0] = n;
-      h[1] = nlev;
-      h[2] = nnz;
-      h[3] = nnz > 65535 ? 4 : 2;
-      *(int64_t*)(sec + 16) = star_ptr[s];
-      int32_t* es = (int32_t*)(sec + 24);
-      uint16_t* eo = (uint16_t*)(sec + 56);
-      const StarElems se = star_elems(m, star_mesh[s], elem_ptr);
-      for (int cp = 0; cp < 8; ++cp) es[cp] = (cp < m.nc && se.e[cp] >= 0) ? elem_ptr[se.e[cp]] : -1;
-      for (int cp = 0; cp <= 8; ++cp) eo[cp] = (uint16_t)(cp <= m.nc ? se.off[cp < m.nc ? cp : m.nc] : n);
-    }
-    const uint16_t* lvl = (const uint16_t*)(blob + B.lvl);
-    const uint16_t* perm = (const uint16_t*)(blob + B.perm);
     const uint32_t* rowptr = (const uint32_t*)(blob + B.rowptr);
     const uint32_t* colptr = (const uint32_t*)(blob + B.colptr);
+    const uint16_t* lvl = (const uint16_t*)(blob + B.lvl);
+    const uint16_t* perm = (const uint16_t*)(blob + B.perm);
     const uint16_t* rowidx = (const uint16_t*)(blob + B.rowidx);
     const uint16_t* colidx = (const uint16_t*)(blob + B.colidx);
-    const double* v64 = (const double*)(blob + B.v64);  // row values, column values, 1/L_vv
-    for (int q = lane; q <= nlev; q += 32) ((uint16_t*)(sec + L.lvl))[q] = lvl[q];
-    for (int q = lane; q < n; q += 32) ((uint16_t*)(sec + L.perm))[q] = perm[q];
-    if (nnz > 65535) {
-      for (int q = lane; q <= n; q += 32) {
-        ((uint32_t*)(sec + L.rowptr))[q] = rowptr[q];
-        ((uint32_t*)(sec + L.colptr))[q] = colptr[q];
-      }
-    } else {
-      for (int q = lane; q <= n; q += 32) {
-        ((uint16_t*)(sec + L.rowptr))[q] = (uint16_t)rowptr[q];
-        ((uint16_t*)(sec + L.colptr))[q] = (uint16_t)colptr[q];
+    const double* rowv = (const double*)(blob + B.v64);
+    const double* colv = rowv + nnz;
+    const double* invd = colv + nnz;
+    const int64_t e0 = eoff[s], wb = star_ptr[s];
+    if (lane == 0) {
+      StarHdr h;
+      h.eoff = e0;
+      h.wbase = wb;
+      h.n = n;
+      h.ne = 2 * (n + nnz);
+      const StarElems se = star_elems(m, star_mesh[s], elem_ptr);
+      for (int cp = 0; cp < 8; ++cp) h.es[cp] = (cp < m.nc && se.e[cp] >= 0) ? elem_ptr[se.e[cp]] : -1;
+      for (int cp = 0; cp <= 8; ++cp) h.eo[cp] = (uint16_t)(cp <= m.nc ? se.off[cp < m.nc ? cp : m.nc] : n);
+      h.pad[0] = h.pad[1] = h.pad[2] = 0;
+      hdr[s] = h;
+    }
+    for (int pos = lane; pos < n; pos += 32) iperm[wb + perm[pos]] = (uint16_t)pos;
+    const int64_t ef = (int64_t)n + nnz;  // forward entries
+    for (int l = 0; l < nlev; ++l) {
+      const int v0 = lvl[l], v1 = lvl[l + 1];
+      // backward segments of this level start after the levels above it
+      const int64_t bl = ef + (int64_t)(nnz - colptr[v1]) + (n - v1);
+      for (int v = v0 + lane; v < v1; v += 32) {
+        const double dv = invd[v];
+        const unsigned last = v == v1 - 1 ? LEVEL_END : 0u;
+        int64_t o = e0 + rowptr[v] + v;
+        for (uint32_t q = rowptr[v]; q < rowptr[v + 1]; ++q, ++o) {
+          emeta[o] = rowidx[q];
+          ecoef[o] = (T)(-rowv[q] * dv);
+        }
+        emeta[o] = (uint16_t)(v | SEG_END | last);
+        ecoef[o] = (T)dv;
+        o = e0 + bl + (colptr[v] - colptr[v0]) + (v - v0);
+        for (uint32_t q = colptr[v]; q < colptr[v + 1]; ++q, ++o) {
+          emeta[o] = colidx[q];
+          ecoef[o] = (T)(-colv[q] * dv);
+        }
+        emeta[o] = (uint16_t)(v | SEG_END | last);
+        ecoef[o] = (T)dv;
       }
     }
-    for (int q = lane; q < nnz; q += 32) {
-      ((uint16_t*)(sec + L.rowidx))[q] = rowidx[q];
-      ((uint16_t*)(sec + L.colidx))[q] = colidx[q];
-    }
-    T* vals = (T*)(sec + L.rowval);  // rowval, colval, invd are contiguous
-    for (int q = lane; q < 2 * nnz + n; q += 32) vals[q] = (T)v64[q];
   }
 }
 
-template <class T, class PT>
-__device__ __forceinline__ void solve_section(const char* sec, T* y, const double* __restrict__ r,
-                                              double* __restrict__ w, int lane) {
-  const int32_t* h = (const int32_t*)sec;
-  const int n = h[0], nlev = h[1], nnz = h[2];
-  const SecLayout L = sec_layout(n, nlev, nnz, sizeof(T));
-  const int64_t base = *(const int64_t*)(sec + 16);
-  const int32_t* es = (const int32_t*)(sec + 24);
-  const uint16_t* eo = (const uint16_t*)(sec + 56);
-  const uint16_t* lvl = (const uint16_t*)(sec + L.lvl);
-  const uint16_t* perm = (const uint16_t*)(sec + L.perm);
-  const PT* rowptr = (const PT*)(sec + L.rowptr);
-  const PT* colptr = (const PT*)(sec + L.colptr);
-  const uint16_t* rowidx = (const uint16_t*)(sec + L.rowidx);
-  const uint16_t* colidx = (const uint16_t*)(sec + L.colidx);
-  const T* rowv = (const T*)(sec + L.rowval);
-  const T* colv = (const T*)(sec + L.colval);
-  const T* invd = (const T*)(sec + L.invd);
-  // gather r over the star: position -> element-concatenated index -> pc index
-  constexpr int GU = 4;
-  for (int p0 = 0; p0 < n; p0 += 32 * GU) {
-    double rv[GU];
-#pragma unroll
-    for (int u = 0; u < GU; ++u) {
-      const int pos = p0 + u * 32 + lane;
-      rv[u] = 0.0;
-      if (pos < n) {
-        const int t = perm[pos];
-        int cp = 0;
-#pragma unroll
-        for (int c = 1; c < 8; ++c)
-          if (t >= (int)eo[c] && es[c] >= 0) cp = c;
-        rv[u] = __ldg(&r[es[cp] + (t - (int)eo[cp])]);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < GU; ++u) {
-      const int pos = p0 + u * 32 + lane;
-      if (pos < n) y[pos] = (T)rv[u];
-    }
-  }
-  __syncwarp();
-  for (int l = 0; l < nlev; ++l) {
-    const int v1 = lvl[l + 1];
-    for (int v = lvl[l] + lane; v < v1; v += 32) {
-      T acc = y[v];
-      const int q1 = rowptr[v + 1];
-      for (int q = rowptr[v]; q < q1; ++q) acc -= rowv[q] * y[rowidx[q]];
-      y[v] = acc * invd[v];
-    }
-    __syncwarp();
-  }
-  for (int l = nlev - 1; l >= 0; --l) {
-    const int v1 = lvl[l + 1];
-    for (int v = lvl[l] + lane; v < v1; v += 32) {
-      T acc = y[v];
-      const int q1 = colptr[v + 1];
-      for (int q = colptr[v]; q < q1; ++q) acc -= colv[q] * y[colidx[q]];
-      y[v] = acc * invd[v];
-    }
-    __syncwarp();
-  }
-  for (int pos = lane; pos < n; pos += 32) w[base + perm[pos]] = (double)y[pos];
+__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async_8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most `pending` of this thread's copy groups are still in flight
+__device__ __forceinline__ void cp_async_wait_pending(int pending) {
+  switch (pending) {
+    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+  }
+}
+static_assert(RING_CH == 4, "cp_async_wait_pending covers up to RING_CH - 1 pending groups");
 
-// block b solves stars blk[b] .. blk[b+1]-1; a block flagged "global" (one star
-// too large for the budget) reads its section from global memory and keeps y
-// in the global scratch
+// chunk k of a star's stream into ring slot k % RING_CH: lane copies entries 2*lane, 2*lane+1
 template <class T>
-__global__ void __launch_bounds__(SOLVE_WPB * 32) k_star_solve(const int32_t* __restrict__ blk,
-                                                                const uint8_t* __restrict__ blk_global,
-                                                                const char* __restrict__ spool,
-                                                                const int64_t* __restrict__ soff,
-                                                                const int64_t* __restrict__ star_ptr,
-                                                                const double* __restrict__ r,
-                                                                double* __restrict__ w, T* ybuf,
-                                                                const int* done) {
+__device__ __forceinline__ void stream_fetch(int k, int lane, const uint16_t* emeta, const T* ecoef, int64_t e0,
+                                             uint16_t* rmeta, T* rcoef) {
+  const int64_t g = e0 + (int64_t)k * STREAM_CHUNK + 2 * lane;
+  const int sl = (k & (RING_CH - 1)) * STREAM_CHUNK + 2 * lane;
+  cp_async_4(rmeta + sl, emeta + g);
+  if (sizeof(T) == 4) cp_async_8(rcoef + sl, ecoef + g);
+  else cp_async_16(rcoef + sl, ecoef + g);
+  cp_async_commit();
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_star_stream(int S, int wpb, int ymax, const StarHdr* __restrict__ hdr,
+                                                     const uint16_t* __restrict__ emeta, const T* __restrict__ ecoef,
+                                                     const uint16_t* __restrict__ iperm, const double* __restrict__ r,
+                                                     double* __restrict__ w, const int* done) {
   extern __shared__ int4 smem4[];
   if (done && *done) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int s0 = blk[blockIdx.x], s1 = blk[blockIdx.x + 1];
-  const int64_t g0 = soff[s0], g1 = soff[s1];
-  if (blk_global[blockIdx.x]) {
-    for (int s = s0 + wid; s < s1; s += SOLVE_WPB) {
-      const char* sec = spool + soff[s];
-      const int nnz = ((const int32_t*)sec)[2];
-      T* y = ybuf + star_ptr[s];
-      if (nnz > 65535) solve_section<T, uint32_t>(sec, y, r, w, lane);
-      else solve_section<T, uint16_t>(sec, y, r, w, lane);
+  const int s = blockIdx.x * wpb + wid;
+  if (wid >= wpb || s >= S) return;  // no block-wide barrier follows
+  constexpr unsigned FULL = 0xffffffffu;
+  char* base = (char*)smem4 + (int64_t)wid * stream_warp_bytes((int)sizeof(T), ymax);
+  uint16_t* rmeta = (uint16_t*)base;
+  T* rcoef = (T*)(base + align_up(2ll * RING_E, 16));
+  T* y = (T*)((char*)rcoef + align_up((int64_t)sizeof(T) * RING_E, 16));
+  uint16_t* ip = (uint16_t*)((char*)y + align_up((int64_t)sizeof(T) * ymax, 16));
+  StarHdr* h = (StarHdr*)((char*)ip + align_up(2ll * ymax, 16));
+  if (lane < (int)(sizeof(StarHdr) / 4)) ((int32_t*)h)[lane] = __ldg(((const int32_t*)(hdr + s)) + lane);
+  __syncwarp();
+  const int64_t e0 = h->eoff, wb = h->wbase;
+  const int n = h->n, ne = h->ne;
+  const int nch = (ne + STREAM_CHUNK - 1) / STREAM_CHUNK;
+  int F = 0;
+  for (; F < nch && F < RING_CH; ++F) stream_fetch<T>(F, lane, emeta, ecoef, e0, rmeta, rcoef);
+  // gather r over the star in local order (element ranges: coalesced), place it at the elimination position
+  constexpr int GU = 4;
+  for (int t0 = 0; t0 < n; t0 += 32 * GU) {
+    double rv[GU];
+    int pv[GU];
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const int t = t0 + u * 32 + lane;
+      rv[u] = 0.0;
+      pv[u] = 0;
+      if (t < n) {
+        int cp = 0;
+#pragma unroll
+        for (int c = 1; c < 8; ++c) cp += t >= (int)h->eo[c] ? 1 : 0;
+        rv[u] = __ldg(&r[h->es[cp] + (t - (int)h->eo[cp])]);
+        pv[u] = __ldg(&iperm[wb + t]);
+      }
     }
-    return;
+#pragma unroll
+    for (int u = 0; u < GU; ++u) {
+      const int t = t0 + u * 32 + lane;
+      if (t < n) {
+        y[pv[u]] = (T)rv[u];
+        ip[t] = (uint16_t)pv[u];
+      }
+    }
   }
-  const int n4 = (int)((g1 - g0) >> 4);
-  const int4* src = (const int4*)(spool + g0);
-  for (int q = threadIdx.x; q < n4; q += blockDim.x) smem4[q] = __ldg(&src[q]);
-  __syncthreads();
-  const char* sm = (const char*)smem4;
-  for (int s = s0 + wid; s < s1; s += SOLVE_WPB) {
-    // y of this star after all sections, behind the vectors of the block's earlier stars
-    int64_t yo = g1 - g0;
-    for (int t = s0; t < s; ++t) yo += align_up((int64_t)sizeof(T) * ((const int32_t*)(sm + (soff[t] - g0)))[0], 16);
-    const char* sec = sm + (soff[s] - g0);
-    const int nnz = ((const int32_t*)sec)[2];
-    T* y = (T*)(sm + yo);
-    if (nnz > 65535) solve_section<T, uint32_t>(sec, y, r, w, lane);
-    else solve_section<T, uint16_t>(sec, y, r, w, lane);
+  // the stream: forward levels, then backward levels
+  int c = 0;
+  T carry = T(0);
+  while (c < ne) {
+    const int cw = c / STREAM_CHUNK;
+    for (; F < nch && F < cw + RING_CH; ++F) stream_fetch<T>(F, lane, emeta, ecoef, e0, rmeta, rcoef);
+    const int kneed = min((c + 31) / STREAM_CHUNK, nch - 1);
+    cp_async_wait_pending(F - 1 - kneed);
+    __syncwarp();
+    const int sl = (c + lane) & (RING_E - 1);
+    const unsigned mt = rmeta[sl];
+    const T a = rcoef[sl];
+    const unsigned lend = __ballot_sync(FULL, (mt & LEVEL_END) != 0u);
+    int cnt = lend ? __ffs(lend) : 32;
+    cnt = min(cnt, ne - c);
+    const bool act = lane < cnt;
+    const int col = (int)(mt & COL_MASK);
+    T v = T(0);
+    if (act) v = a * y[col];
+    if (lane == 0) v += carry;
+    const bool se = act && (mt & SEG_END) != 0u;
+    const unsigned ends = __ballot_sync(FULL, se);
+    const unsigned heads = (ends << 1) | 1u;
+    const int seg0 = 31 - __clz(heads & (FULL >> (31 - lane)));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T t = __shfl_up_sync(FULL, v, o);
+      if (lane - o >= seg0) v += t;
+    }
+    if (se) y[col] = v;
+    carry = __shfl_sync(FULL, v, cnt - 1);
+    if ((ends >> (cnt - 1)) & 1u) carry = T(0);
+    c += cnt;
+    __syncwarp();
   }
+  for (int t = lane; t < n; t += 32) w[wb + t] = (double)y[ip[t]];
 }
 
 void launch_star_solve(spnet_pc_s* pc, const double* r, const int* done, cudaStream_t s) {
   if (pc->S == 0) return;
   note_launch();
   ProfScope ps(KID_STARS, s);
+  const int wpb = pc->solve_wpb;
+  const unsigned grid = (unsigned)((pc->S + wpb - 1) / wpb);
   if (pc->precision == SPNET_PREC_FP64)
-    k_star_solve<double><<<pc->solve_blocks, SOLVE_WPB * 32, SOLVE_BUDGET, s>>>(
-        pc->blk_star, pc->blk_global, pc->spool, pc->soff, pc->star_ptr, r, pc->w, (double*)pc->ybuf, done);
+    k_star_stream<double><<<grid, wpb * 32, pc->solve_smem, s>>>(pc->S, wpb, pc->max_star, (const StarHdr*)pc->shdr, pc->emeta,
+                                                                  (const double*)pc->ecoef, pc->iperm_star, r, pc->w,
+                                                                  done);
   else
-    k_star_solve<float><<<pc->solve_blocks, SOLVE_WPB * 32, SOLVE_BUDGET, s>>>(
-        pc->blk_star, pc->blk_global, pc->spool, pc->soff, pc->star_ptr, r, pc->w, (float*)pc->ybuf, done);
+    k_star_stream<float><<<grid, wpb * 32, pc->solve_smem, s>>>(pc->S, wpb, pc->max_star, (const StarHdr*)pc->shdr, pc->emeta,
+                                                                 (const float*)pc->ecoef, pc->iperm_star, r, pc->w,
+                                                                 done);
 }
 
-// compact sections in star order, grouped into blocks by the shared-memory budget
-static int pack_sections(spnet_pc_s* pc, DevArena& tmp) {
+// headers, inverse permutations and entry streams of all stars
+static int pack_streams(spnet_pc_s* pc, DevArena& tmp) {
   cudaStream_t s = pc->op->stream;
   const int S = pc->S;
   const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
   int64_t* sz = nullptr;
-  int32_t* yb = nullptr;
+  int64_t* eoff = nullptr;
   SPNET_TRY(tmp.get(&sz, S + 1));
-  SPNET_TRY(tmp.get(&yb, S));
-  SPNET_TRY(pc->mem.get(&pc->soff, S + 1));
+  SPNET_TRY(tmp.get(&eoff, S + 1));
   note_launch();
-  k_sec_sizes<<<(S + 255) / 256, 256, 0, s>>>(S, pc->pool, pc->star_off, vb, sz, yb);
-  SPNET_TRY(scan_exclusive64(sz, pc->soff, S, s, tmp));
-  std::vector<int64_t> hoff(S + 1);
-  std::vector<int32_t> hyb(S);
-  SPNET_CUDA_TRY(cudaMemcpyAsync(hoff.data(), pc->soff, sizeof(int64_t) * (S + 1), cudaMemcpyDeviceToHost, s));
-  SPNET_CUDA_TRY(cudaMemcpyAsync(hyb.data(), yb, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, s));
+  k_stream_sizes<<<(S + 255) / 256, 256, 0, s>>>(S, pc->pool, pc->star_off, sz);
+  SPNET_TRY(scan_exclusive64(sz, eoff, S, s, tmp));
+  int64_t total = 0;
+  SPNET_CUDA_TRY(cudaMemcpyAsync(&total, eoff + S, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   SPNET_CUDA_TRY(cudaStreamSynchronize(s));
-  pc->spool_bytes = hoff[S];
-  SPNET_TRY(pc->mem.get(&pc->spool, hoff[S] > 0 ? hoff[S] : 16));
+  // a chunk read may run up to one chunk past the last star's entries
+  const int64_t cap = total + STREAM_CHUNK;
+  pc->n_entries = total;
+  SPNET_TRY(pc->mem.alloc(&pc->shdr, (size_t)S * sizeof(StarHdr)));
+  SPNET_TRY(pc->mem.get(&pc->iperm_star, pc->sum_s > 0 ? pc->sum_s : 1));
+  SPNET_TRY(pc->mem.get(&pc->emeta, cap));
+  SPNET_TRY(pc->mem.get(&pc->ecoef, cap * vb));
+  SPNET_CUDA_TRY(cudaMemsetAsync(pc->emeta, 0, sizeof(uint16_t) * cap, s));
+  SPNET_CUDA_TRY(cudaMemsetAsync(pc->ecoef, 0, (size_t)vb * cap, s));
+  pc->stream_bytes = (int64_t)S * (int64_t)sizeof(StarHdr) + 2 * pc->sum_s + (2ll + vb) * total;
   note_launch();
   if (vb == 8)
-    k_sec_pack<double><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_mesh,
-                                                   pc->elem_ptr, pc->star_ptr, pc->spool, pc->soff);
+    k_stream_pack<double><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_mesh,
+                                                      pc->elem_ptr, pc->star_ptr, eoff, (StarHdr*)pc->shdr,
+                                                      pc->iperm_star, pc->emeta, (double*)pc->ecoef);
   else
-    k_sec_pack<float><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_mesh,
-                                                  pc->elem_ptr, pc->star_ptr, pc->spool, pc->soff);
-  // greedy grouping in star order
-  std::vector<int32_t> blk;
-  std::vector<uint8_t> glob;
-  int st = 0;
-  while (st < S) {
-    int e = st;
-    int64_t bytes = 0;
-    while (e < S && e - st < SOLVE_WPB) {
-      const int64_t add = (hoff[e + 1] - hoff[e]) + hyb[e];
-      if (bytes + add > SOLVE_BUDGET) break;
-      bytes += add;
-      ++e;
-    }
-    blk.push_back(st);
-    if (e == st) {  // one star beyond the budget: solved from global memory
-      glob.push_back(1);
-      e = st + 1;
-    } else {
-      glob.push_back(0);
-    }
-    st = e;
-  }
-  blk.push_back(S);
-  pc->solve_blocks = (int)glob.size();
-  SPNET_TRY(pc->mem.get(&pc->blk_star, blk.size()));
-  SPNET_TRY(pc->mem.get(&pc->blk_global, glob.size()));
-  SPNET_CUDA_TRY(cudaMemcpyAsync(pc->blk_star, blk.data(), sizeof(int32_t) * blk.size(), cudaMemcpyHostToDevice, s));
-  SPNET_CUDA_TRY(cudaMemcpyAsync(pc->blk_global, glob.data(), glob.size(), cudaMemcpyHostToDevice, s));
-  SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+    k_stream_pack<float><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_mesh,
+                                                     pc->elem_ptr, pc->star_ptr, eoff, (StarHdr*)pc->shdr,
+                                                     pc->iperm_star, pc->emeta, (float*)pc->ecoef);
+  SPNET_CUDA_TRY(cudaGetLastError());
+  // warps per block: as many as the shared-memory budget holds, at most eight
+  const int64_t wb = stream_warp_bytes(vb, pc->max_star);
+  int wpb = (int)(STREAM_SMEM / wb);
+  wpb = wpb > 8 ? 8 : wpb;
+  if (wpb < 1) return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: a star too large for the solve's shared memory");
+  pc->solve_wpb = wpb;
+  pc->solve_smem = (size_t)(wpb * wb);
   static bool attr_set[64][2] = {};
   int dev = 0;
   SPNET_CUDA_TRY(cudaGetDevice(&dev));
   dev &= 63;
   if (vb == 8 && !attr_set[dev][1]) {
-    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_BUDGET));
+    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_stream<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, STREAM_SMEM));
     attr_set[dev][1] = true;
   }
   if (vb == 4 && !attr_set[dev][0]) {
-    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_BUDGET));
+    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_stream<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, STREAM_SMEM));
     attr_set[dev][0] = true;
   }
+  SPNET_CUDA_TRY(cudaStreamSynchronize(s));
   return SPNET_OK;
 }
 
 int pc_factor_stars(spnet_pc_s* pc) {
   cudaStream_t s = pc->op->stream;
   if (pc->S == 0) return SPNET_OK;
-  if (pc->max_star > 65535)
-    return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: a star holds more than 65535 dofs");
+  if (pc->max_star > STREAM_MAX_N)
+    return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: a star holds more than " +
+                                           std::to_string(STREAM_MAX_N) + " dofs");
   DevArena tmp;
   tmp.stream = s;
   struct Guard {
@@ -937,11 +957,8 @@ int pc_factor_stars(spnet_pc_s* pc) {
     pc->total_levels += lev[i];
     pc->max_levels = lev[i] > pc->max_levels ? lev[i] : pc->max_levels;
   }
-  // vectors of stars solved from global memory, then the packed solve sections;
-  // the set-up blobs are released
-  const int vbytes = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
-  SPNET_TRY(pc->mem.alloc(&pc->ybuf, (size_t)pc->sum_s * vbytes));
-  SPNET_TRY(pack_sections(pc, tmp));
+  // the solve streams; the set-up blobs are released
+  SPNET_TRY(pack_streams(pc, tmp));
   pc->mem.release(pc->pool);
   pc->pool = nullptr;
   return SPNET_OK;

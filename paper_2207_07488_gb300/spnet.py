@@ -65,7 +65,8 @@ class PcInfo(C.Structure):
                 ("n_stars", C.c_int), ("max_star", C.c_int), ("sum_star", C.c_int64),
                 ("factor_nnz", C.c_int64), ("total_levels", C.c_int64), ("max_levels", C.c_int),
                 ("precision", C.c_int), ("star_set", C.c_int), ("flexible", C.c_int),
-                ("setup_ms", C.c_double), ("device_bytes", C.c_int64), ("reserved", C.c_int64 * 5)]
+                ("setup_ms", C.c_double), ("device_bytes", C.c_int64), ("star_stream_bytes", C.c_int64),
+                ("reserved", C.c_int64 * 4)]
 
 
 _lib = None
