@@ -133,22 +133,29 @@ def peaks():
 # algorithmic bytes of one launch of the iteration kernels
 # ---------------------------------------------------------------------------
 def kernel_bytes(op, pc, prec_bytes):
+    """Algorithmic bytes of one launch of each iteration kernel: every array the
+    kernel must touch, counted once per pass (the star gather counts each star's
+    copy of r)."""
     n = op.info.n_free
     nnz = op.info.nnz_ff
     i = pc.info
-    S, ss, fnz, lev = i.n_stars, i.sum_star, i.factor_nnz, i.total_levels
-    nc = 2 ** op.dim
+    ss = i.sum_star
+    d = op.dim
+    nc = 2 ** d
+    vb = prec_bytes                      # factor, coarse inverse and star result bytes
+    xb = 8 if prec_bytes == 8 else 4     # local coordinates read by update / combine
+    nt = (i.m0 + 127) // 128
     return {
-        # values + columns, row pointers (int64), x gathered once, y written
-        "spmv": 12 * nnz + 8 * (n + 1) + 8 * n + 8 * n,
-        # solve streams (headers, inverse permutations, entries), the gather of r
-        # over every star and the write of w
-        "stars": i.star_stream_bytes + 8 * ss + 8 * ss,
-        "coarse": prec_bytes * i.m0 * i.m0 + 16 * i.m0,
-        "restrict": n * (8 + 8 * nc) + 8 * i.m0,
-        "combine": n * (8 + 8 * nc + 4 + 8 + 8 + 8) + 8 * ss,
-        "update": 8 * n * 6,
-        "direction": 8 * n * 3,
+        # values + columns, row pointers (int64), z gathered, p and q read and written
+        "spmv": 12 * nnz + 8 * (n + 1) + 8 * n + 32 * n,
+        # headers, inverse permutations and window records; r over every star; w written
+        "stars": i.star_stream_bytes + 8 * ss + vb * ss,
+        # the packed upper tiles of A_0^{-1}; r_c formed from the corner sums
+        "coarse": vb * (nt * (nt + 1) // 2) * 128 * 128 + 8 * 8 * i.m0 + 8 * i.m0,
+        # x, p, r, q read, x and r written, local coordinates, corner sums written
+        "update": 48 * n + xb * d * n + 8 * nc * i.n_elem,
+        # local coordinates, star results, r and the old z read, z written
+        "combine": xb * d * n + vb * ss + 24 * n,
     }
 
 

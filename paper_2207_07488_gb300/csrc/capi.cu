@@ -78,7 +78,13 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
   int rc;
   if ((rc = pc_setup_structure(pc))) return bail(rc);
   pc->G = 4 * num_sms();
+  pc->PG = 16 * num_sms();
   pc->spmv_lanes = choose_spmv_lanes(pc->K);
+  {  // one row group per warp in a single pass, capped at 64 blocks per SM
+    const int64_t want = (pc->N * pc->spmv_lanes + 255) / 256;
+    const int64_t cap = 64ll * num_sms();
+    pc->spmv_blocks = (int)(want < 1 ? 1 : want > cap ? cap : want);
+  }
   // coarse space: Galerkin matrix and its inverse
   if (pc->m0 > 0) {
     double* A0 = nullptr;
@@ -96,10 +102,11 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
   const int64_t N = pc->N;
   if ((rc = pc->mem.get(&pc->x, N)) || (rc = pc->mem.get(&pc->r, N)) || (rc = pc->mem.get(&pc->p, N)) ||
       (rc = pc->mem.get(&pc->q, N)) || (rc = pc->mem.get(&pc->z, N)) || (rc = pc->mem.get(&pc->b, N)) ||
-      (rc = pc->mem.get(&pc->vtmp, N)) || (rc = pc->mem.get(&pc->w, pc->sum_s > 0 ? pc->sum_s : 1)) ||
+      (rc = pc->mem.get(&pc->vtmp, N)) || (rc = pc->mem.alloc(&pc->w, (size_t)(pc->sum_s > 0 ? pc->sum_s : 1) * (pc->precision == SPNET_PREC_FP64 ? 8 : 4))) ||
       (rc = pc->mem.get(&pc->rc, pc->m0 > 0 ? pc->m0 : 1)) ||
       (rc = pc->mem.get(&pc->zc, pc->m0 > 0 ? pc->m0 : 1)) ||
-      (rc = pc->mem.get(&pc->partial, 5 * pc->G)) || (rc = pc->mem.get(&pc->scal, 1)) ||
+      (rc = pc->mem.get(&pc->partial, 5 * pc->PG)) || (rc = pc->mem.get(&pc->pspmv, pc->spmv_blocks)) ||
+      (rc = pc->mem.get(&pc->scal, 1)) ||
       (rc = pc->mem.get(&pc->epart, (size_t)pc->n_elem * pc->nc * pc->ndof)))
     return bail(rc);
   cudaMemsetAsync(pc->scal, 0, sizeof(Scal), s);
@@ -321,7 +328,7 @@ static int prolong_fn(spnet_pc_s* pc, const double* zc, double* z) {
   cudaStream_t s = pc->op->stream;
   if (pc->m0 > 0)
     SPNET_CUDA_TRY(cudaMemcpyAsync(pc->zc, zc, sizeof(double) * pc->m0, cudaMemcpyDeviceToDevice, s));
-  launch_combine(pc, pc->vtmp, pc->z, 1, 0, 0, s);
+  launch_combine(pc, pc->vtmp, pc->z, 1, 0, 0, s, 1);  // the stand-alone prolongation: FP64
   from_pc(pc, pc->z, z);
   return SPNET_OK;
 }

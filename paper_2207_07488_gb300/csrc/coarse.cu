@@ -5,10 +5,12 @@
 //   A_ij -> A_ij - A_iK P A_Kj,  A_iK -> A_iK P,  A_Kj -> P A_Kj,  A_KK -> -P
 // with P = A_KK^{-1}; after sweeping every block the matrix holds -A^{-1}.
 // For an SPD matrix the pivot blocks are Schur complements, hence SPD, so no
-// pivoting is needed.  Each application is then one dense matrix-vector
-// product that every SM can share, instead of two dependent triangular solves.
+// pivoting is needed.  Each application is then one dense symmetric
+// matrix-vector product that every SM can share, instead of two dependent
+// triangular solves.
 // The sweeps and the product run in FP64 or, for the mixed-precision
 // preconditioner, in FP32.
+#include <climits>
 #include <cmath>
 
 #include "spnet_internal.cuh"
@@ -18,78 +20,99 @@ namespace spnet {
 constexpr int NB = 64;  // pivot block
 
 // invert the SPD pivot block D = Z[k0.., k0..] (kb x kb) into P by scalar sweeps
-// in the arithmetic of T; 1024 threads, 2 x 2 entries each
+// in the arithmetic of T.  256 threads, each holding a 4 x 4 tile of D in
+// registers (thread (tr, tc) owns rows 4tr.., columns 4tc..); row and column p
+// of each step pass through shared memory, double-buffered so that one barrier
+// per step suffices.  Every thread forms 1 / D_pp itself.
 template <class T>
-__global__ void __launch_bounds__(1024) k_pivot_inverse(T* Z, int64_t ld, int k0, int kb, T* P, int* flags) {
-  __shared__ T D[NB][NB + 1];
-  __shared__ T col[NB], row[NB];
-  __shared__ T ipiv;
-  const int tj = threadIdx.x, ti = threadIdx.y;  // 32 x 32
-  for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 2; ++b) {
-      const int i = ti + 32 * a, j = tj + 32 * b;
-      D[i][j] = (i < kb && j < kb) ? Z[(int64_t)(k0 + i) * ld + (k0 + j)] : (T)0;
+__global__ void __launch_bounds__(256) k_pivot_inverse(T* Z, int64_t ld, int k0, int kb, T* P, int* flags) {
+  __shared__ T rowp[2][NB], colp[2][NB];
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+  T d[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = 4 * tr + a, j = 4 * tc + b;
+      d[a][b] = (i < kb && j < kb) ? Z[(int64_t)(k0 + i) * ld + (k0 + j)] : (T)0;
     }
-  __syncthreads();
-  for (int p = 0; p < kb; ++p) {
-    if (ti == 0 && tj == 0) {
-      T piv = D[p][p];
+  bool bad = false;
+  for (int q = 0; q < NB / 4; ++q) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int p = 4 * q + a;
+      if (p >= kb) break;  // uniform
+      const int buf = p & 1;
+      if (tr == q) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) rowp[buf][4 * tc + b] = d[a][b];
+      }
+      if (tc == q) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) colp[buf][4 * tr + b] = d[b][a];
+      }
+      __syncthreads();
+      T piv = colp[buf][p];
       if (!(piv > (T)0)) {
-        atomicOr(flags, FLAG_COARSE_SPD);
+        bad = true;
         piv = (T)1;
       }
-      ipiv = (T)1 / piv;
-    }
-    if (ti == 0) {
-      row[tj] = D[p][tj];
-      row[tj + 32] = D[p][tj + 32];
-    }
-    if (tj == 0) {
-      col[ti] = D[ti][p];
-      col[ti + 32] = D[ti + 32][p];
-    }
-    __syncthreads();
-    const T ip = ipiv;
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 2; ++b) {
-        const int i = ti + 32 * a, j = tj + 32 * b;
-        if (i < kb && j < kb) {
-          if (i != p && j != p) D[i][j] -= col[i] * row[j] * ip;
-          else if (i == p && j == p) D[i][j] = -ip;
-          else if (i == p) D[i][j] = row[j] * ip;
-          else D[i][j] = col[i] * ip;
-        }
+      const T ip = (T)1 / piv;
+      T cv[4], rv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cv[u] = colp[buf][4 * tr + u];
+        rv[u] = rowp[buf][4 * tc + u];
       }
-    __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const bool ri = 4 * tr + u == p, cj = 4 * tc + v == p;
+          if (!ri && !cj) d[u][v] -= cv[u] * rv[v] * ip;
+          else if (ri && cj) d[u][v] = -ip;
+          else if (ri) d[u][v] = rv[v] * ip;
+          else d[u][v] = cv[u] * ip;
+        }
+    }
   }
-  for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 2; ++b) {
-      const int i = ti + 32 * a, j = tj + 32 * b;
-      P[i * NB + j] = (i < kb && j < kb) ? -D[i][j] : (T)0;
+  if (bad && threadIdx.x == 0) atomicOr(flags, FLAG_COARSE_SPD);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = 4 * tr + a, j = 4 * tc + b;
+      P[i * NB + j] = (i < kb && j < kb) ? -d[a][b] : (T)0;
     }
 }
 
-// R = Z[k0:k0+kb, :] (copy of the pivot rows), Tm = P R
+// R = Z[k0:k0+kb, :] (copy of the pivot rows), Tm = P R.  A block takes 16
+// columns; thread (g, c) loads column c's kb pivot-row entries and forms rows
+// 4g..4g+3 of P R for it.
 template <class T>
-__global__ void __launch_bounds__(128) k_panel(const T* Z, int64_t m0, int64_t ld, int k0, int kb,
+__global__ void __launch_bounds__(256) k_panel(const T* Z, int64_t m0, int64_t ld, int k0, int kb,
                                                const T* P, T* R, T* Tm) {
-  __shared__ T sP[NB][NB];
+  __shared__ T sP[NB][NB + 1];
   for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) sP[q / NB][q % NB] = P[q];
   __syncthreads();
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < m0;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    T col[NB];
+  const int g = threadIdx.x >> 4;
+  const int64_t c = (int64_t)blockIdx.x * 16 + (threadIdx.x & 15);
+  if (c >= m0) return;
+  T col[NB];
 #pragma unroll
-    for (int t = 0; t < NB; ++t) col[t] = t < kb ? Z[(int64_t)(k0 + t) * ld + c] : (T)0;
+  for (int t = 0; t < NB; ++t) col[t] = t < kb ? Z[(int64_t)(k0 + t) * ld + c] : (T)0;
 #pragma unroll
-    for (int t = 0; t < NB; ++t)
-      if (t < kb) R[(int64_t)t * m0 + c] = col[t];
-    for (int t = 0; t < kb; ++t) {
-      T acc = 0;
+  for (int u = 0; u < 4; ++u) {
+    const int t = 4 * g + u;
+    if (t < kb) R[(int64_t)t * m0 + c] = Z[(int64_t)(k0 + t) * ld + c];
+  }
 #pragma unroll
-      for (int u = 0; u < NB; ++u) acc += sP[t][u] * col[u];
-      Tm[(int64_t)t * m0 + c] = acc;
-    }
+  for (int u = 0; u < 4; ++u) {
+    const int t = 4 * g + u;
+    T acc = 0;
+#pragma unroll
+    for (int v = 0; v < NB; ++v) acc += sP[t][v] * col[v];
+    if (t < kb) Tm[(int64_t)t * m0 + c] = acc;
   }
 }
 
@@ -246,9 +269,9 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
   for (int k0 = 0; k0 < m0; k0 += NB) {
     const int kb = (int)((m0 - k0) < NB ? (m0 - k0) : NB);
     note_launch();
-    k_pivot_inverse<T><<<1, dim3(32, 32), 0, s>>>(Z, ld, k0, kb, P, pc->op->dflags);
+    k_pivot_inverse<T><<<1, 256, 0, s>>>(Z, ld, k0, kb, P, pc->op->dflags);
     note_launch();
-    k_panel<T><<<(unsigned)((m0 + 127) / 128), 128, 0, s>>>(Z, m0, ld, k0, kb, P, R, Tm);
+    k_panel<T><<<(unsigned)((m0 + 15) / 16), 256, 0, s>>>(Z, m0, ld, k0, kb, P, R, Tm);
     note_launch();
     ProfScope ps(KID_SWEEP, s);
     k_sweep<T, TB><<<tiles, 256, smem, s>>>(Z, m0, ld, k0, kb, P, R, Tm);
@@ -265,64 +288,247 @@ int pc_coarse_invert(spnet_pc_s* pc, double* A0) {
   return invert_impl<float>(pc, A0);
 }
 
-// z_c = Z r_c: r_c staged in shared memory, one warp per row, 16-byte loads of Z
-template <class T, class V>
-__global__ void __launch_bounds__(256) k_coarse_gemv(const T* __restrict__ Z, int64_t m0, int64_t ld,
-                                                     const double* __restrict__ rc,
-                                                     double* __restrict__ zc, const int* done) {
-  extern __shared__ __align__(16) char sm_raw[];
-  T* srv = reinterpret_cast<T*>(sm_raw);
-  if (done && *done) return;
-  for (int64_t c = threadIdx.x; c < ld; c += blockDim.x) srv[c] = c < m0 ? (T)rc[c] : (T)0;
-  __syncthreads();
-  constexpr int VW = sizeof(V) / sizeof(T);
-  const int lane = threadIdx.x & 31;
-  const int64_t nv = ld / VW;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < m0; row += nw) {
-    const V* zr = reinterpret_cast<const V*>(Z + row * ld);
-    T acc = 0;
-#pragma unroll 4
-    for (int64_t c = lane; c < nv; c += 32) {
-      const V z = __ldg(&zr[c]);
-      const T* zz = reinterpret_cast<const T*>(&z);
-#pragma unroll
-      for (int u = 0; u < VW; ++u) acc += zz[u] * srv[c * VW + u];
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) zc[row] = (double)acc;
+// ---------------------------------------------------------------------------
+// z_c = Z r_c with Z = A_0^{-1} symmetric: only the upper tiles (I <= J) of
+// CT x CT are kept, packed tile after tile (row-major inside a tile, zero
+// padded past m0), which halves the bytes of every application.  One block per
+// stored tile reads it once and uses it twice:
+//   row sums     Z_IJ r_J   -> part[I][J]   (the contribution of column block J to z_I)
+//   column sums  Z_IJ^T r_I -> part[J][I]   (I < J: the contribution of row block I to z_J)
+// Every part[R][K] has one writer.  A counter per row block R counts the parts
+// written; the block that writes the last one sums part[R][0..nt-1] in K order
+// (deterministic) into z_c and resets the counter for the next application.
+// ---------------------------------------------------------------------------
+constexpr int CT = 128;
+
+__host__ __device__ inline int64_t n_upper_tiles(int nt) { return (int64_t)nt * (nt + 1) / 2; }
+
+// linear upper-tile index -> (I, J), row-major over I <= J
+__device__ inline void upper_tile(int t, int nt, int* I, int* J) {
+  int i = 0;
+  while (t >= nt - i) {
+    t -= nt - i;
+    ++i;
+  }
+  *I = i;
+  *J = i + t;
+}
+
+template <class T>
+__global__ void k_pack_tiles(const T* __restrict__ Z, int64_t m0, int64_t ld, int nt, T* __restrict__ tiles) {
+  int I, J;
+  upper_tile(blockIdx.x, nt, &I, &J);
+  T* out = tiles + (int64_t)blockIdx.x * CT * CT;
+  for (int q = threadIdx.x; q < CT * CT; q += blockDim.x) {
+    const int64_t i = (int64_t)I * CT + q / CT, j = (int64_t)J * CT + q % CT;
+    out[q] = (i < m0 && j < m0) ? Z[i * ld + j] : (T)0;
   }
 }
 
+template <class T>
+struct Vec4 {
+  T v[4];
+};
+
+__device__ __forceinline__ Vec4<float> load4(const float* p) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  return Vec4<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Vec4<double> load4(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return Vec4<double>{{a.x, a.y, b.x, b.y}};
+}
+
+// r_c[ci] = (R_0 r)[ci] from the element corner sums E[e][c][a] around the mesh
+// node of coarse dof ci (the restriction of Section 2.3): rtab[ci][cp] is the
+// offset of E[e][c][a] for the element e at position cp around the node, -1
+// where there is none; the same terms in the same order as the stand-alone
+// restriction
+__device__ __forceinline__ double restrict_one(int ci, const int32_t* __restrict__ rtab,
+                                               const double* __restrict__ epart) {
+  const int4 t0 = __ldg(reinterpret_cast<const int4*>(rtab + 8ll * ci));
+  const int4 t1 = __ldg(reinterpret_cast<const int4*>(rtab + 8ll * ci) + 1);
+  const int ix[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+  double v[8];
+#pragma unroll
+  for (int cp = 0; cp < 8; ++cp) v[cp] = ix[cp] >= 0 ? __ldg(&epart[ix[cp]]) : 0.0;
+  double s = 0.0;
+#pragma unroll
+  for (int cp = 0; cp < 8; ++cp)
+    if (ix[cp] >= 0) s += v[cp];
+  return s;
+}
+
+// 256 threads: warp w takes tile rows [16w, 16w + 16), lane l columns [4l, 4l + 4).
+// The input is r_c itself (rc != null) or, fused with the restriction, the
+// element corner sums (rc == null).
+template <class T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_coarse_symv(const T* __restrict__ tiles, int nt, int64_t m0,
+                                                     const double* __restrict__ rc,
+                                                     const double* __restrict__ epart,
+                                                     const int32_t* __restrict__ rtab,
+                                                     T* __restrict__ part,
+                                                     unsigned* __restrict__ cnt, double* __restrict__ zc,
+                                                     const int* done) {
+  constexpr int RW = CT / 8;                  // rows per warp
+  constexpr int RB = 8;                       // rows loaded per batch
+  __shared__ T sI[CT], sJ[CT];
+  __shared__ T scol[8][CT];
+  __shared__ int red[2];
+  if (done && *done) return;
+  int I, J;
+  upper_tile(blockIdx.x, nt, &I, &J);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const T* Zt = tiles + (int64_t)blockIdx.x * CT * CT + (int64_t)(wid * RW) * CT + 4 * lane;
+  Vec4<T> v[RB];
+#pragma unroll
+  for (int k = 0; k < RB; ++k) v[k] = load4(Zt + (int64_t)k * CT);
+  {
+    const bool first = threadIdx.x < CT;
+    const int64_t i = (int64_t)(first ? I : J) * CT + (threadIdx.x & (CT - 1));
+    T val = (T)0;
+    if (i < m0) val = (T)(rc ? rc[i] : restrict_one((int)i, rtab, epart));
+    if (first) sI[threadIdx.x] = val;
+    else sJ[threadIdx.x - CT] = val;
+  }
+  __syncthreads();
+  T rj[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) rj[u] = sJ[4 * lane + u];
+  T rowp[RW];
+  T col[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int b = 0; b < RW; b += RB) {
+    if (b > 0) {
+#pragma unroll
+      for (int k = 0; k < RB; ++k) v[k] = load4(Zt + (int64_t)(b + k) * CT);
+    }
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+      const T ri = sI[wid * RW + b + k];
+      T acc = v[k].v[0] * rj[0];
+#pragma unroll
+      for (int u = 1; u < 4; ++u) acc += v[k].v[u] * rj[u];
+      rowp[b + k] = acc;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) col[u] += v[k].v[u] * ri;
+    }
+  }
+  const T tot = reduce_scatter<RW>(rowp, lane);
+  if (rs_writer<RW>(lane)) part[((int64_t)I * nt + J) * CT + wid * RW + rs_index<RW>(lane)] = tot;
+  if (I != J) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) scol[wid][4 * lane + u] = col[u];
+    __syncthreads();
+    if (threadIdx.x < CT) {
+      T sum = scol[0][threadIdx.x];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) sum += scol[w][threadIdx.x];
+      part[((int64_t)J * nt + I) * CT + threadIdx.x] = sum;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    red[0] = atomicAdd(&cnt[I], 1u) == (unsigned)(nt - 1) ? 1 : 0;
+    red[1] = (I != J && atomicAdd(&cnt[J], 1u) == (unsigned)(nt - 1)) ? 1 : 0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    if (!red[side]) continue;  // uniform over the block
+    __threadfence();
+    const int R = side == 0 ? I : J;
+    if (threadIdx.x < CT) {
+      const int64_t i = (int64_t)R * CT + threadIdx.x;
+      const T* pr = part + (int64_t)R * nt * CT + threadIdx.x;
+      double sum = 0.0;
+      // eight independent loads in flight, summed in K order
+      for (int K0 = 0; K0 < nt; K0 += 8) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = K0 + u < nt ? __ldcg(pr + (int64_t)(K0 + u) * CT) : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (K0 + u < nt) sum += (double)v[u];
+      }
+      if (i < m0) zc[i] = sum;
+    }
+    if (threadIdx.x == 0) cnt[R] = 0u;
+  }
+}
+
+// z_c = A_0^{-1} r_c; with rc == null, r_c = R_0 r is formed from the element
+// corner sums of the last update (restriction fused into the product)
 void launch_coarse_apply(spnet_pc_s* pc, const double* rc, double* zc, const int* done,
                          cudaStream_t s) {
   if (pc->m0 == 0) return;
-  int blocks = 2 * num_sms();
-  const int64_t rows_blocks = (pc->m0 + 7) / 8;
-  if (blocks > rows_blocks) blocks = (int)rows_blocks;
-  const size_t vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
-  const size_t smem = vb * (size_t)pc->ldz;
+  const unsigned tiles = (unsigned)n_upper_tiles(pc->ctiles_n);
   note_launch();
   ProfScope ps(KID_COARSE, s);
   if (pc->precision == SPNET_PREC_FP64)
-    k_coarse_gemv<double, double2><<<blocks, 256, smem, s>>>((const double*)pc->Z, pc->m0, pc->ldz, rc, zc, done);
+    k_coarse_symv<double><<<tiles, 256, 0, s>>>((const double*)pc->ctiles, pc->ctiles_n, pc->m0, rc, pc->epart,
+                                                 pc->rtab, (double*)pc->cpart, pc->ccnt, zc, done);
   else
-    k_coarse_gemv<float, float4><<<blocks, 256, smem, s>>>((const float*)pc->Z, pc->m0, pc->ldz, rc, zc, done);
+    k_coarse_symv<float><<<tiles, 256, 0, s>>>((const float*)pc->ctiles, pc->ctiles_n, pc->m0, rc, pc->epart,
+                                                pc->rtab, (float*)pc->cpart, pc->ccnt, zc, done);
+}
+
+// rtab[ci][cp]: offset of the corner sum of the element at position cp around
+// the mesh node of coarse dof ci (corner nc-1-cp of that element), -1 if none
+__global__ void k_restrict_table(int64_t nmc, Mesh m, int ndof, const int32_t* __restrict__ cidx,
+                                 int32_t* __restrict__ rtab) {
+  for (int64_t ka = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ka < nmc; ka += (int64_t)gridDim.x * blockDim.x) {
+    const int ci = cidx[ka];
+    if (ci < 0) continue;
+    const int k = (int)(ka / ndof), a = (int)(ka % ndof);
+    int km[3];
+    mesh_multi(m, k, km);
+    for (int cp = 0; cp < 8; ++cp) {
+      int off = -1;
+      if (cp < m.nc) {
+        const int e = elem_around(m, km, cp);
+        if (e >= 0) off = (int)(((int64_t)e * m.nc + (m.nc - 1 - cp)) * ndof + a);
+      }
+      rtab[8ll * ci + cp] = off;
+    }
+  }
+}
+
+// pack the upper tiles of Z, release the full matrix, allocate the parts and counters
+template <class T>
+static int pack_coarse_tiles(spnet_pc_s* pc) {
+  cudaStream_t s = pc->op->stream;
+  const int nt = (int)((pc->m0 + CT - 1) / CT);
+  const int64_t nti = n_upper_tiles(nt);
+  T* tiles = nullptr;
+  T* part = nullptr;
+  SPNET_TRY(pc->mem.get(&tiles, nti * CT * CT));
+  SPNET_TRY(pc->mem.get(&part, (int64_t)nt * nt * CT));
+  SPNET_TRY(pc->mem.get(&pc->ccnt, nt));
+  SPNET_CUDA_TRY(cudaMemsetAsync(pc->ccnt, 0, sizeof(unsigned) * nt, s));
+  const int64_t nmc = (int64_t)pc->n_mesh * pc->ndof;
+  if ((int64_t)pc->n_elem * pc->nc * pc->ndof > INT32_MAX)
+    return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: too many element corner sums for 32-bit offsets");
+  SPNET_TRY(pc->mem.get(&pc->rtab, 8ll * pc->m0));
+  note_launch();
+  k_restrict_table<<<(unsigned)((nmc + 255) / 256), 256, 0, s>>>(nmc, mesh_of_pc(pc), pc->ndof, pc->cidx, pc->rtab);
+  note_launch();
+  k_pack_tiles<T><<<(unsigned)nti, 256, 0, s>>>((const T*)pc->Z, pc->m0, pc->ldz, nt, tiles);
+  SPNET_CUDA_TRY(cudaGetLastError());
+  pc->mem.release(pc->Z);
+  pc->Z = nullptr;
+  pc->ctiles = tiles;
+  pc->cpart = part;
+  pc->ctiles_n = nt;
+  return SPNET_OK;
 }
 
 int coarse_gemv_prepare(spnet_pc_s* pc) {
   if (pc->m0 == 0) return SPNET_OK;
-  const size_t vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
-  const size_t smem = vb * (size_t)pc->ldz;
-  if (smem > 220 * 1024)
-    return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: coarse space too large for the staged product");
-  if (smem > 48 * 1024) {
-    if (pc->precision == SPNET_PREC_FP64)
-      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    else
-      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv<float, float4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
-  return SPNET_OK;
+  if (pc->precision == SPNET_PREC_FP64) return pack_coarse_tiles<double>(pc);
+  return pack_coarse_tiles<float>(pc);
 }
 
 }  // namespace spnet

@@ -192,12 +192,15 @@ void launch_spmv(const Csr& A, const double* x, double* y, double* partial, int 
   }
 }
 
+// lanes per row: one thread per row for the short rows of networks (a few
+// entries), a few lanes per row as rows get longer
 int choose_spmv_lanes(const Csr& A) {
   double avg = A.n > 0 ? (double)A.nnz / (double)A.n : 1.0;
-  if (avg <= 4.5) return 2;
-  if (avg <= 9) return 4;
-  if (avg <= 24) return 8;
-  if (avg <= 48) return 16;
+  if (avg <= 6) return 1;
+  if (avg <= 12) return 2;
+  if (avg <= 24) return 4;
+  if (avg <= 48) return 8;
+  if (avg <= 96) return 16;
   return 32;
 }
 

@@ -1,13 +1,13 @@
 // Preconditioned conjugate gradients (Section 4.2) on the free dofs in pc
 // order, and the restriction / combination steps of B (Section 4.1).
 //
-// One iteration is six kernels; the star solves run on a second stream beside
-// the restriction and the coarse solve:
+// One iteration is five kernels; the star solves run on a second stream beside
+// the coarse solve:
 //   spmv_dir  p = z + beta p;  q = A z + beta q  (= A p);  (p, q) -> alpha
 //   update    x += alpha p; r -= alpha q; |r|^2 -> stop test; per element the
 //             Q1-weighted sums of r at its 2^d corners
-//   restrict  r_c = R_0 r from the element sums         | stars  w_j = A_j^{-1} E_j^T r
-//   coarse    z_c = A_0^{-1} r_c                        |
+//   coarse    z_c = A_0^{-1} R_0 r, R_0 r formed      | stars  w_j = A_j^{-1} E_j^T r
+//             from the element sums in each block     |
 //   combine   z = R_0^T z_c + sum_j E_j w_j; (r, z) [and (r, z_old)] -> beta
 // Each reduction is finished by the last block of its kernel (fixed order:
 // bitwise reproducible), which publishes the scalar for the next kernel.
@@ -115,7 +115,7 @@ __global__ void k_residual(int64_t N, const double* b, const double* q, double* 
 }
 
 // ---------------------------------------------------------------------------
-// spmv_dir: p = z + beta p, q = A z + beta q, partial (p, q); last block: alpha
+// spmv_dir: p = z + beta p, q = A z + beta q, block partials of (p, q)
 // ---------------------------------------------------------------------------
 template <int L>
 __global__ void __launch_bounds__(256) k_spmv_dir(int64_t n, const int64_t* __restrict__ ptr,
@@ -135,6 +135,15 @@ __global__ void __launch_bounds__(256) k_spmv_dir(int64_t n, const int64_t* __re
   for (int64_t base = gwarp * RPW; base < n; base += nwarps * RPW) {
     const int64_t row = base + lane / L;
     const bool valid = row < n;
+    // the row's own entries of z, p, q depend on nothing: load them first
+    double zr = 0.0, pr = 0.0, qr = 0.0;
+    if (valid && sub == 0) {
+      zr = z[row];
+      if (beta != 0.0) {
+        pr = p[row];
+        qr = q[row];
+      }
+    }
     double s = 0.0;
     if (valid) {
       const int64_t a = ptr[row], b = ptr[row + 1];
@@ -143,97 +152,101 @@ __global__ void __launch_bounds__(256) k_spmv_dir(int64_t n, const int64_t* __re
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, L);
     if (valid && sub == 0) {
-      double pn, qn;
-      if (beta == 0.0) {
-        pn = z[row];
-        qn = s;
-      } else {
-        pn = fma(beta, p[row], z[row]);
-        qn = fma(beta, q[row], s);
-      }
+      const double pn = beta == 0.0 ? zr : fma(beta, pr, zr);
+      const double qn = beta == 0.0 ? s : fma(beta, qr, s);
       p[row] = pn;
       q[row] = qn;
       dot = fma(pn, qn, dot);
     }
   }
-  block_partial(dot, partial, sh);
-  if (last_block(&sc->cnt[0])) {
-    double pq = block_sum(partial, gridDim.x, sh);
-    if (threadIdx.x == 0) {
-      sc->pq = pq;
-      sc->alpha = sc->rz / pq;
-      sc->cnt[0] = 0;
-    }
-  }
+  block_partial(dot, partial, sh);  // summed by every block of the update (alpha)
 }
 
 // ---------------------------------------------------------------------------
 // update (one warp per element): x += alpha p, r -= alpha q (mode 0) or r as is
-// (mode 1); |r|^2; corner sums E[e][c][a] = sum_{p in e, comp a} phi_c(p) r_p.
-// Last block: |r|^2 and, in mode 0, the iteration count and the stop test.
+// (mode 1); block partials of |r|^2; corner sums E[e][c][a] = sum_{p in e,
+// comp a} phi_c(p) r_p.
 // ---------------------------------------------------------------------------
-template <int NC, int ND>
-__global__ void __launch_bounds__(256) k_update(int n_elem, int64_t N, const int32_t* __restrict__ elem_ptr,
+template <int NC, int ND, class CT>
+__global__ void __launch_bounds__(256, ND == 1 ? 4 : 2) k_update(int n_elem, int64_t N, const int32_t* __restrict__ elem_ptr,
                                                 const int8_t* __restrict__ comp_of,
-                                                const double* __restrict__ q1w, double* __restrict__ x,
+                                                const CT* __restrict__ xi, double* __restrict__ x,
                                                 double* __restrict__ r, const double* __restrict__ p,
                                                 const double* __restrict__ q, double* __restrict__ epart,
-                                                double* partial, Scal* sc, int mode) {
+                                                const double* __restrict__ ppq, int npq, double* partial,
+                                                Scal* sc, int mode) {
+  constexpr int D = NC == 4 ? 2 : 3;
   __shared__ double sh[32];
   if (mode == 0 && sc->done) return;
-  const double alpha = mode == 0 ? sc->alpha : 0.0;
+  // alpha = (r, z) / (p, q): every block sums the SpMV's partials in the same order
+  const double alpha = mode == 0 ? sc->rz / block_sum(ppq, npq, sh) : 0.0;
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double rr = 0.0;
   for (int64_t e = gwarp; e < n_elem; e += nwarps) {
-    double acc[NC * ND];
+    CT acc[NC * ND];
 #pragma unroll
-    for (int t = 0; t < NC * ND; ++t) acc[t] = 0.0;
+    for (int t = 0; t < NC * ND; ++t) acc[t] = CT(0);
     const int a0 = elem_ptr[e], a1 = elem_ptr[e + 1];
-    for (int i = a0 + lane; i < a1; i += 32) {
-      double v;
-      if (mode == 0) {
-        x[i] = fma(alpha, p[i], x[i]);
-        v = fma(-alpha, q[i], r[i]);
-        r[i] = v;
-      } else {
-        v = r[i];
+    for (int i0 = a0; i0 < a1; i0 += 64) {
+      // two dofs per lane; every load (from a valid address) before any use
+      int ii[2];
+      bool ok[2];
+      double xv[2], pv[2], rv[2], qv[2];
+      CT t[2][3];
+      int cm[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        ii[h] = i0 + 32 * h + lane;
+        ok[h] = ii[h] < a1;
+        const int i = ok[h] ? ii[h] : a0;
+        rv[h] = r[i];
+        if (mode == 0) {
+          xv[h] = x[i];
+          pv[h] = p[i];
+          qv[h] = q[i];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) t[h][a] = a < D ? __ldg(&xi[(int64_t)a * N + i]) : CT(0);
+        cm[h] = ND == 1 ? 0 : comp_of[i];
       }
-      rr = fma(v, v, rr);
-      const int a = ND == 1 ? 0 : comp_of[i];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const double wv = q1w[(int64_t)c * N + i] * v;
-        if (ND == 1) {
-          acc[c] += wv;
+      for (int h = 0; h < 2; ++h) {
+        if (!ok[h]) continue;
+        double v;
+        if (mode == 0) {
+          x[ii[h]] = fma(alpha, pv[h], xv[h]);
+          v = fma(-alpha, qv[h], rv[h]);
+          r[ii[h]] = v;
         } else {
+          v = rv[h];
+        }
+        rr = fma(v, v, rr);
+        CT w[NC];
+        q1_from_xi<NC>(t[h], w);
+        const CT vc = (CT)v;
 #pragma unroll
-          for (int b = 0; b < ND; ++b)
-            if (b == a) acc[c * ND + b] += wv;
+        for (int c = 0; c < NC; ++c) {
+          const CT wv = w[c] * vc;
+          if (ND == 1) {
+            acc[c] += wv;
+          } else {  // selects, not an index: the accumulators stay in registers
+#pragma unroll
+            for (int b2 = 0; b2 < ND; ++b2) acc[c * ND + b2] += b2 == cm[h] ? wv : CT(0);
+          }
         }
       }
     }
     constexpr int K = Pow2<NC * ND>::value;
-    double red[K];
+    CT red[K];
 #pragma unroll
-    for (int t = 0; t < K; ++t) red[t] = t < NC * ND ? acc[t] : 0.0;
-    const double tot = reduce_scatter<K>(red, lane);
+    for (int t = 0; t < K; ++t) red[t] = t < NC * ND ? acc[t] : CT(0);
+    const CT tot = reduce_scatter<K>(red, lane);
     const int ti = rs_index<K>(lane);
-    if (rs_writer<K>(lane) && ti < NC * ND) epart[e * (NC * ND) + ti] = tot;
+    if (rs_writer<K>(lane) && ti < NC * ND) epart[e * (NC * ND) + ti] = (double)tot;
   }
-  block_partial(rr, partial, sh);
-  if (last_block(&sc->cnt[1])) {
-    double t = block_sum(partial, gridDim.x, sh);
-    if (threadIdx.x == 0) {
-      sc->rr = t;
-      if (mode == 0) {
-        sc->iter += 1;
-        if (sqrt(t) <= sc->rtol * sqrt(sc->bb) || sc->iter >= sc->maxit) sc->done = 1;
-      }
-      sc->cnt[1] = 0;
-    }
-  }
+  block_partial(rr, partial, sh);  // |r|^2, summed by the last block of the combine
 }
 
 // r_c = R_0 r from the corner sums of the elements around each mesh node
@@ -260,17 +273,20 @@ __global__ void k_restrict(int n_mesh, Mesh m, int ndof, const double* __restric
 // z = [R_0^T z_c] + [sum_j E_j w_j], one warp per element: the element's
 // coarse values z_c at its corners and the bases of its entries in the star
 // results are loaded once and held in registers; partials (r, z) and
-// (r, z_old); last block: beta
-template <int NC, int ND>
-__global__ void __launch_bounds__(256) k_combine(int n_elem, int64_t N, const int32_t* __restrict__ elem_ptr,
+// (r, z_old); last block: beta and, in a PCG step, |r|^2 from the update's
+// partials, the iteration count and the stop test
+template <int NC, int ND, class CT, class WS>
+__global__ void __launch_bounds__(128, ND == 1 ? 7 : 4) k_combine(int n_elem, int64_t N, const int32_t* __restrict__ elem_ptr,
                                                  const int8_t* __restrict__ comp_of,
-                                                 const double* __restrict__ q1w,
+                                                 const CT* __restrict__ xi,
                                                  const int32_t* __restrict__ ecoarse,
                                                  const int64_t* __restrict__ estar,
-                                                 const double* __restrict__ zc, const double* __restrict__ w,
+                                                 const double* __restrict__ zc, const WS* __restrict__ w,
                                                  const double* __restrict__ r, double* __restrict__ z,
-                                                 double* part1, double* part2, int with_coarse,
-                                                 int with_stars, Scal* sc, int flexible, int first) {
+                                                 double* part1, double* part2, const double* __restrict__ prr,
+                                                 int nrr, int with_coarse, int with_stars, Scal* sc,
+                                                 int flexible, int first) {
+  constexpr int D = NC == 4 ? 2 : 3;
   __shared__ double sh[32];
   if (sc && sc->done) return;
   const int lane = threadIdx.x & 31;
@@ -278,48 +294,58 @@ __global__ void __launch_bounds__(256) k_combine(int n_elem, int64_t N, const in
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double s1 = 0.0, s2 = 0.0;
   for (int64_t e = gwarp; e < n_elem; e += nwarps) {
-    double zl = 0.0;
-    long long sl = -1;
+    CT zl = CT(0);
+    int sl = -1;  // star bases fit 32 bits (checked at set-up)
     if (lane < NC * ND && with_coarse) {
       const int ci = ecoarse[e * (NC * ND) + lane];
-      if (ci >= 0) zl = zc[ci];
+      if (ci >= 0) zl = (CT)zc[ci];
     }
-    if (lane < NC && with_stars) sl = estar[e * NC + lane];
-    double zcv[NC * ND];
-    long long sb[NC];
-#pragma unroll
-    for (int t = 0; t < NC * ND; ++t) zcv[t] = __shfl_sync(0xffffffffu, zl, t);
+    if (lane < NC && with_stars) sl = (int)estar[e * NC + lane];
+    // lane t keeps the coarse value of corner-component t; a dof fetches its
+    // corners' values by shuffles (per-lane source: the dof's component)
+    int sb[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) sb[c] = __shfl_sync(0xffffffffu, sl, c);
     const int a0 = elem_ptr[e], a1 = elem_ptr[e + 1];
-    for (int i = a0 + lane; i < a1; i += 32) {
-      // every load is issued before any is used (no loads under branches)
-      const int a = ND == 1 ? 0 : comp_of[i];
-      const int off = i - a0;
-      double qv[NC], wv[NC];
+    constexpr int U = 1;  // dofs per lane and pass (more would spill under the 64-register bound)
+    for (int i0 = a0; i0 < a1; i0 += 32 * U) {
+      // every load (from a valid address) before any use
+      int ii[U];
+      bool ok[U];
+      CT t[U][3], wv[U][NC];
+      double rv[U], zo[U];
+      int cm[U];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        qv[c] = __ldg(&q1w[(int64_t)c * N + i]);
-        wv[c] = __ldg(&w[sb[c] >= 0 ? sb[c] + off : 0]);
+      for (int h = 0; h < U; ++h) {
+        ii[h] = i0 + 32 * h + lane;
+        ok[h] = ii[h] < a1;
+        const int i = ok[h] ? ii[h] : a0;
+        const int off = i - a0;
+        cm[h] = ND == 1 ? 0 : comp_of[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) t[h][a] = a < D ? __ldg(&xi[(int64_t)a * N + i]) : CT(0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) wv[h][c] = (CT)__ldg(&w[sb[c] >= 0 ? sb[c] + off : 0]);
+        rv[h] = sc ? __ldg(&r[i]) : 0.0;
+        zo[h] = sc ? z[i] : 0.0;
       }
-      const double ri = sc ? __ldg(&r[i]) : 0.0;
-      const double zo = sc ? z[i] : 0.0;
-      double v = 0.0;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        double zv = zcv[c * ND];
+      for (int h = 0; h < U; ++h) {  // every lane computes (the shuffles need all lanes); valid ones write
+        CT qw[NC];
+        q1_from_xi<NC>(t[h], qw);
+        CT vc = CT(0);
 #pragma unroll
-        for (int b = 1; b < ND; ++b)
-          if (b == a) zv = zcv[c * ND + b];
-        v = fma(qv[c], zv, v);
+        for (int c = 0; c < NC; ++c) vc = fma(qw[c], __shfl_sync(0xffffffffu, zl, c * ND + cm[h]), vc);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) vc += sb[c] >= 0 ? wv[h][c] : CT(0);
+        if (!ok[h]) continue;
+        const double v = (double)vc;
+        if (sc) {
+          s1 = fma(rv[h], v, s1);
+          s2 = fma(rv[h], zo[h], s2);
+        }
+        z[ii[h]] = v;
       }
-#pragma unroll
-      for (int c = 0; c < NC; ++c) v += sb[c] >= 0 ? wv[c] : 0.0;
-      if (sc) {
-        s1 = fma(ri, v, s1);
-        s2 = fma(ri, zo, s2);
-      }
-      z[i] = v;
     }
   }
   if (!sc) return;
@@ -328,11 +354,18 @@ __global__ void __launch_bounds__(256) k_combine(int n_elem, int64_t N, const in
   if (last_block(&sc->cnt[2])) {
     const double rz_new = block_sum(part1, gridDim.x, sh);
     const double rzo = block_sum(part2, gridDim.x, sh);
+    // in a PCG step also |r|^2 of the update, the iteration count and the stop test
+    const double rr = first ? 0.0 : block_sum(prr, nrr, sh);
     if (threadIdx.x == 0) {
       double beta = 0.0;
       if (!first) beta = flexible ? (rz_new - rzo) / sc->rz : rz_new / sc->rz;
       sc->beta = beta;
       sc->rz = rz_new;
+      if (!first) {
+        sc->rr = rr;
+        sc->iter += 1;
+        if (sqrt(rr) <= sc->rtol * sqrt(sc->bb) || sc->iter >= sc->maxit) sc->done = 1;
+      }
       sc->cnt[2] = 0;
     }
   }
@@ -364,35 +397,53 @@ int pc_elem_tables(spnet_pc_s* pc) {
   return SPNET_OK;
 }
 
-template <int NC, int ND>
-static void launch_update_t(spnet_pc_s* pc, double* x, double* r, const double* p, const double* q,
-                            Scal* sc, int mode, cudaStream_t s) {
-  k_update<NC, ND><<<pc->G, 256, 0, s>>>(pc->n_elem, pc->N, pc->elem_ptr, pc->comp_of, pc->q1w, x, r,
-                                        p, q, pc->epart, pc->partial + pc->G, sc, mode);
+// one warp per element (blocks of `warps` warps), all resident at once when
+// they fit; at most PG blocks (the stride of the partial-sum slots)
+static int elem_grid(const spnet_pc_s* pc, int warps) {
+  const int need = (pc->n_elem + warps - 1) / warps;
+  return need < 1 ? 1 : need > pc->PG ? pc->PG : need;
 }
 
+template <int NC, int ND, class CT>
+static void launch_update_t(spnet_pc_s* pc, const CT* xi, double* x, double* r, const double* p, const double* q,
+                            Scal* sc, int mode, cudaStream_t s) {
+  k_update<NC, ND, CT><<<elem_grid(pc, 8), 256, 0, s>>>(pc->n_elem, pc->N, pc->elem_ptr, pc->comp_of, xi, x, r, p,
+                                                       q, pc->epart, pc->pspmv, pc->spmv_blocks,
+                                                       pc->partial + pc->PG, sc, mode);
+}
+
+template <class CT>
+static void launch_update_c(spnet_pc_s* pc, const CT* xi, double* x, double* r, const double* p, const double* q,
+                            Scal* sc, int mode, cudaStream_t s) {
+  if (pc->nc == 4 && pc->ndof == 1) launch_update_t<4, 1>(pc, xi, x, r, p, q, sc, mode, s);
+  else if (pc->nc == 8 && pc->ndof == 1) launch_update_t<8, 1>(pc, xi, x, r, p, q, sc, mode, s);
+  else if (pc->nc == 4) launch_update_t<4, 3>(pc, xi, x, r, p, q, sc, mode, s);
+  else launch_update_t<8, 3>(pc, xi, x, r, p, q, sc, mode, s);
+}
+
+// exact: the corner sums in FP64 whatever the precision (the stand-alone
+// restriction); otherwise in the arithmetic of the preconditioner
 static void launch_update(spnet_pc_s* pc, double* x, double* r, const double* p, const double* q,
-                          Scal* sc, int mode, cudaStream_t s) {
+                          Scal* sc, int mode, cudaStream_t s, int exact = 0) {
   note_launch();
   ProfScope ps(KID_UPDATE, s);
-  if (pc->nc == 4 && pc->ndof == 1) launch_update_t<4, 1>(pc, x, r, p, q, sc, mode, s);
-  else if (pc->nc == 8 && pc->ndof == 1) launch_update_t<8, 1>(pc, x, r, p, q, sc, mode, s);
-  else if (pc->nc == 4) launch_update_t<4, 3>(pc, x, r, p, q, sc, mode, s);
-  else launch_update_t<8, 3>(pc, x, r, p, q, sc, mode, s);
+  if (exact || pc->precision == SPNET_PREC_FP64) launch_update_c<double>(pc, pc->xi, x, r, p, q, sc, mode, s);
+  else launch_update_c<float>(pc, pc->xi32, x, r, p, q, sc, mode, s);
 }
 
 static void launch_spmv_dir(spnet_pc_s* pc, cudaStream_t s) {
   note_launch();
   ProfScope ps(KID_SPMV, s);
   const Csr& A = pc->K;
-  const int G = pc->G;
+  const int G = pc->spmv_blocks;
+  double* part = pc->pspmv;
   switch (pc->spmv_lanes) {
-    case 1: k_spmv_dir<1><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, pc->partial, pc->scal); break;
-    case 2: k_spmv_dir<2><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, pc->partial, pc->scal); break;
-    case 4: k_spmv_dir<4><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, pc->partial, pc->scal); break;
-    case 8: k_spmv_dir<8><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, pc->partial, pc->scal); break;
-    case 16: k_spmv_dir<16><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, pc->partial, pc->scal); break;
-    default: k_spmv_dir<32><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, pc->partial, pc->scal); break;
+    case 1: k_spmv_dir<1><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, part, pc->scal); break;
+    case 2: k_spmv_dir<2><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, part, pc->scal); break;
+    case 4: k_spmv_dir<4><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, part, pc->scal); break;
+    case 8: k_spmv_dir<8><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, part, pc->scal); break;
+    case 16: k_spmv_dir<16><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, part, pc->scal); break;
+    default: k_spmv_dir<32><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, part, pc->scal); break;
   }
 }
 
@@ -406,25 +457,39 @@ void launch_restrict(spnet_pc_s* pc, double* rc, const int* done, cudaStream_t s
   k_restrict<<<blocks, 256, 0, s>>>(pc->n_mesh, mesh_of_pc(pc), pc->ndof, pc->epart, pc->cidx, rc, done);
 }
 
-template <int NC, int ND>
-static void launch_combine_t(spnet_pc_s* pc, const double* r, double* z, int with_coarse, int with_stars,
-                             int dots, cudaStream_t s) {
-  k_combine<NC, ND><<<pc->G, 256, 0, s>>>(pc->n_elem, pc->N, pc->elem_ptr, pc->comp_of, pc->q1w, pc->ecoarse,
-                                         pc->estar, pc->zc, pc->w, r, z, pc->partial + 2 * pc->G,
-                                         pc->partial + 3 * pc->G, with_coarse && pc->m0 > 0,
-                                         with_stars && pc->S > 0, dots ? pc->scal : nullptr, pc->flexible,
-                                         dots == 2 ? 1 : 0);
+template <int NC, int ND, class CT, class WS>
+static void launch_combine_t(spnet_pc_s* pc, const CT* xi, const WS* w, const double* r, double* z,
+                             int with_coarse, int with_stars, int dots, cudaStream_t s) {
+  k_combine<NC, ND, CT, WS><<<elem_grid(pc, 4), 128, 0, s>>>(
+      pc->n_elem, pc->N, pc->elem_ptr, pc->comp_of, xi, pc->ecoarse, pc->estar, pc->zc, w, r, z,
+      pc->partial + 2 * pc->PG, pc->partial + 3 * pc->PG, pc->partial + pc->PG, elem_grid(pc, 8),
+      with_coarse && pc->m0 > 0, with_stars && pc->S > 0, dots ? pc->scal : nullptr, pc->flexible,
+      dots == 2 ? 1 : 0);
 }
 
-// dots: 0 none, 1 PCG step (beta from the previous rz), 2 PCG start (beta = 0)
-void launch_combine(spnet_pc_s* pc, const double* r, double* z, int with_coarse, int with_stars,
-                    int dots, cudaStream_t s) {
+template <class CT, class WS>
+static void launch_combine_c(spnet_pc_s* pc, const CT* xi, const double* r, double* z, int with_coarse,
+                             int with_stars, int dots, cudaStream_t s) {
+  const WS* w = (const WS*)pc->w;
+  if (pc->nc == 4 && pc->ndof == 1) launch_combine_t<4, 1>(pc, xi, w, r, z, with_coarse, with_stars, dots, s);
+  else if (pc->nc == 8 && pc->ndof == 1) launch_combine_t<8, 1>(pc, xi, w, r, z, with_coarse, with_stars, dots, s);
+  else if (pc->nc == 4) launch_combine_t<4, 3>(pc, xi, w, r, z, with_coarse, with_stars, dots, s);
+  else launch_combine_t<8, 3>(pc, xi, w, r, z, with_coarse, with_stars, dots, s);
+}
+
+// dots: 0 none, 1 PCG step (beta from the previous rz), 2 PCG start (beta = 0).
+// exact: the prolongation in FP64 whatever the precision (the stand-alone
+// prolongation); otherwise in the arithmetic of the preconditioner
+void launch_combine(spnet_pc_s* pc, const double* r, double* z, int with_coarse, int with_stars, int dots,
+                    cudaStream_t s, int exact) {
   note_launch();
   ProfScope ps(KID_COMBINE, s);
-  if (pc->nc == 4 && pc->ndof == 1) launch_combine_t<4, 1>(pc, r, z, with_coarse, with_stars, dots, s);
-  else if (pc->nc == 8 && pc->ndof == 1) launch_combine_t<8, 1>(pc, r, z, with_coarse, with_stars, dots, s);
-  else if (pc->nc == 4) launch_combine_t<4, 3>(pc, r, z, with_coarse, with_stars, dots, s);
-  else launch_combine_t<8, 3>(pc, r, z, with_coarse, with_stars, dots, s);
+  if (pc->precision == SPNET_PREC_FP64)
+    launch_combine_c<double, double>(pc, pc->xi, r, z, with_coarse, with_stars, dots, s);
+  else if (exact)
+    launch_combine_c<double, float>(pc, pc->xi, r, z, with_coarse, with_stars, dots, s);
+  else
+    launch_combine_c<float, float>(pc, pc->xi32, r, z, with_coarse, with_stars, dots, s);
 }
 
 // z = B r for a vector r already in pc order (corner sums of r computed here)
@@ -432,8 +497,7 @@ static void precond_any(spnet_pc_s* pc, double* r, double* z, int with_coarse, i
                         cudaStream_t s) {
   if (with_coarse && pc->m0 > 0) {
     launch_update(pc, nullptr, r, nullptr, nullptr, pc->scal, 1, s);
-    launch_restrict(pc, pc->rc, nullptr, s);
-    launch_coarse_apply(pc, pc->rc, pc->zc, nullptr, s);
+    launch_coarse_apply(pc, nullptr, pc->zc, nullptr, s);  // restriction fused
   }
   if (with_stars) launch_star_solve(pc, r, nullptr, s);
   launch_combine(pc, r, z, with_coarse, with_stars, dots, s);
@@ -452,8 +516,7 @@ static void iteration(spnet_pc_s* pc, cudaStream_t s, cudaStream_t side) {
   } else {
     launch_star_solve(pc, pc->r, done, s);
   }
-  launch_restrict(pc, pc->rc, done, s);
-  launch_coarse_apply(pc, pc->rc, pc->zc, done, s);
+  launch_coarse_apply(pc, nullptr, pc->zc, done, s);  // restriction fused
   if (side) cudaStreamWaitEvent(s, pc->ev_join, 0);
   launch_combine(pc, pc->r, pc->z, 1, 1, 1, s);
 }
@@ -581,7 +644,7 @@ int pc_restrict_free(spnet_pc_s* pc, const double* r_free, double* rc) {
   cudaStream_t s = pc->op->stream;
   to_pc(pc, r_free, pc->vtmp);
   if (pc->m0 == 0) return SPNET_OK;
-  launch_update(pc, nullptr, pc->vtmp, nullptr, nullptr, pc->scal, 1, s);
+  launch_update(pc, nullptr, pc->vtmp, nullptr, nullptr, pc->scal, 1, s, 1);
   launch_restrict(pc, rc, nullptr, s);
   SPNET_CUDA_TRY(cudaGetLastError());
   return SPNET_OK;

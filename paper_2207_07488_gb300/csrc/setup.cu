@@ -74,7 +74,8 @@ __global__ void k_segment_sort(int n_elem, const int64_t* eptr, const int32_t* t
 __global__ void k_pc_maps(int64_t N, const int32_t* perm, const int32_t* elem_free,
                           const int8_t* comp_free, const int64_t* free_dofs, int ndof,
                           const double* coords, Mesh m, double l0, double l1, double l2,
-                          int32_t* iperm, int32_t* elem_of, int8_t* comp_of, double* q1w) {
+                          int32_t* iperm, int32_t* elem_of, int8_t* comp_of, double* q1w, double* xio,
+                          float* xio32) {
   double l[3] = {l0, l1, l2};
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -86,6 +87,10 @@ __global__ void k_pc_maps(int64_t N, const int32_t* perm, const int32_t* elem_fr
     double x[3], xi[3];
     for (int a = 0; a < m.d; ++a) x[a] = coords[node * m.d + a];
     host_element(m, x, l, xi);
+    for (int a = 0; a < m.d; ++a) {
+      xio[(int64_t)a * N + p] = xi[a];
+      xio32[(int64_t)a * N + p] = (float)xi[a];
+    }
     for (int c = 0; c < m.nc; ++c) {
       double w = 1.0;
       for (int a = 0; a < m.d; ++a) w *= ((c >> a) & 1) ? xi[a] : (1.0 - xi[a]);
@@ -260,6 +265,8 @@ int pc_setup_structure(spnet_pc_s* pc) {
   SPNET_TRY(pc->mem.get(&pc->comp_of, N));
   SPNET_TRY(pc->mem.get(&pc->elem_ptr, pc->n_elem + 1));
   SPNET_TRY(pc->mem.get(&pc->q1w, (int64_t)pc->nc * N));
+  SPNET_TRY(pc->mem.get(&pc->xi, (int64_t)m.d * N));
+  SPNET_TRY(pc->mem.get(&pc->xi32, (int64_t)m.d * N));
   note_launch();
   k_segment_sort<<<grid, 128, 0, s>>>(pc->n_elem, eptr, ptmp, pc->perm);
   note_launch();
@@ -267,7 +274,7 @@ int pc_setup_structure(spnet_pc_s* pc) {
   note_launch();
   k_pc_maps<<<grid, 256, 0, s>>>(N, pc->perm, elem_free, comp_free, op->free_dofs, op->ndof,
                                  op->coords, m, op->domain[0], op->domain[1], op->domain[2],
-                                 pc->iperm, pc->elem_of, pc->comp_of, pc->q1w);
+                                 pc->iperm, pc->elem_of, pc->comp_of, pc->q1w, pc->xi, pc->xi32);
   // A in pc order
   int32_t* len = nullptr;
   SPNET_TRY(tmp.get(&len, N + 1));

@@ -123,6 +123,8 @@ struct spnet_pc_s {
   int8_t* comp_of = nullptr;   // [N]
   int32_t* elem_ptr = nullptr; // [n_elem+1]
   double* q1w = nullptr;       // [nc][N]
+  double* xi = nullptr;        // [d*N] local coordinates of each dof in its element (axis-major)
+  float* xi32 = nullptr;       // [d*N] the same in FP32 (mixed precision: restriction and prolongation in FP32)
   spnet::Csr K;                // A in pc order
   // coarse space
   int m0 = 0;
@@ -133,6 +135,7 @@ struct spnet_pc_s {
   void* cpart = nullptr;       // [nt*nt*CT] per row block and tile column: partial products
   unsigned* ccnt = nullptr;    // [nt] parts written per row block (zero between applications)
   int ctiles_n = 0;            // nt: tiles per dimension
+  int32_t* rtab = nullptr;     // [m0*8] offsets of the corner sums that make up each r_c entry
   double* A0 = nullptr;        // [m0*m0] copy of A_0 if m0 <= A0_KEEP
   // stars
   int S = 0, max_star = 0, max_levels = 0;
@@ -147,18 +150,20 @@ struct spnet_pc_s {
   int32_t* star_n = nullptr;       // [S]
   int32_t* star_lev = nullptr;     // [S]
   int32_t* star_nnz = nullptr;     // [S]
-  // solve streams: per-star header (80 B), inverse permutation, entries
+  // solve windows: per-star header (80 B), inverse permutation, window records
   void* shdr = nullptr;            // [S] headers
   uint16_t* iperm_star = nullptr;  // [sum_s] local index -> elimination position, at star_ptr
-  uint16_t* emeta = nullptr;       // [n_entries + chunk] column | flags
-  char* ecoef = nullptr;           // [n_entries + chunk] coefficients in the solve precision
-  int64_t n_entries = 0;
-  int64_t stream_bytes = 0;        // bytes one solve reads from the streams
+  char* srec = nullptr;            // [n_entries] window records (208 B FP32, 336 B FP64)
+  int64_t n_entries = 0;           // window records of all stars
+  int64_t stream_bytes = 0;        // bytes one solve reads from headers, permutations and records
   int solve_wpb = 0;               // warps (stars) per block of the solve
+  int solve_blocks = 0;            // blocks of the solve (a multiple of the SM count)
   size_t solve_smem = 0;           // its dynamic shared memory per block
+  int32_t* sorder = nullptr;       // [solve_blocks*solve_wpb] star of each warp slot, -1: idle
   // work vectors (pc order)
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *b = nullptr;
-  double *w = nullptr, *rc = nullptr, *zc = nullptr, *partial = nullptr, *vtmp = nullptr;
+  double *rc = nullptr, *zc = nullptr, *partial = nullptr, *vtmp = nullptr;
+  void* w = nullptr;               // [sum_s] star results in the solve precision (float or double)
   double* epart = nullptr;         // [n_elem*nc*ndof] Q1-weighted corner sums of r
   int32_t* ecoarse = nullptr;      // [n_elem*nc*ndof] coarse index at each corner (-1: none)
   int64_t* estar = nullptr;        // [n_elem*nc] base of the element's entries in w (-1: no star)
@@ -168,7 +173,10 @@ struct spnet_pc_s {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int graph_launches = 0;
   int G = 0;         // reduction grid
+  int PG = 0;        // stride of the partial-sum slots (max blocks of a reducing kernel)
   int spmv_lanes = 1;
+  int spmv_blocks = 1;             // grid of the SpMV of an iteration (one pass over the rows)
+  double* pspmv = nullptr;         // [spmv_blocks] its partial dot products
   double setup_ms = 0;
 };
 
@@ -282,7 +290,7 @@ void launch_coarse_apply(spnet_pc_s* pc, const double* rc, double* zc, const int
 // pcg.cu
 void launch_restrict(spnet_pc_s* pc, double* rc, const int* done, cudaStream_t s);
 void launch_combine(spnet_pc_s* pc, const double* r, double* z, int with_coarse, int with_stars,
-                    int dots, cudaStream_t s);
+                    int dots, cudaStream_t s, int exact = 0);
 int pc_restrict_free(spnet_pc_s* pc, const double* r_free, double* rc);
 int pc_elem_tables(spnet_pc_s* pc);
 int pc_apply_free(spnet_pc_s* pc, const double* r_free_dev, double* z_free_dev, int which);
@@ -325,6 +333,25 @@ __device__ __forceinline__ int rs_index(int lane) {
 template <int K>
 __device__ __forceinline__ bool rs_writer(int lane) {
   return (lane & (32 / K - 1)) == 0;
+}
+
+// Q1 values phi_c = prod_a (bit a of c ? xi_a : 1 - xi_a) at local coordinates
+// t, multiplied in axis order (the same products as the stored Q1 values)
+template <int NC, class CT>
+__device__ __forceinline__ void q1_from_xi(const CT (&t)[3], CT (&w)[NC]) {
+  const CT one = CT(1);
+  const CT f0[2] = {one - t[0], t[0]}, f1[2] = {one - t[1], t[1]};
+  if (NC == 4) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) w[c] = f0[c & 1] * f1[(c >> 1) & 1];
+  } else {
+    const CT f2[2] = {one - t[2], t[2]};
+    CT g[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) g[c] = f0[c & 1] * f1[c >> 1];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) w[c] = g[c & 3] * f2[(c >> 2) & 1];
+  }
 }
 
 template <int N>

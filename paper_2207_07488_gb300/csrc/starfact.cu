@@ -17,7 +17,10 @@
 // places each star's blob in a pool; pass 2 (numeric) fills the values level
 // by level, every lane computing one column left-looking in FP64.  Values are
 // kept in FP64 and rounded to FP32 for the mixed-precision solve.
+#include <algorithm>
+#include <climits>
 #include <cmath>
+#include <queue>
 
 #include "spnet_internal.cuh"
 
@@ -524,66 +527,138 @@ __global__ void __launch_bounds__(128) k_star_numeric(int S, char* pool, const i
 }
 
 // ---------------------------------------------------------------------------
-// Solve streams.  Both triangular solves of a star are written as one stream of
-// entries (column, coefficient), level after level: the forward levels of
+// Solve windows.  Both triangular solves of a star are written as one sequence
+// of entries (column, coefficient), level after level: the forward levels of
 // L y = r in elimination order, then the levels of L^T z = y in reverse.  A row
 // v of a level is a segment of consecutive entries
 //   forward:   (u, -L_vu / L_vv) for the u of row v, then (v, 1 / L_vv)
 //   backward:  (u, -L_uv / L_vv) for the u of column v, then (v, 1 / L_vv)
-// so that the new value is the segment's sum of coefficient * y[column], the
-// diagonal entry last: its column names the row written.  Rows of one level do
-// not read one another, so the sums of a level run in parallel and the update
-// is in place.  Entry metadata (u16): column (14 bits), SEG_END on a row's
-// last entry, LEVEL_END on a level's last entry.
+// so that the new value of row v is the segment's sum of coefficient *
+// y[column], the diagonal entry last: its column names the row written.  Rows
+// of one level do not read one another, so the sums of a level run in parallel
+// and the update is in place.
 //
-// A warp solves one star.  It streams the entries through a ring in shared
-// memory (cp.async, RING_CH chunks of 64 entries in flight) and consumes them
-// 32 at a time: every lane multiplies one entry, a segmented shuffle scan sums
-// the segments in a fixed order (deterministic), and the last lane of each
-// segment writes its row.  A window stops at a level's end; a segment cut by
-// the window's end carries its partial sum into the next window.  Only the
-// star's vector (and its inverse permutation) stays in shared memory.
+// A level's entries are cut into windows of 32 slots (zero coefficients pad the
+// last one; a padding slot reads y[0]).  Each window is one record:
+//   descriptor (8 B): u32 mask of the slots that end a segment, u8 scan steps
+//   (the longest segment inside the window needs that many doublings), u8 flags
+//   (bit 0: the window's last segment continues in the next window); 8 B pad;
+//   32 u16 columns; 32 coefficients in the solve precision.
+// Everything that depends only on the factor is decided here, at set-up, so a
+// window costs the solve a handful of instructions: one product per lane, a
+// segmented shuffle scan of `steps` steps (a fixed order: deterministic), the
+// writes of the segment ends, a carry of a cut segment into the next window.
+//
+// A warp solves one star.  Records stream through a ring of RING_W windows in
+// shared memory (cp.async, one group per window); only the star's vector and
+// its inverse permutation stay resident.
 // ---------------------------------------------------------------------------
-constexpr int STREAM_CHUNK = 64;                // entries per copy group
-constexpr int RING_CH = 4;                      // chunks in the ring
-constexpr int RING_E = STREAM_CHUNK * RING_CH;  // ring entries (power of two)
-constexpr int STREAM_MAX_N = 16383;             // star size the 14-bit columns address
-constexpr unsigned SEG_END = 0x4000u, LEVEL_END = 0x8000u, COL_MASK = 0x3fffu;
-constexpr int STREAM_SMEM = 200 * 1024;         // shared memory budget per block
+constexpr int WIN = 32;                      // slots per window
+constexpr int RING_W = 16;                   // windows in flight
+constexpr int STREAM_MAX_N = 65535;          // star size the u16 columns address
+constexpr int STREAM_SMEM = 200 * 1024;      // shared memory budget per block
+constexpr int REC_HDR = 16;                  // descriptor + pad
+constexpr int REC_COEF = REC_HDR + 2 * WIN;  // offset of the coefficients
+
+__host__ __device__ inline int rec_bytes(int vb) { return REC_COEF + WIN * vb; }  // 208 or 336
 
 // per-star header of the solve, 80 bytes
 struct StarHdr {
-  int64_t eoff;   // first entry of the star's stream
+  int64_t eoff;   // first window record of the star
   int64_t wbase;  // first slot of the star in w (star_ptr)
   int32_t n;      // dofs
-  int32_t ne;     // entries (forward + backward)
+  int32_t ne;     // window records (forward + backward)
   int32_t es[8];  // pc index of the first dof of each of the 2^d elements, -1 if absent
   uint16_t eo[9]; // local offset of each element's dofs within the star
   uint16_t pad[3];
 };
 static_assert(sizeof(StarHdr) == 80, "StarHdr layout");
 
-// shared memory of one warp: ring (metadata, coefficients), y, inverse permutation, header
+// shared memory of one warp: ring, y, inverse permutation, header
 __host__ __device__ inline int64_t stream_warp_bytes(int vb, int ymax) {
-  return align_up(2ll * RING_E, 16) + align_up((int64_t)vb * RING_E, 16) + align_up((int64_t)vb * ymax, 16) +
-         align_up(2ll * ymax, 16) + (int64_t)sizeof(StarHdr);
+  return (int64_t)RING_W * rec_bytes(vb) + align_up((int64_t)vb * ymax, 16) + align_up(2ll * ymax, 16) +
+         (int64_t)sizeof(StarHdr);
+}
+
+// windows of a level with E entries
+__host__ __device__ inline int level_windows(int64_t E) { return (int)((E + WIN - 1) / WIN); }
+
+// entries of level l: forward (row form) or backward (column form)
+__device__ inline int64_t level_entries(const uint32_t* ptr, const uint16_t* lvl, int l) {
+  const int v0 = lvl[l], v1 = lvl[l + 1];
+  return (int64_t)(ptr[v1] - ptr[v0]) + (v1 - v0);
 }
 
 __global__ void k_stream_sizes(int S, const char* pool, const int64_t* star_off, int64_t* sz) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
-    const int32_t* h = (const int32_t*)(pool + star_off[s]);
-    sz[s] = align_up(2ll * ((int64_t)h[0] + h[2]), 8);
+    const char* blob = pool + star_off[s];
+    const int32_t* h = (const int32_t*)blob;
+    const int n = h[0], nlev = h[1], nnz = h[2];
+    const BlobLayout B = blob_layout(n, nlev, nnz, 8);
+    const uint32_t* rowptr = (const uint32_t*)(blob + B.rowptr);
+    const uint32_t* colptr = (const uint32_t*)(blob + B.colptr);
+    const uint16_t* lvl = (const uint16_t*)(blob + B.lvl);
+    int64_t nw = 0;
+    for (int l = 0; l < nlev; ++l)
+      nw += level_windows(level_entries(rowptr, lvl, l)) + level_windows(level_entries(colptr, lvl, l));
+    sz[s] = nw;
   }
 }
 
-// warp per star: set-up blob (FP64 factor) -> header, inverse permutation, entry stream
+// scan steps a window needs: a segment of at least 2^k + 1 slots holds 2^k
+// consecutive slots that end no segment
+__device__ inline int window_steps(unsigned ends, int cnt) {
+  unsigned run = ~ends & (cnt >= 32 ? 0xffffffffu : ((1u << cnt) - 1u));
+  int steps = 0;
+  while (run) {
+    run &= run >> (1 << steps);
+    ++steps;
+  }
+  return steps;
+}
+
+// the windows of one level: entries of the rows of the level in order, the
+// descriptor of every window (ends, steps, carry flag)
+template <class T>
+__device__ void pack_level(char* recs, int64_t wb, int lane, int v0, int v1, const uint32_t* ptr,
+                           const uint16_t* idx, const double* val, const double* invd, int vb) {
+  const int RB = rec_bytes(vb);
+  const int64_t E = (int64_t)(ptr[v1] - ptr[v0]) + (v1 - v0);
+  for (int v = v0 + lane; v < v1; v += 32) {
+    const double dv = invd[v];
+    int64_t j = (int64_t)(ptr[v] - ptr[v0]) + (v - v0);
+    for (uint32_t q = ptr[v]; q <= ptr[v + 1]; ++q, ++j) {
+      const bool diag = q == ptr[v + 1];
+      char* rec = recs + (wb + j / WIN) * RB;
+      const int sl = (int)(j % WIN);
+      ((uint16_t*)(rec + REC_HDR))[sl] = diag ? (uint16_t)v : idx[q];
+      ((T*)(rec + REC_COEF))[sl] = (T)(diag ? dv : -val[q] * dv);
+      if (diag) atomicOr((unsigned*)rec, 1u << sl);
+    }
+  }
+  __syncwarp();
+  __threadfence_block();
+  const int nwl = level_windows(E);
+  for (int k = lane; k < nwl; k += 32) {
+    char* rec = recs + (wb + k) * RB;
+    const int cnt = (int)((E - (int64_t)k * WIN) < WIN ? (E - (int64_t)k * WIN) : WIN);
+    const unsigned ends = *(volatile unsigned*)rec;
+    const int steps = window_steps(ends, cnt);
+    const unsigned carry = (cnt == WIN && !((ends >> 31) & 1u)) ? 1u : 0u;
+    ((unsigned*)rec)[1] = (unsigned)steps | (carry << 8);
+  }
+  __syncwarp();
+}
+
+// warp per star: set-up blob (FP64 factor) -> header, inverse permutation, window records
 template <class T>
 __global__ void k_stream_pack(int S, Mesh m, const char* __restrict__ pool, const int64_t* __restrict__ star_off,
                               const int32_t* __restrict__ star_mesh, const int32_t* __restrict__ elem_ptr,
-                              const int64_t* __restrict__ star_ptr, const int64_t* __restrict__ eoff,
-                              StarHdr* __restrict__ hdr, uint16_t* __restrict__ iperm,
-                              uint16_t* __restrict__ emeta, T* __restrict__ ecoef) {
+                              const int64_t* __restrict__ star_ptr, const int64_t* __restrict__ roff,
+                              StarHdr* __restrict__ hdr, uint16_t* __restrict__ iperm, char* __restrict__ recs) {
   const int lane = threadIdx.x & 31;
+  const int vb = (int)sizeof(T);
+  const int RB = rec_bytes(vb);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
     const char* blob = pool + star_off[s];
@@ -599,13 +674,13 @@ __global__ void k_stream_pack(int S, Mesh m, const char* __restrict__ pool, cons
     const double* rowv = (const double*)(blob + B.v64);
     const double* colv = rowv + nnz;
     const double* invd = colv + nnz;
-    const int64_t e0 = eoff[s], wb = star_ptr[s];
+    const int64_t r0 = roff[s], r1 = roff[s + 1], wb = star_ptr[s];
     if (lane == 0) {
       StarHdr h;
-      h.eoff = e0;
+      h.eoff = r0;
       h.wbase = wb;
       h.n = n;
-      h.ne = 2 * (n + nnz);
+      h.ne = (int32_t)(r1 - r0);
       const StarElems se = star_elems(m, star_mesh[s], elem_ptr);
       for (int cp = 0; cp < 8; ++cp) h.es[cp] = (cp < m.nc && se.e[cp] >= 0) ? elem_ptr[se.e[cp]] : -1;
       for (int cp = 0; cp <= 8; ++cp) h.eo[cp] = (uint16_t)(cp <= m.nc ? se.off[cp < m.nc ? cp : m.nc] : n);
@@ -613,94 +688,75 @@ __global__ void k_stream_pack(int S, Mesh m, const char* __restrict__ pool, cons
       hdr[s] = h;
     }
     for (int pos = lane; pos < n; pos += 32) iperm[wb + perm[pos]] = (uint16_t)pos;
-    const int64_t ef = (int64_t)n + nnz;  // forward entries
-    for (int l = 0; l < nlev; ++l) {
-      const int v0 = lvl[l], v1 = lvl[l + 1];
-      // backward segments of this level start after the levels above it
-      const int64_t bl = ef + (int64_t)(nnz - colptr[v1]) + (n - v1);
-      for (int v = v0 + lane; v < v1; v += 32) {
-        const double dv = invd[v];
-        const unsigned last = v == v1 - 1 ? LEVEL_END : 0u;
-        int64_t o = e0 + rowptr[v] + v;
-        for (uint32_t q = rowptr[v]; q < rowptr[v + 1]; ++q, ++o) {
-          emeta[o] = rowidx[q];
-          ecoef[o] = (T)(-rowv[q] * dv);
-        }
-        emeta[o] = (uint16_t)(v | SEG_END | last);
-        ecoef[o] = (T)dv;
-        o = e0 + bl + (colptr[v] - colptr[v0]) + (v - v0);
-        for (uint32_t q = colptr[v]; q < colptr[v + 1]; ++q, ++o) {
-          emeta[o] = colidx[q];
-          ecoef[o] = (T)(-colv[q] * dv);
-        }
-        emeta[o] = (uint16_t)(v | SEG_END | last);
-        ecoef[o] = (T)dv;
-      }
+    // zero records (padding slots: column 0, coefficient 0)
+    int4* z4 = (int4*)(recs + r0 * RB);
+    const int64_t n16 = (r1 - r0) * RB / 16;
+    for (int64_t q = lane; q < n16; q += 32) z4[q] = make_int4(0, 0, 0, 0);
+    __syncwarp();
+    __threadfence_block();
+    int64_t w = r0;
+    for (int l = 0; l < nlev; ++l) {  // forward levels
+      pack_level<T>(recs, w, lane, lvl[l], lvl[l + 1], rowptr, rowidx, rowv, invd, vb);
+      w += level_windows(level_entries(rowptr, lvl, l));
+    }
+    for (int l = nlev - 1; l >= 0; --l) {  // backward levels, last first
+      pack_level<T>(recs, w, lane, lvl[l], lvl[l + 1], colptr, colidx, colv, invd, vb);
+      w += level_windows(level_entries(colptr, lvl, l));
     }
   }
 }
 
-__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_8(void* dst, const void* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// wait until at most `pending` of this thread's copy groups are still in flight
-__device__ __forceinline__ void cp_async_wait_pending(int pending) {
-  switch (pending) {
-    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
-    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
-    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
-    default: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
-  }
-}
-static_assert(RING_CH == 4, "cp_async_wait_pending covers up to RING_CH - 1 pending groups");
 
-// chunk k of a star's stream into ring slot k % RING_CH: lane copies entries 2*lane, 2*lane+1
+// one scan step of the segmented inclusive scan: lanes at least o past their
+// segment's first lane add the value o lanes down
 template <class T>
-__device__ __forceinline__ void stream_fetch(int k, int lane, const uint16_t* emeta, const T* ecoef, int64_t e0,
-                                             uint16_t* rmeta, T* rcoef) {
-  const int64_t g = e0 + (int64_t)k * STREAM_CHUNK + 2 * lane;
-  const int sl = (k & (RING_CH - 1)) * STREAM_CHUNK + 2 * lane;
-  cp_async_4(rmeta + sl, emeta + g);
-  if (sizeof(T) == 4) cp_async_8(rcoef + sl, ecoef + g);
-  else cp_async_16(rcoef + sl, ecoef + g);
-  cp_async_commit();
+__device__ __forceinline__ T scan_step(T v, int o, int dl) {
+  const T t = __shfl_up_sync(0xffffffffu, v, o);
+  return dl >= o ? v + t : v;
 }
 
+// slot (block, warp) -> star: sorder[blockIdx.x * wpb + warp], -1 for an idle slot
 template <class T>
-__global__ void __launch_bounds__(256) k_star_stream(int S, int wpb, int ymax, const StarHdr* __restrict__ hdr,
-                                                     const uint16_t* __restrict__ emeta, const T* __restrict__ ecoef,
+__global__ void __launch_bounds__(256) k_star_stream(int wpb, int ymax, const int32_t* __restrict__ sorder,
+                                                     const StarHdr* __restrict__ hdr, const char* __restrict__ recs,
                                                      const uint16_t* __restrict__ iperm, const double* __restrict__ r,
-                                                     double* __restrict__ w, const int* done) {
+                                                     T* __restrict__ w, const int* done) {
   extern __shared__ int4 smem4[];
   if (done && *done) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int s = blockIdx.x * wpb + wid;
-  if (wid >= wpb || s >= S) return;  // no block-wide barrier follows
+  const int s = sorder[blockIdx.x * wpb + wid];
+  if (s < 0) return;  // no block-wide barrier follows
   constexpr unsigned FULL = 0xffffffffu;
-  char* base = (char*)smem4 + (int64_t)wid * stream_warp_bytes((int)sizeof(T), ymax);
-  uint16_t* rmeta = (uint16_t*)base;
-  T* rcoef = (T*)(base + align_up(2ll * RING_E, 16));
-  T* y = (T*)((char*)rcoef + align_up((int64_t)sizeof(T) * RING_E, 16));
+  constexpr int RB = REC_COEF + WIN * (int)sizeof(T);
+  constexpr unsigned RING_BYTES = (unsigned)(RING_W * RB);
+  char* ring = (char*)smem4 + (int64_t)wid * stream_warp_bytes((int)sizeof(T), ymax);
+  T* y = (T*)(ring + RING_BYTES);
   uint16_t* ip = (uint16_t*)((char*)y + align_up((int64_t)sizeof(T) * ymax, 16));
   StarHdr* h = (StarHdr*)((char*)ip + align_up(2ll * ymax, 16));
   if (lane < (int)(sizeof(StarHdr) / 4)) ((int32_t*)h)[lane] = __ldg(((const int32_t*)(hdr + s)) + lane);
   __syncwarp();
-  const int64_t e0 = h->eoff, wb = h->wbase;
-  const int n = h->n, ne = h->ne;
-  const int nch = (ne + STREAM_CHUNK - 1) / STREAM_CHUNK;
+  const int64_t wb = h->wbase;
+  const int n = h->n, nw = h->ne;
+  // records stream in order: src is the next record to fetch, dst its ring slot
+  const bool copier = lane * 16 < RB;
+  const char* src = recs + h->eoff * RB + lane * 16;
+  const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring);
+  unsigned dst = ring_s + lane * 16;
   int F = 0;
-  for (; F < nch && F < RING_CH; ++F) stream_fetch<T>(F, lane, emeta, ecoef, e0, rmeta, rcoef);
+  for (; F < nw && F < RING_W; ++F) {
+    if (copier) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    src += RB;
+    dst += RB;
+  }
+  if (dst - ring_s - lane * 16 >= RING_BYTES) dst -= RING_BYTES;
   // gather r over the star in local order (element ranges: coalesced), place it at the elimination position
+  int eo[8], es[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    eo[c] = h->eo[c];
+    es[c] = h->es[c];
+  }
   constexpr int GU = 4;
   for (int t0 = 0; t0 < n; t0 += 32 * GU) {
     double rv[GU];
@@ -711,10 +767,10 @@ __global__ void __launch_bounds__(256) k_star_stream(int S, int wpb, int ymax, c
       rv[u] = 0.0;
       pv[u] = 0;
       if (t < n) {
-        int cp = 0;
+        int base = es[0] - eo[0];
 #pragma unroll
-        for (int c = 1; c < 8; ++c) cp += t >= (int)h->eo[c] ? 1 : 0;
-        rv[u] = __ldg(&r[h->es[cp] + (t - (int)h->eo[cp])]);
+        for (int c = 1; c < 8; ++c) base = t >= eo[c] ? es[c] - eo[c] : base;
+        rv[u] = __ldg(&r[base + t]);
         pv[u] = __ldg(&iperm[wb + t]);
       }
     }
@@ -727,42 +783,44 @@ __global__ void __launch_bounds__(256) k_star_stream(int S, int wpb, int ymax, c
       }
     }
   }
-  // the stream: forward levels, then backward levels
-  int c = 0;
+  const unsigned le = FULL >> (31 - lane);  // lanes 0..lane
+  const char* rec = ring;
+  const char* const ring_end = ring + RING_BYTES;
   T carry = T(0);
-  while (c < ne) {
-    const int cw = c / STREAM_CHUNK;
-    for (; F < nch && F < cw + RING_CH; ++F) stream_fetch<T>(F, lane, emeta, ecoef, e0, rmeta, rcoef);
-    const int kneed = min((c + 31) / STREAM_CHUNK, nch - 1);
-    cp_async_wait_pending(F - 1 - kneed);
+  for (int k = 0; k < nw; ++k) {
+    if (F == k + RING_W) asm volatile("cp.async.wait_group %0;\n" ::"n"(RING_W - 1) : "memory");
+    else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncwarp();
-    const int sl = (c + lane) & (RING_E - 1);
-    const unsigned mt = rmeta[sl];
-    const T a = rcoef[sl];
-    const unsigned lend = __ballot_sync(FULL, (mt & LEVEL_END) != 0u);
-    int cnt = lend ? __ffs(lend) : 32;
-    cnt = min(cnt, ne - c);
-    const bool act = lane < cnt;
-    const int col = (int)(mt & COL_MASK);
-    T v = T(0);
-    if (act) v = a * y[col];
-    if (lane == 0) v += carry;
-    const bool se = act && (mt & SEG_END) != 0u;
-    const unsigned ends = __ballot_sync(FULL, se);
-    const unsigned heads = (ends << 1) | 1u;
-    const int seg0 = 31 - __clz(heads & (FULL >> (31 - lane)));
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const T t = __shfl_up_sync(FULL, v, o);
-      if (lane - o >= seg0) v += t;
+    const uint2 d = *(const uint2*)rec;
+    const int col = ((const uint16_t*)(rec + REC_HDR))[lane];
+    const T a = ((const T*)(rec + REC_COEF))[lane];
+    const unsigned ends = d.x;
+    const unsigned steps = d.y & 0xffu;
+    T v = a * y[col];
+    const int dl = lane - (31 - __clz(((ends << 1) | 1u) & le));  // lanes since the segment's first
+    if (steps > 0u) v = scan_step(v, 1, dl);
+    if (steps > 1u) v = scan_step(v, 2, dl);
+    if (steps > 2u) v = scan_step(v, 4, dl);
+    if (steps > 3u) v = scan_step(v, 8, dl);
+    if (steps > 4u) v = scan_step(v, 16, dl);
+    // a segment cut by the previous window: its partial sum joins this window's first segment
+    if (lane <= dl) v += carry;  // lanes of the first segment (dl == lane there)
+    if ((ends >> lane) & 1u) y[col] = v;
+    carry = T(0);
+    if (d.y & 0x100u) carry = __shfl_sync(FULL, v, 31);
+    __syncwarp();
+    rec += RB;
+    if (rec == ring_end) rec = ring;
+    if (F < nw) {  // refill the slot just consumed
+      if (copier) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+      src += RB;
+      dst += RB;
+      if (dst - ring_s - lane * 16 >= RING_BYTES) dst -= RING_BYTES;
+      ++F;
     }
-    if (se) y[col] = v;
-    carry = __shfl_sync(FULL, v, cnt - 1);
-    if ((ends >> (cnt - 1)) & 1u) carry = T(0);
-    c += cnt;
-    __syncwarp();
   }
-  for (int t = lane; t < n; t += 32) w[wb + t] = (double)y[ip[t]];
+  for (int t = lane; t < n; t += 32) w[wb + t] = y[ip[t]];
 }
 
 void launch_star_solve(spnet_pc_s* pc, const double* r, const int* done, cudaStream_t s) {
@@ -770,59 +828,54 @@ void launch_star_solve(spnet_pc_s* pc, const double* r, const int* done, cudaStr
   note_launch();
   ProfScope ps(KID_STARS, s);
   const int wpb = pc->solve_wpb;
-  const unsigned grid = (unsigned)((pc->S + wpb - 1) / wpb);
+  const unsigned grid = (unsigned)pc->solve_blocks;
   if (pc->precision == SPNET_PREC_FP64)
-    k_star_stream<double><<<grid, wpb * 32, pc->solve_smem, s>>>(pc->S, wpb, pc->max_star, (const StarHdr*)pc->shdr, pc->emeta,
-                                                                  (const double*)pc->ecoef, pc->iperm_star, r, pc->w,
-                                                                  done);
+    k_star_stream<double><<<grid, wpb * 32, pc->solve_smem, s>>>(wpb, pc->max_star, pc->sorder,
+                                                                  (const StarHdr*)pc->shdr, pc->srec,
+                                                                  pc->iperm_star, r, (double*)pc->w, done);
   else
-    k_star_stream<float><<<grid, wpb * 32, pc->solve_smem, s>>>(pc->S, wpb, pc->max_star, (const StarHdr*)pc->shdr, pc->emeta,
-                                                                 (const float*)pc->ecoef, pc->iperm_star, r, pc->w,
-                                                                 done);
+    k_star_stream<float><<<grid, wpb * 32, pc->solve_smem, s>>>(wpb, pc->max_star, pc->sorder,
+                                                                 (const StarHdr*)pc->shdr, pc->srec,
+                                                                 pc->iperm_star, r, (float*)pc->w, done);
 }
 
 // headers, inverse permutations and entry streams of all stars
-static int pack_streams(spnet_pc_s* pc, DevArena& tmp) {
+static int pack_streams(spnet_pc_s* pc, DevArena& tmp, const std::vector<int32_t>& lev,
+                        const std::vector<int32_t>& nz) {
   cudaStream_t s = pc->op->stream;
   const int S = pc->S;
   const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
   int64_t* sz = nullptr;
-  int64_t* eoff = nullptr;
+  int64_t* roff = nullptr;
   SPNET_TRY(tmp.get(&sz, S + 1));
-  SPNET_TRY(tmp.get(&eoff, S + 1));
+  SPNET_TRY(tmp.get(&roff, S + 1));
   note_launch();
   k_stream_sizes<<<(S + 255) / 256, 256, 0, s>>>(S, pc->pool, pc->star_off, sz);
-  SPNET_TRY(scan_exclusive64(sz, eoff, S, s, tmp));
+  SPNET_TRY(scan_exclusive64(sz, roff, S, s, tmp));
   int64_t total = 0;
-  SPNET_CUDA_TRY(cudaMemcpyAsync(&total, eoff + S, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SPNET_CUDA_TRY(cudaMemcpyAsync(&total, roff + S, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   SPNET_CUDA_TRY(cudaStreamSynchronize(s));
-  // a chunk read may run up to one chunk past the last star's entries
-  const int64_t cap = total + STREAM_CHUNK;
-  pc->n_entries = total;
+  const int RB = rec_bytes(vb);
+  pc->n_entries = total;  // window records
   SPNET_TRY(pc->mem.alloc(&pc->shdr, (size_t)S * sizeof(StarHdr)));
   SPNET_TRY(pc->mem.get(&pc->iperm_star, pc->sum_s > 0 ? pc->sum_s : 1));
-  SPNET_TRY(pc->mem.get(&pc->emeta, cap));
-  SPNET_TRY(pc->mem.get(&pc->ecoef, cap * vb));
-  SPNET_CUDA_TRY(cudaMemsetAsync(pc->emeta, 0, sizeof(uint16_t) * cap, s));
-  SPNET_CUDA_TRY(cudaMemsetAsync(pc->ecoef, 0, (size_t)vb * cap, s));
-  pc->stream_bytes = (int64_t)S * (int64_t)sizeof(StarHdr) + 2 * pc->sum_s + (2ll + vb) * total;
+  SPNET_TRY(pc->mem.get(&pc->srec, (total > 0 ? total : 1) * RB));
+  pc->stream_bytes = (int64_t)S * (int64_t)sizeof(StarHdr) + 2 * pc->sum_s + (int64_t)RB * total;
   note_launch();
   if (vb == 8)
     k_stream_pack<double><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_mesh,
-                                                      pc->elem_ptr, pc->star_ptr, eoff, (StarHdr*)pc->shdr,
-                                                      pc->iperm_star, pc->emeta, (double*)pc->ecoef);
+                                                      pc->elem_ptr, pc->star_ptr, roff, (StarHdr*)pc->shdr,
+                                                      pc->iperm_star, pc->srec);
   else
     k_stream_pack<float><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_mesh,
-                                                     pc->elem_ptr, pc->star_ptr, eoff, (StarHdr*)pc->shdr,
-                                                     pc->iperm_star, pc->emeta, (float*)pc->ecoef);
+                                                     pc->elem_ptr, pc->star_ptr, roff, (StarHdr*)pc->shdr,
+                                                     pc->iperm_star, pc->srec);
   SPNET_CUDA_TRY(cudaGetLastError());
   // warps per block: as many as the shared-memory budget holds, at most eight
   const int64_t wb = stream_warp_bytes(vb, pc->max_star);
   int wpb = (int)(STREAM_SMEM / wb);
   wpb = wpb > 8 ? 8 : wpb;
   if (wpb < 1) return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: a star too large for the solve's shared memory");
-  pc->solve_wpb = wpb;
-  pc->solve_smem = (size_t)(wpb * wb);
   static bool attr_set[64][2] = {};
   int dev = 0;
   SPNET_CUDA_TRY(cudaGetDevice(&dev));
@@ -835,6 +888,55 @@ static int pack_streams(spnet_pc_s* pc, DevArena& tmp) {
     SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_stream<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, STREAM_SMEM));
     attr_set[dev][0] = true;
   }
+  // The solve is bound by the instruction issue of each SM, so every SM gets
+  // the same number k of blocks (a grid of k * SMs blocks; the shared memory of
+  // a block is padded so that no SM can hold more than k when they all fit in
+  // one wave) and the stars are dealt to the blocks largest first, each to the
+  // block with the least work so far.  Work of a star ~ entries / 32 + 2 levels.
+  const int nsm = num_sms();
+  int k = (int)((S + (int64_t)nsm * wpb - 1) / ((int64_t)nsm * wpb));
+  if (k < 1) k = 1;
+  size_t smem = (size_t)(wpb * wb);
+  auto occupancy = [&](size_t bytes, int* nb) -> cudaError_t {
+    return vb == 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_star_stream<double>, wpb * 32, bytes)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_star_stream<float>, wpb * 32, bytes);
+  };
+  int nb = 0;
+  SPNET_CUDA_TRY(occupancy(smem, &nb));
+  if (nb >= k) {
+    while (nb > k && smem + 1024 <= (size_t)STREAM_SMEM) {
+      smem += 1024;
+      SPNET_CUDA_TRY(occupancy(smem, &nb));
+    }
+    if (nb < k) smem -= 1024;  // never fewer than k blocks per SM
+  }
+  const int B = nsm * k;
+  std::vector<int32_t> sn(S);
+  SPNET_CUDA_TRY(cudaMemcpyAsync(sn.data(), pc->star_n, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, s));
+  SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<double> cost(S);
+  std::vector<int32_t> ord(S);
+  for (int i = 0; i < S; ++i) {
+    cost[i] = 2.0 * ((double)sn[i] + nz[i]) / 32.0 + 2.0 * lev[i];
+    ord[i] = i;
+  }
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<int32_t> slot((size_t)B * wpb, -1);
+  std::vector<int> fill(B, 0);
+  std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<std::pair<double, int>>> heap;
+  for (int b = 0; b < B; ++b) heap.push({0.0, b});
+  for (int i : ord) {
+    const std::pair<double, int> top = heap.top();
+    heap.pop();
+    const int b = top.second;
+    slot[(size_t)b * wpb + fill[b]++] = i;
+    if (fill[b] < wpb) heap.push({top.first + cost[i], b});
+  }
+  SPNET_TRY(pc->mem.get(&pc->sorder, slot.size()));
+  SPNET_CUDA_TRY(cudaMemcpyAsync(pc->sorder, slot.data(), sizeof(int32_t) * slot.size(), cudaMemcpyHostToDevice, s));
+  pc->solve_wpb = wpb;
+  pc->solve_blocks = B;
+  pc->solve_smem = smem;
   SPNET_CUDA_TRY(cudaStreamSynchronize(s));
   return SPNET_OK;
 }
@@ -842,6 +944,8 @@ static int pack_streams(spnet_pc_s* pc, DevArena& tmp) {
 int pc_factor_stars(spnet_pc_s* pc) {
   cudaStream_t s = pc->op->stream;
   if (pc->S == 0) return SPNET_OK;
+  if (pc->sum_s > INT32_MAX)
+    return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: the stars hold more than 2^31-1 entries in total");
   if (pc->max_star > STREAM_MAX_N)
     return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: a star holds more than " +
                                            std::to_string(STREAM_MAX_N) + " dofs");
@@ -958,7 +1062,7 @@ int pc_factor_stars(spnet_pc_s* pc) {
     pc->max_levels = lev[i] > pc->max_levels ? lev[i] : pc->max_levels;
   }
   // the solve streams; the set-up blobs are released
-  SPNET_TRY(pack_streams(pc, tmp));
+  SPNET_TRY(pack_streams(pc, tmp, lev, nz));
   pc->mem.release(pc->pool);
   pc->pool = nullptr;
   return SPNET_OK;

@@ -29,6 +29,7 @@ int DevArena::alloc(void** p, size_t n) {
                                          " bytes failed: " + cudaGetErrorString(e));
   }
   ptrs.push_back(*p);
+  sizes.push_back((int64_t)n);
   bytes += (int64_t)n;
   return SPNET_OK;
 }
@@ -37,7 +38,9 @@ void DevArena::release(void* p) {
   for (size_t i = 0; i < ptrs.size(); ++i) {
     if (ptrs[i] == p) {
       cudaFreeAsync(p, stream);
+      bytes -= sizes[i];
       ptrs.erase(ptrs.begin() + i);
+      sizes.erase(sizes.begin() + i);
       return;
     }
   }
@@ -46,6 +49,7 @@ void DevArena::release(void* p) {
 void DevArena::free_all() {
   for (void* p : ptrs) cudaFreeAsync(p, stream);
   ptrs.clear();
+  sizes.clear();
   bytes = 0;
 }
 
