@@ -17,25 +17,52 @@
 
 namespace spnet {
 
-constexpr int NB = 64;  // pivot block
+constexpr int NB = 64;   // pivot block, and the sub-tile a sweep block updates
+constexpr int CT = 128;  // storage tile
 
-// invert the SPD pivot block D = Z[k0.., k0..] (kb x kb) into P by scalar sweeps
-// in the arithmetic of T.  256 threads, each holding a 4 x 4 tile of D in
-// registers (thread (tr, tc) owns rows 4tr.., columns 4tc..); row and column p
-// of each step pass through shared memory, double-buffered so that one barrier
-// per step suffices.  Every thread forms 1 / D_pp itself.
+// ---------------------------------------------------------------------------
+// Storage.  Z is symmetric throughout the sweeps, so only its upper tiles
+// (I <= J) of CT x CT entries are kept, packed tile after tile (row-major inside
+// a tile, zero padded past m0); a diagonal tile holds both of its triangles.
+// The coarse product reads the same array.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int64_t n_upper_tiles(int nt) { return (int64_t)nt * (nt + 1) / 2; }
+__host__ __device__ inline int64_t tile_index(int I, int J, int nt) {
+  return (int64_t)I * nt - (int64_t)I * (I - 1) / 2 + (J - I);
+}
+
+// linear index -> (I, J) of the upper triangle of an n x n grid, row-major
+__device__ inline void upper_tile(int64_t t, int n, int* I, int* J) {
+  int i = 0;
+  while (t >= n - i) {
+    t -= n - i;
+    ++i;
+  }
+  *I = i;
+  *J = i + (int)t;
+}
+
+// entry (i, j) of the symmetric Z, any i, j
 template <class T>
-__global__ void __launch_bounds__(256) k_pivot_inverse(T* Z, int64_t ld, int k0, int kb, T* P, int* flags) {
-  __shared__ T rowp[2][NB], colp[2][NB];
+__device__ inline T zat(const T* tiles, int nt, int64_t i, int64_t j) {
+  if (i / CT > j / CT) {
+    const int64_t t = i;
+    i = j;
+    j = t;
+  }
+  return tiles[tile_index((int)(i / CT), (int)(j / CT), nt) * CT * CT + (i % CT) * CT + (j % CT)];
+}
+
+// Invert the SPD block held 4 x 4 per thread by 256 threads (thread (tr, tc)
+// owns rows 4tr.., columns 4tc.. of a 64 x 64 block; kb valid rows) by scalar
+// Gauss-Jordan sweeps in the arithmetic of T: sweeping pivot p maps
+// D_ij -> D_ij - D_ip D_pj / D_pp, D_ip -> D_ip / D_pp, D_pj -> D_pj / D_pp,
+// D_pp -> -1 / D_pp; after kb pivots the block holds -D^{-1}.  Row and column
+// p pass through shared memory, double-buffered (one barrier per pivot); every
+// thread forms 1 / D_pp itself.  Returns true where a pivot was not positive.
+template <class T>
+__device__ bool invert_block_regs(T (&d)[4][4], int kb, T (*rowp)[NB], T (*colp)[NB]) {
   const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
-  T d[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int i = 4 * tr + a, j = 4 * tc + b;
-      d[a][b] = (i < kb && j < kb) ? Z[(int64_t)(k0 + i) * ld + (k0 + j)] : (T)0;
-    }
   bool bad = false;
   for (int q = 0; q < NB / 4; ++q) {
 #pragma unroll
@@ -76,7 +103,13 @@ __global__ void __launch_bounds__(256) k_pivot_inverse(T* Z, int64_t ld, int k0,
         }
     }
   }
-  if (bad && threadIdx.x == 0) atomicOr(flags, FLAG_COARSE_SPD);
+  return bad;
+}
+
+// P = (the inverted block) = -(d after the sweeps), zero outside kb x kb
+template <class T>
+__device__ void store_pivot(const T (&d)[4][4], int kb, T* P) {
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -86,33 +119,61 @@ __global__ void __launch_bounds__(256) k_pivot_inverse(T* Z, int64_t ld, int k0,
     }
 }
 
-// R = Z[k0:k0+kb, :] (copy of the pivot rows), Tm = P R.  A block takes 16
-// columns; thread (g, c) loads column c's kb pivot-row entries and forms rows
-// 4g..4g+3 of P R for it.
+// the upper tiles of A_0 (dense FP64, m0 x m0) in the arithmetic of T
 template <class T>
-__global__ void __launch_bounds__(256) k_panel(const T* Z, int64_t m0, int64_t ld, int k0, int kb,
-                                               const T* P, T* R, T* Tm) {
+__global__ void k_tiles_from_A0(const double* __restrict__ A0, int64_t m0, int nt, T* __restrict__ tiles) {
+  int I, J;
+  upper_tile(blockIdx.x, nt, &I, &J);
+  T* out = tiles + (int64_t)blockIdx.x * CT * CT;
+  for (int q = threadIdx.x; q < CT * CT; q += blockDim.x) {
+    const int64_t i = (int64_t)I * CT + q / CT, j = (int64_t)J * CT + q % CT;
+    out[q] = (i < m0 && j < m0) ? (T)A0[i * m0 + j] : (T)0;
+  }
+}
+
+// the first pivot block (its inverse P); later ones are inverted by the sweep
+template <class T>
+__global__ void __launch_bounds__(256) k_pivot_inverse(const T* tiles, int nt, int k0, int kb, T* P, int* flags) {
+  __shared__ T rowp[2][NB], colp[2][NB];
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+  T d[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = 4 * tr + a, j = 4 * tc + b;
+      d[a][b] = (i < kb && j < kb) ? zat(tiles, nt, k0 + i, k0 + j) : (T)0;
+    }
+  const bool bad = invert_block_regs(d, kb, rowp, colp);
+  if (bad) atomicOr(flags, FLAG_COARSE_SPD);
+  store_pivot(d, kb, P);
+}
+
+// R[t][c] = Z[k0 + t][c] (the pivot rows, zero past m0), Tm = P R; rows of
+// length ldr.  A block takes 16 columns; thread (g, c) reads column c's kb
+// pivot-row entries and forms rows 4g..4g+3 of R and of P R for it.
+template <class T>
+__global__ void __launch_bounds__(256) k_panel(const T* __restrict__ tiles, int nt, int64_t m0, int64_t ldr, int k0,
+                                               int kb, const T* __restrict__ P, T* __restrict__ R,
+                                               T* __restrict__ Tm) {
   __shared__ T sP[NB][NB + 1];
   for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) sP[q / NB][q % NB] = P[q];
   __syncthreads();
   const int g = threadIdx.x >> 4;
   const int64_t c = (int64_t)blockIdx.x * 16 + (threadIdx.x & 15);
-  if (c >= m0) return;
+  if (c >= ldr) return;
   T col[NB];
 #pragma unroll
-  for (int t = 0; t < NB; ++t) col[t] = t < kb ? Z[(int64_t)(k0 + t) * ld + c] : (T)0;
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int t = 4 * g + u;
-    if (t < kb) R[(int64_t)t * m0 + c] = Z[(int64_t)(k0 + t) * ld + c];
-  }
+  for (int t = 0; t < NB; ++t) col[t] = (t < kb && c < m0) ? zat(tiles, nt, k0 + t, c) : (T)0;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int t = 4 * g + u;
     T acc = 0;
 #pragma unroll
     for (int v = 0; v < NB; ++v) acc += sP[t][v] * col[v];
-    if (t < kb) Tm[(int64_t)t * m0 + c] = acc;
+    // all NB rows: rows past kb (the last, partial pivot block) are zero
+    R[(int64_t)t * ldr + c] = (t < kb && c < m0) ? zat(tiles, nt, k0 + t, c) : (T)0;
+    Tm[(int64_t)t * ldr + c] = acc;
   }
 }
 
@@ -124,110 +185,141 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::);
 }
 
-// the rank-kb sweep update: tiles of TB x TB entries, (TB/16)^2 per thread; only
-// tiles on or above the block diagonal are computed, each writes itself and its
-// mirror image (the swept matrix stays symmetric).  The tile's old values are
-// copied to shared memory asynchronously while the update is computed.
-template <class T, int TB>
-__global__ void __launch_bounds__(256) k_sweep(T* Z, int64_t m0, int64_t ld, int k0, int kb, const T* P,
-                                               const T* __restrict__ R, const T* __restrict__ Tm) {
-  constexpr int RT = TB / 16;       // register tile
-  constexpr int SO = TB + 16 / sizeof(T);  // padded row of the staged tile (16-byte aligned)
-  extern __shared__ __align__(16) char sm_raw[];
-  T (*sR)[TB] = reinterpret_cast<T (*)[TB]>(sm_raw);
-  T (*sT)[TB] = reinterpret_cast<T (*)[TB]>(sm_raw + sizeof(T) * NB * TB);
-  T (*sO)[SO] = reinterpret_cast<T (*)[SO]>(sm_raw + 2 * sizeof(T) * NB * TB);
-  // map the linear block index to an upper-triangular tile (bi <= bj)
-  const int nt = (int)((m0 + TB - 1) / TB);
-  int rem = blockIdx.x, bi = 0;
-  while (rem >= nt - bi) {
-    rem -= nt - bi;
-    ++bi;
+template <class T>
+struct V4 {
+  T v[4];
+};
+// four consecutive T (16-byte aligned; 32 for double)
+template <class T>
+__device__ __forceinline__ V4<T> ld4s(const T* p) {
+  V4<T> r;
+  if (sizeof(T) == 4) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    r.v[0] = a.x;
+    r.v[1] = a.y;
+    r.v[2] = a.z;
+    r.v[3] = a.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *(reinterpret_cast<const double2*>(p) + 1);
+    r.v[0] = a.x;
+    r.v[1] = a.y;
+    r.v[2] = b.x;
+    r.v[3] = b.y;
   }
-  const int bj = bi + rem;
-  const int64_t i0 = (int64_t)bi * TB, j0 = (int64_t)bj * TB;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  // old tile values -> sO (16-byte chunks; rows are 16-byte aligned, ld padded)
-  constexpr int CH = TB * sizeof(T) / 16;  // chunks per tile row
-  for (int q = threadIdx.x; q < TB * CH; q += 256) {
-    const int li = q / CH, ch = q % CH;
-    const int64_t i = i0 + li, j = j0 + ch * (16 / sizeof(T));
-    if (i < m0 && j < ld) cp_async16(&sO[li][ch * (16 / sizeof(T))], &Z[i * ld + j]);
-  }
-  for (int q = threadIdx.x; q < NB * TB; q += 256) {
-    const int t = q / TB, c = q % TB;
-    sR[t][c] = (t < kb && i0 + c < m0) ? R[(int64_t)t * m0 + i0 + c] : (T)0;
-    sT[t][c] = (t < kb && j0 + c < m0) ? Tm[(int64_t)t * m0 + j0 + c] : (T)0;
-  }
-  __syncthreads();
-  T acc[RT][RT];
-#pragma unroll
-  for (int a = 0; a < RT; ++a)
-#pragma unroll
-    for (int b = 0; b < RT; ++b) acc[a][b] = 0;
-  for (int t = 0; t < kb; ++t) {
-    T ri[RT], tj[RT];
-#pragma unroll
-    for (int a = 0; a < RT; ++a) ri[a] = sR[t][ty + 16 * a];
-#pragma unroll
-    for (int b = 0; b < RT; ++b) tj[b] = sT[t][tx + 16 * b];
-#pragma unroll
-    for (int a = 0; a < RT; ++a)
-#pragma unroll
-      for (int b = 0; b < RT; ++b) acc[a][b] += ri[a] * tj[b];
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  // new values of the tile (i, j), in place in shared memory
-#pragma unroll
-  for (int a = 0; a < RT; ++a) {
-    const int li = ty + 16 * a;
-    const int64_t i = i0 + li;
-    const bool iK = i >= k0 && i < k0 + kb;
-#pragma unroll
-    for (int b = 0; b < RT; ++b) {
-      const int lj = tx + 16 * b;
-      const int64_t j = j0 + lj;
-      T v = 0;
-      if (i < m0 && j < m0) {
-        const bool jK = j >= k0 && j < k0 + kb;
-        if (!iK && !jK) v = sO[li][lj] - acc[a][b];
-        else if (iK && jK) v = -P[(i - k0) * NB + (j - k0)];
-        else if (iK) v = sT[i - k0][lj];
-        else v = Tm[(j - k0) * m0 + i];  // A_iK P = (P A_Ki)^T by symmetry
-      }
-      acc[a][b] = v;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int a = 0; a < RT; ++a)
-#pragma unroll
-    for (int b = 0; b < RT; ++b) sO[ty + 16 * a][tx + 16 * b] = acc[a][b];
-  __syncthreads();
-  for (int q = threadIdx.x; q < TB * TB; q += 256) {
-    const int li = q / TB, lj = q % TB;
-    const int64_t i = i0 + li, j = j0 + lj;
-    if (i < m0 && j < m0) Z[i * ld + j] = sO[li][lj];
-  }
-  if (bi != bj) {
-    for (int q = threadIdx.x; q < TB * TB; q += 256) {
-      const int lj = q / TB, li = q % TB;  // write the mirror tile row by row
-      const int64_t i = i0 + li, j = j0 + lj;
-      if (i < m0 && j < m0) Z[j * ld + i] = sO[li][lj];
-    }
+  return r;
+}
+template <class T>
+__device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
+  if (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *(reinterpret_cast<double2*>(p) + 1) = make_double2(v[2], v[3]);
   }
 }
 
-// mode 0: Z = A0 (rows padded to ld with zeros); mode 1: Z = -Z
+// One sweep (pivot sub-tile kp = k0 / 64 of a 64-grid with n64 sub-tiles per
+// side): every sub-tile (a, b), a <= b, of the upper tiles, 64 x 64 per block,
+// 4 x 4 per thread:
+//   a, b != kp:        Z_ab -= R[:, a]^T Tm[:, b]       (= Z_aK P Z_Kb)
+//   a == b == kp:      -P
+//   a == kp:           Tm[:, b]                          (P Z_Kb)
+//   b == kp:           Tm[:, a]^T                        (Z_aK P, by symmetry)
+// The upper-right sub-tile of a diagonal storage tile also writes its
+// transpose into the lower-left one.  Block 0 updates the next pivot block
+// (kp + 1, kp + 1) and then inverts it into Pn: the next step needs no
+// separate pivot kernel, and its work hides behind the other blocks.
 template <class T>
-__global__ void k_negate_from(const double* A0, T* Z, int64_t m0, int64_t ld, int mode) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m0 * ld;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = q / ld, j = q % ld;
-    if (mode == 0) Z[q] = j < m0 ? (T)A0[i * m0 + j] : (T)0;
-    else Z[q] = -Z[q];
+__global__ void __launch_bounds__(256) k_sweep(T* __restrict__ tiles, int nt, int n64, int64_t m0, int64_t ldr,
+                                               int k0, const T* __restrict__ P, const T* __restrict__ R,
+                                               const T* __restrict__ Tm, T* __restrict__ Pn, int* flags) {
+  extern __shared__ __align__(16) char sm_sweep[];  // R and Tm slices, NB x NB each
+  T (*sR)[NB] = reinterpret_cast<T (*)[NB]>(sm_sweep);
+  T (*sT)[NB] = reinterpret_cast<T (*)[NB]>(sm_sweep + sizeof(T) * NB * NB);
+  const int kp = k0 / NB;
+  const bool has_next = (int64_t)(kp + 1) * NB < m0;
+  // block -> sub-tile: block 0 takes the next pivot block, the rest go in order
+  int64_t L = blockIdx.x;
+  if (has_next) {
+    const int64_t Lp = tile_index(kp + 1, kp + 1, n64);
+    L = blockIdx.x == 0 ? Lp : ((int64_t)blockIdx.x <= Lp ? (int64_t)blockIdx.x - 1 : (int64_t)blockIdx.x);
   }
+  int a, b;
+  upper_tile(L, n64, &a, &b);
+  const int64_t i0 = (int64_t)a * NB, j0 = (int64_t)b * NB;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  T* zt = tiles + tile_index(a >> 1, b >> 1, nt) * CT * CT + (a & 1) * NB * CT + (b & 1) * NB;
+  // R and Tm slices -> shared memory (16-byte chunks; rows of length ldr, a multiple of 64)
+  constexpr int CH = NB * (int)sizeof(T) / 16;  // chunks per row
+  for (int q = threadIdx.x; q < NB * CH; q += 256) {
+    const int t = q / CH, ch = q % CH;
+    const int e = ch * (16 / (int)sizeof(T));
+    cp_async16(&sR[t][e], R + (int64_t)t * ldr + i0 + e);
+    cp_async16(&sT[t][e], Tm + (int64_t)t * ldr + j0 + e);
+  }
+  // old values
+  T d[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const V4<T> o = ld4s(zt + (4 * ty + u) * CT + 4 * tx);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) d[u][v] = o.v[v];
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int kb = (int)((m0 - k0) < NB ? (m0 - k0) : NB);
+  if (a != kp && b != kp) {
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = (T)0;
+    for (int t = 0; t < kb; ++t) {
+      const V4<T> ri = ld4s(&sR[t][4 * ty]);
+      const V4<T> tj = ld4s(&sT[t][4 * tx]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] += ri.v[u] * tj.v[v];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) d[u][v] -= acc[u][v];
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int li = 4 * ty + u, lj = 4 * tx + v;
+        if (a == kp && b == kp) d[u][v] = -P[li * NB + lj];
+        else if (a == kp) d[u][v] = sT[li][lj];
+        else d[u][v] = Tm[(int64_t)lj * ldr + i0 + li];
+      }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) st4(zt + (4 * ty + u) * CT + 4 * tx, d[u]);
+  if ((a & 1) == 0 && b == a + 1) {  // mirror into the lower-left sub-tile of the diagonal tile
+    T* zl = tiles + tile_index(a >> 1, a >> 1, nt) * CT * CT + NB * CT;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const T col[4] = {d[0][v], d[1][v], d[2][v], d[3][v]};
+      st4(zl + (4 * tx + v) * CT + 4 * ty, col);
+    }
+  }
+  if (has_next && blockIdx.x == 0) {  // the next pivot block, already updated: invert it
+    __shared__ T rowp[2][NB], colp[2][NB];
+    const int kbn = (int)((m0 - k0 - NB) < NB ? (m0 - k0 - NB) : NB);
+    const bool bad = invert_block_regs(d, kbn, rowp, colp);
+    if (bad) atomicOr(flags, FLAG_COARSE_SPD);
+    store_pivot(d, kbn, Pn);
+  }
+}
+
+template <class T>
+__global__ void k_negate(T* z, int64_t n) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    z[q] = -z[q];
 }
 
 template <class T>
@@ -240,44 +332,49 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
     DevArena& a;
     ~Guard() { a.free_all(); }
   } guard{tmp};
-  // rows padded to 16 bytes so that the coarse product can load them as vectors
-  const int64_t ld = (m0 + (16 / (int64_t)sizeof(T)) - 1) / (16 / (int64_t)sizeof(T)) * (16 / (int64_t)sizeof(T));
-  T* Z = nullptr;
-  SPNET_TRY(pc->mem.get(&Z, m0 * ld));
-  pc->Z = Z;
-  pc->ldz = ld;
+  const int nt = (int)((m0 + CT - 1) / CT);
+  const int n64 = (int)((m0 + NB - 1) / NB);
+  const int64_t ldr = (int64_t)n64 * NB;
+  const int64_t nti = n_upper_tiles(nt);
+  T* tiles = nullptr;
+  SPNET_TRY(pc->mem.get(&tiles, nti * CT * CT));
+  pc->ctiles = tiles;
+  pc->ctiles_n = nt;
   T *P = nullptr, *R = nullptr, *Tm = nullptr;
-  SPNET_TRY(tmp.get(&P, NB * NB));
-  SPNET_TRY(tmp.get(&R, NB * m0));
-  SPNET_TRY(tmp.get(&Tm, NB * m0));
-  const int grid = 4 * num_sms();
+  SPNET_TRY(tmp.get(&P, 2 * NB * NB));
+  SPNET_TRY(tmp.get(&R, NB * ldr));
+  SPNET_TRY(tmp.get(&Tm, NB * ldr));
+  SPNET_CUDA_TRY(cudaMemsetAsync(R, 0, sizeof(T) * NB * ldr, s));
+  SPNET_CUDA_TRY(cudaMemsetAsync(Tm, 0, sizeof(T) * NB * ldr, s));
   note_launch();
-  k_negate_from<T><<<grid, 256, 0, s>>>(A0, Z, m0, ld, 0);
+  k_tiles_from_A0<T><<<(unsigned)nti, 256, 0, s>>>(A0, m0, nt, tiles);
   SPNET_CUDA_TRY(cudaMemsetAsync(pc->op->dflags, 0, sizeof(int), s));
-  constexpr int TB = sizeof(T) == 4 ? 128 : 64;
-  const int nt = (int)((m0 + TB - 1) / TB);
-  const unsigned tiles = (unsigned)(nt * (nt + 1) / 2);
-  const size_t smem = sizeof(T) * (2 * NB * TB + TB * (TB + 16 / sizeof(T)));
-  static bool attr_set[64] = {};  // per device and instantiation; the size depends only on T
-  int dev = 0;
-  SPNET_CUDA_TRY(cudaGetDevice(&dev));
-  dev &= 63;
-  if (!attr_set[dev]) {
-    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_sweep<T, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set[dev] = true;
+  note_launch();
+  k_pivot_inverse<T><<<1, 256, 0, s>>>(tiles, nt, 0, (int)(m0 < NB ? m0 : NB), P, pc->op->dflags);
+  const unsigned subtiles = (unsigned)n_upper_tiles(n64);
+  const size_t sweep_smem = 2 * sizeof(T) * NB * NB;
+  if (sweep_smem > 48 * 1024) {
+    static bool attr_set[64] = {};  // per device; the size depends only on T
+    int dev = 0;
+    SPNET_CUDA_TRY(cudaGetDevice(&dev));
+    dev &= 63;
+    if (!attr_set[dev]) {
+      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem));
+      attr_set[dev] = true;
+    }
   }
-  for (int k0 = 0; k0 < m0; k0 += NB) {
+  for (int k0 = 0, step = 0; k0 < m0; k0 += NB, ++step) {
     const int kb = (int)((m0 - k0) < NB ? (m0 - k0) : NB);
+    T* Pc = P + (step & 1) * NB * NB;
+    T* Pn = P + ((step + 1) & 1) * NB * NB;
     note_launch();
-    k_pivot_inverse<T><<<1, 256, 0, s>>>(Z, ld, k0, kb, P, pc->op->dflags);
-    note_launch();
-    k_panel<T><<<(unsigned)((m0 + 15) / 16), 256, 0, s>>>(Z, m0, ld, k0, kb, P, R, Tm);
+    k_panel<T><<<(unsigned)(ldr / 16), 256, 0, s>>>(tiles, nt, m0, ldr, k0, kb, Pc, R, Tm);
     note_launch();
     ProfScope ps(KID_SWEEP, s);
-    k_sweep<T, TB><<<tiles, 256, smem, s>>>(Z, m0, ld, k0, kb, P, R, Tm);
+    k_sweep<T><<<subtiles, 256, sweep_smem, s>>>(tiles, nt, n64, m0, ldr, k0, Pc, R, Tm, Pn, pc->op->dflags);
   }
   note_launch();
-  k_negate_from<T><<<grid, 256, 0, s>>>(A0, Z, m0, ld, 1);
+  k_negate<T><<<4 * num_sms(), 256, 0, s>>>(tiles, nti * CT * CT);
   SPNET_CUDA_TRY(cudaGetLastError());
   return check_flags(pc->op->dflags, s, "setup_preconditioner (coarse matrix)");
 }
@@ -299,32 +396,6 @@ int pc_coarse_invert(spnet_pc_s* pc, double* A0) {
 // written; the block that writes the last one sums part[R][0..nt-1] in K order
 // (deterministic) into z_c and resets the counter for the next application.
 // ---------------------------------------------------------------------------
-constexpr int CT = 128;
-
-__host__ __device__ inline int64_t n_upper_tiles(int nt) { return (int64_t)nt * (nt + 1) / 2; }
-
-// linear upper-tile index -> (I, J), row-major over I <= J
-__device__ inline void upper_tile(int t, int nt, int* I, int* J) {
-  int i = 0;
-  while (t >= nt - i) {
-    t -= nt - i;
-    ++i;
-  }
-  *I = i;
-  *J = i + t;
-}
-
-template <class T>
-__global__ void k_pack_tiles(const T* __restrict__ Z, int64_t m0, int64_t ld, int nt, T* __restrict__ tiles) {
-  int I, J;
-  upper_tile(blockIdx.x, nt, &I, &J);
-  T* out = tiles + (int64_t)blockIdx.x * CT * CT;
-  for (int q = threadIdx.x; q < CT * CT; q += blockDim.x) {
-    const int64_t i = (int64_t)I * CT + q / CT, j = (int64_t)J * CT + q % CT;
-    out[q] = (i < m0 && j < m0) ? Z[i * ld + j] : (T)0;
-  }
-}
-
 template <class T>
 struct Vec4 {
   T v[4];
@@ -376,6 +447,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_coarse_symv(con
   __shared__ T sI[CT], sJ[CT];
   __shared__ T scol[8][CT];
   __shared__ int red[2];
+  pdl_wait();
+  pdl_trigger();
   if (done && *done) return;
   int I, J;
   upper_tile(blockIdx.x, nt, &I, &J);
@@ -468,11 +541,11 @@ void launch_coarse_apply(spnet_pc_s* pc, const double* rc, double* zc, const int
   note_launch();
   ProfScope ps(KID_COARSE, s);
   if (pc->precision == SPNET_PREC_FP64)
-    k_coarse_symv<double><<<tiles, 256, 0, s>>>((const double*)pc->ctiles, pc->ctiles_n, pc->m0, rc, pc->epart,
-                                                 pc->rtab, (double*)pc->cpart, pc->ccnt, zc, done);
+    launch_pdl(k_coarse_symv<double>, tiles, 256, 0, s, (const double*)pc->ctiles, pc->ctiles_n, (int64_t)pc->m0,
+               rc, (const double*)pc->epart, (const int32_t*)pc->rtab, (double*)pc->cpart, pc->ccnt, zc, done);
   else
-    k_coarse_symv<float><<<tiles, 256, 0, s>>>((const float*)pc->ctiles, pc->ctiles_n, pc->m0, rc, pc->epart,
-                                                pc->rtab, (float*)pc->cpart, pc->ccnt, zc, done);
+    launch_pdl(k_coarse_symv<float>, tiles, 256, 0, s, (const float*)pc->ctiles, pc->ctiles_n, (int64_t)pc->m0,
+               rc, (const double*)pc->epart, (const int32_t*)pc->rtab, (float*)pc->cpart, pc->ccnt, zc, done);
 }
 
 // rtab[ci][cp]: offset of the corner sum of the element at position cp around
@@ -496,15 +569,12 @@ __global__ void k_restrict_table(int64_t nmc, Mesh m, int ndof, const int32_t* _
   }
 }
 
-// pack the upper tiles of Z, release the full matrix, allocate the parts and counters
+// the partial products, their counters and the restriction table of the product
 template <class T>
-static int pack_coarse_tiles(spnet_pc_s* pc) {
+static int prepare_product(spnet_pc_s* pc) {
   cudaStream_t s = pc->op->stream;
-  const int nt = (int)((pc->m0 + CT - 1) / CT);
-  const int64_t nti = n_upper_tiles(nt);
-  T* tiles = nullptr;
+  const int nt = pc->ctiles_n;
   T* part = nullptr;
-  SPNET_TRY(pc->mem.get(&tiles, nti * CT * CT));
   SPNET_TRY(pc->mem.get(&part, (int64_t)nt * nt * CT));
   SPNET_TRY(pc->mem.get(&pc->ccnt, nt));
   SPNET_CUDA_TRY(cudaMemsetAsync(pc->ccnt, 0, sizeof(unsigned) * nt, s));
@@ -514,21 +584,15 @@ static int pack_coarse_tiles(spnet_pc_s* pc) {
   SPNET_TRY(pc->mem.get(&pc->rtab, 8ll * pc->m0));
   note_launch();
   k_restrict_table<<<(unsigned)((nmc + 255) / 256), 256, 0, s>>>(nmc, mesh_of_pc(pc), pc->ndof, pc->cidx, pc->rtab);
-  note_launch();
-  k_pack_tiles<T><<<(unsigned)nti, 256, 0, s>>>((const T*)pc->Z, pc->m0, pc->ldz, nt, tiles);
   SPNET_CUDA_TRY(cudaGetLastError());
-  pc->mem.release(pc->Z);
-  pc->Z = nullptr;
-  pc->ctiles = tiles;
   pc->cpart = part;
-  pc->ctiles_n = nt;
   return SPNET_OK;
 }
 
 int coarse_gemv_prepare(spnet_pc_s* pc) {
   if (pc->m0 == 0) return SPNET_OK;
-  if (pc->precision == SPNET_PREC_FP64) return pack_coarse_tiles<double>(pc);
-  return pack_coarse_tiles<float>(pc);
+  if (pc->precision == SPNET_PREC_FP64) return prepare_product<double>(pc);
+  return prepare_product<float>(pc);
 }
 
 }  // namespace spnet

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/spnet.h"
@@ -129,9 +130,7 @@ struct spnet_pc_s {
   // coarse space
   int m0 = 0;
   int32_t* cidx = nullptr;     // [n_mesh*ndof]
-  void* Z = nullptr;           // [m0*ldz] A_0^{-1} during set-up (float or double by precision), rows padded
-  int64_t ldz = 0;
-  void* ctiles = nullptr;      // upper CT x CT tiles of Z, packed (the product reads these)
+  void* ctiles = nullptr;      // A_0^{-1} (float or double by precision): its upper 128 x 128 tiles, packed
   void* cpart = nullptr;       // [nt*nt*CT] per row block and tile column: partial products
   unsigned* ccnt = nullptr;    // [nt] parts written per row block (zero between applications)
   int ctiles_n = 0;            // nt: tiles per dimension
@@ -333,6 +332,32 @@ __device__ __forceinline__ int rs_index(int lane) {
 template <int K>
 __device__ __forceinline__ bool rs_writer(int lane) {
   return (lane & (32 / K - 1)) == 0;
+}
+
+// Programmatic dependent launch.  A kernel of the iteration lets the next
+// kernel of its stream launch as soon as all of its blocks run
+// (pdl_trigger), and waits, before it reads anything the previous kernel
+// wrote, until that kernel has finished and its memory is visible (pdl_wait).
+// Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+// launch with programmatic stream serialization: the kernel may start while
+// the previous kernel of the stream finishes (it must call pdl_wait first)
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // Q1 values phi_c = prod_a (bit a of c ? xi_a : 1 - xi_a) at local coordinates
