@@ -100,7 +100,7 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
   if ((rc = pc_elem_tables(pc))) return bail(rc);
   // work vectors
   const int64_t N = pc->N;
-  if ((rc = pc->mem.get(&pc->x, N)) || (rc = pc->mem.get(&pc->r, N)) || (rc = pc->mem.get(&pc->p, N)) ||
+  if ((rc = pc->mem.get(&pc->x, N)) || (rc = pc->mem.get(&pc->r, N)) || (rc = pc->mem.get(&pc->r2, N)) || (rc = pc->mem.get(&pc->p, N)) ||
       (rc = pc->mem.get(&pc->q, N)) || (rc = pc->mem.get(&pc->z, N)) || (rc = pc->mem.get(&pc->b, N)) ||
       (rc = pc->mem.get(&pc->vtmp, N)) || (rc = pc->mem.alloc(&pc->w, (size_t)(pc->sum_s > 0 ? pc->sum_s : 1) * (pc->precision == SPNET_PREC_FP64 ? 8 : 4))) ||
       (rc = pc->mem.get(&pc->rc, pc->m0 > 0 ? pc->m0 : 1)) ||

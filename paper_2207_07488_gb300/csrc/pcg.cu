@@ -47,10 +47,28 @@ __device__ __forceinline__ bool last_block(unsigned* cnt) {
   return is_last;
 }
 
+// a thread's share of the sum of n partials: part[tid], part[tid + B], ... in
+// that order, eight L2 loads in flight (the partials were written by other
+// blocks or by the previous kernel)
+__device__ __forceinline__ double thread_share(const double* part, int n) {
+  double s = 0.0;
+  constexpr int U = 8;
+  for (int i0 = threadIdx.x; i0 < n; i0 += U * (int)blockDim.x) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      v[u] = i < n ? __ldcg(part + i) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) s += v[u];
+  }
+  return s;
+}
+
 // sum of n partials by one block in a fixed order (result valid in every thread)
 __device__ __forceinline__ double block_sum(const double* part, int n, double* sh) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += ((volatile const double*)part)[i];
+  double s = thread_share(part, n);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -58,6 +76,25 @@ __device__ __forceinline__ double block_sum(const double* part, int n, double* s
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
   __syncthreads();
   return t;
+}
+
+// three such sums at once (sh holds 3 * 32 doubles)
+__device__ __forceinline__ void block_sum3(const double* p0, int n0, const double* p1, int n1, const double* p2,
+                                           int n2, double* sh, double* out) {
+  double s[3] = {thread_share(p0, n0), thread_share(p1, n1), thread_share(p2, n2)};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    if ((threadIdx.x & 31) == 0) sh[32 * k + (threadIdx.x >> 5)] = s[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[32 * k + w];
+    out[k] = t;
+  }
+  __syncthreads();
 }
 
 // b = f_I - K_ID g (Section 3), in pc order
@@ -124,6 +161,8 @@ __global__ void __launch_bounds__(256) k_spmv_dir(int64_t n, const int64_t* __re
                                                   const double* __restrict__ z, double* __restrict__ p,
                                                   double* __restrict__ q, double* partial, Scal* sc) {
   __shared__ double sh[32];
+  pdl_wait();
+  pdl_trigger();
   if (sc->done) return;
   const double beta = sc->beta;
   constexpr int RPW = 32 / L;
@@ -163,20 +202,24 @@ __global__ void __launch_bounds__(256) k_spmv_dir(int64_t n, const int64_t* __re
 }
 
 // ---------------------------------------------------------------------------
-// update (one warp per element): x += alpha p, r -= alpha q (mode 0) or r as is
-// (mode 1); block partials of |r|^2; corner sums E[e][c][a] = sum_{p in e,
-// comp a} phi_c(p) r_p.
+// update (one warp per element): x += alpha p, rout = r - alpha q (mode 0; a
+// different buffer, the star solves read r meanwhile) or r as is (mode 1);
+// block partials of |r|^2; corner sums E[e][c][a] = sum_{p in e, comp a}
+// phi_c(p) r_p.
 // ---------------------------------------------------------------------------
 template <int NC, int ND, class CT>
 __global__ void __launch_bounds__(256, ND == 1 ? 4 : 2) k_update(int n_elem, int64_t N, const int32_t* __restrict__ elem_ptr,
                                                 const int8_t* __restrict__ comp_of,
                                                 const CT* __restrict__ xi, double* __restrict__ x,
-                                                double* __restrict__ r, const double* __restrict__ p,
+                                                const double* __restrict__ r, double* __restrict__ rout,
+                                                const double* __restrict__ p,
                                                 const double* __restrict__ q, double* __restrict__ epart,
                                                 const double* __restrict__ ppq, int npq, double* partial,
                                                 Scal* sc, int mode) {
   constexpr int D = NC == 4 ? 2 : 3;
   __shared__ double sh[32];
+  pdl_wait();
+  pdl_trigger();
   if (mode == 0 && sc->done) return;
   // alpha = (r, z) / (p, q): every block sums the SpMV's partials in the same order
   const double alpha = mode == 0 ? sc->rz / block_sum(ppq, npq, sh) : 0.0;
@@ -218,7 +261,7 @@ __global__ void __launch_bounds__(256, ND == 1 ? 4 : 2) k_update(int n_elem, int
         if (mode == 0) {
           x[ii[h]] = fma(alpha, pv[h], xv[h]);
           v = fma(-alpha, qv[h], rv[h]);
-          r[ii[h]] = v;
+          rout[ii[h]] = v;
         } else {
           v = rv[h];
         }
@@ -288,6 +331,8 @@ __global__ void __launch_bounds__(128, ND == 1 ? 7 : 4) k_combine(int n_elem, in
                                                  int flexible, int first) {
   constexpr int D = NC == 4 ? 2 : 3;
   __shared__ double sh[32];
+  pdl_wait();
+  pdl_trigger();
   if (sc && sc->done) return;
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -352,10 +397,11 @@ __global__ void __launch_bounds__(128, ND == 1 ? 7 : 4) k_combine(int n_elem, in
   block_partial(s1, part1, sh);
   block_partial(s2, part2, sh);
   if (last_block(&sc->cnt[2])) {
-    const double rz_new = block_sum(part1, gridDim.x, sh);
-    const double rzo = block_sum(part2, gridDim.x, sh);
     // in a PCG step also |r|^2 of the update, the iteration count and the stop test
-    const double rr = first ? 0.0 : block_sum(prr, nrr, sh);
+    __shared__ double sh3[96];
+    double tot[3];
+    block_sum3(part1, gridDim.x, part2, gridDim.x, prr, first ? 0 : nrr, sh3, tot);
+    const double rz_new = tot[0], rzo = tot[1], rr = tot[2];
     if (threadIdx.x == 0) {
       double beta = 0.0;
       if (!first) beta = flexible ? (rz_new - rzo) / sc->rz : rz_new / sc->rz;
@@ -405,30 +451,31 @@ static int elem_grid(const spnet_pc_s* pc, int warps) {
 }
 
 template <int NC, int ND, class CT>
-static void launch_update_t(spnet_pc_s* pc, const CT* xi, double* x, double* r, const double* p, const double* q,
-                            Scal* sc, int mode, cudaStream_t s) {
-  k_update<NC, ND, CT><<<elem_grid(pc, 8), 256, 0, s>>>(pc->n_elem, pc->N, pc->elem_ptr, pc->comp_of, xi, x, r, p,
-                                                       q, pc->epart, pc->pspmv, pc->spmv_blocks,
-                                                       pc->partial + pc->PG, sc, mode);
+static void launch_update_t(spnet_pc_s* pc, const CT* xi, double* x, const double* r, double* rout,
+                            const double* p, const double* q, Scal* sc, int mode, cudaStream_t s) {
+  launch_pdl(k_update<NC, ND, CT>, elem_grid(pc, 8), 256, 0, s, pc->n_elem, pc->N, (const int32_t*)pc->elem_ptr,
+             (const int8_t*)pc->comp_of, xi, x, r, rout, p, q, pc->epart, (const double*)pc->pspmv,
+             pc->spmv_blocks, pc->partial + pc->PG, sc, mode);
 }
 
 template <class CT>
-static void launch_update_c(spnet_pc_s* pc, const CT* xi, double* x, double* r, const double* p, const double* q,
-                            Scal* sc, int mode, cudaStream_t s) {
-  if (pc->nc == 4 && pc->ndof == 1) launch_update_t<4, 1>(pc, xi, x, r, p, q, sc, mode, s);
-  else if (pc->nc == 8 && pc->ndof == 1) launch_update_t<8, 1>(pc, xi, x, r, p, q, sc, mode, s);
-  else if (pc->nc == 4) launch_update_t<4, 3>(pc, xi, x, r, p, q, sc, mode, s);
-  else launch_update_t<8, 3>(pc, xi, x, r, p, q, sc, mode, s);
+static void launch_update_c(spnet_pc_s* pc, const CT* xi, double* x, const double* r, double* rout,
+                            const double* p, const double* q, Scal* sc, int mode, cudaStream_t s) {
+  if (pc->nc == 4 && pc->ndof == 1) launch_update_t<4, 1>(pc, xi, x, r, rout, p, q, sc, mode, s);
+  else if (pc->nc == 8 && pc->ndof == 1) launch_update_t<8, 1>(pc, xi, x, r, rout, p, q, sc, mode, s);
+  else if (pc->nc == 4) launch_update_t<4, 3>(pc, xi, x, r, rout, p, q, sc, mode, s);
+  else launch_update_t<8, 3>(pc, xi, x, r, rout, p, q, sc, mode, s);
 }
 
+// mode 0: x += alpha p, rout = r - alpha q; mode 1: r as is (rout unused).
 // exact: the corner sums in FP64 whatever the precision (the stand-alone
 // restriction); otherwise in the arithmetic of the preconditioner
-static void launch_update(spnet_pc_s* pc, double* x, double* r, const double* p, const double* q,
-                          Scal* sc, int mode, cudaStream_t s, int exact = 0) {
+static void launch_update(spnet_pc_s* pc, double* x, const double* r, double* rout, const double* p,
+                          const double* q, Scal* sc, int mode, cudaStream_t s, int exact = 0) {
   note_launch();
   ProfScope ps(KID_UPDATE, s);
-  if (exact || pc->precision == SPNET_PREC_FP64) launch_update_c<double>(pc, pc->xi, x, r, p, q, sc, mode, s);
-  else launch_update_c<float>(pc, pc->xi32, x, r, p, q, sc, mode, s);
+  if (exact || pc->precision == SPNET_PREC_FP64) launch_update_c<double>(pc, pc->xi, x, r, rout, p, q, sc, mode, s);
+  else launch_update_c<float>(pc, pc->xi32, x, r, rout, p, q, sc, mode, s);
 }
 
 static void launch_spmv_dir(spnet_pc_s* pc, cudaStream_t s) {
@@ -437,13 +484,17 @@ static void launch_spmv_dir(spnet_pc_s* pc, cudaStream_t s) {
   const Csr& A = pc->K;
   const int G = pc->spmv_blocks;
   double* part = pc->pspmv;
+  auto go = [&](auto kernel) {
+    launch_pdl(kernel, G, 256, 0, s, A.n, (const int64_t*)A.ptr, (const int32_t*)A.col, (const double*)A.val,
+               (const double*)pc->z, pc->p, pc->q, part, pc->scal);
+  };
   switch (pc->spmv_lanes) {
-    case 1: k_spmv_dir<1><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, part, pc->scal); break;
-    case 2: k_spmv_dir<2><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, part, pc->scal); break;
-    case 4: k_spmv_dir<4><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, part, pc->scal); break;
-    case 8: k_spmv_dir<8><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, part, pc->scal); break;
-    case 16: k_spmv_dir<16><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, part, pc->scal); break;
-    default: k_spmv_dir<32><<<G, 256, 0, s>>>(A.n, A.ptr, A.col, A.val, pc->z, pc->p, pc->q, part, pc->scal); break;
+    case 1: go(k_spmv_dir<1>); break;
+    case 2: go(k_spmv_dir<2>); break;
+    case 4: go(k_spmv_dir<4>); break;
+    case 8: go(k_spmv_dir<8>); break;
+    case 16: go(k_spmv_dir<16>); break;
+    default: go(k_spmv_dir<32>); break;
   }
 }
 
@@ -460,11 +511,12 @@ void launch_restrict(spnet_pc_s* pc, double* rc, const int* done, cudaStream_t s
 template <int NC, int ND, class CT, class WS>
 static void launch_combine_t(spnet_pc_s* pc, const CT* xi, const WS* w, const double* r, double* z,
                              int with_coarse, int with_stars, int dots, cudaStream_t s) {
-  k_combine<NC, ND, CT, WS><<<elem_grid(pc, 4), 128, 0, s>>>(
-      pc->n_elem, pc->N, pc->elem_ptr, pc->comp_of, xi, pc->ecoarse, pc->estar, pc->zc, w, r, z,
-      pc->partial + 2 * pc->PG, pc->partial + 3 * pc->PG, pc->partial + pc->PG, elem_grid(pc, 8),
-      with_coarse && pc->m0 > 0, with_stars && pc->S > 0, dots ? pc->scal : nullptr, pc->flexible,
-      dots == 2 ? 1 : 0);
+  launch_pdl(k_combine<NC, ND, CT, WS>, elem_grid(pc, 4), 128, 0, s, pc->n_elem, pc->N,
+             (const int32_t*)pc->elem_ptr, (const int8_t*)pc->comp_of, xi, (const int32_t*)pc->ecoarse,
+             (const int64_t*)pc->estar, (const double*)pc->zc, w, r, z, pc->partial + 2 * pc->PG,
+             pc->partial + 3 * pc->PG, (const double*)(pc->partial + pc->PG), elem_grid(pc, 8),
+             (int)(with_coarse && pc->m0 > 0), (int)(with_stars && pc->S > 0), dots ? pc->scal : nullptr,
+             pc->flexible, dots == 2 ? 1 : 0);
 }
 
 template <class CT, class WS>
@@ -496,32 +548,38 @@ void launch_combine(spnet_pc_s* pc, const double* r, double* z, int with_coarse,
 static void precond_any(spnet_pc_s* pc, double* r, double* z, int with_coarse, int with_stars, int dots,
                         cudaStream_t s) {
   if (with_coarse && pc->m0 > 0) {
-    launch_update(pc, nullptr, r, nullptr, nullptr, pc->scal, 1, s);
+    launch_update(pc, nullptr, r, nullptr, nullptr, nullptr, pc->scal, 1, s);
     launch_coarse_apply(pc, nullptr, pc->zc, nullptr, s);  // restriction fused
   }
-  if (with_stars) launch_star_solve(pc, r, nullptr, s);
+  if (with_stars) launch_star_solve(pc, r, nullptr, nullptr, nullptr, s);
   launch_combine(pc, r, z, with_coarse, with_stars, dots, s);
 }
 
-// one PCG iteration; the star solves go to the side stream when `side` is set
-static void iteration(spnet_pc_s* pc, cudaStream_t s, cudaStream_t side) {
+// one PCG iteration; the star solves go to the side stream when `side` is set.
+// The residual alternates between pc->r and pc->r2 (parity): the update writes
+// the new residual into the other buffer while the star solves, started right
+// after the SpMV, form the same values from the old residual, q and alpha.
+static void iteration(spnet_pc_s* pc, cudaStream_t s, cudaStream_t side, int parity) {
   const int* done = &pc->scal->done;
+  double* rc = parity ? pc->r2 : pc->r;  // residual of the previous iteration
+  double* rn = parity ? pc->r : pc->r2;  // residual of this one
   launch_spmv_dir(pc, s);
-  launch_update(pc, pc->x, pc->r, pc->p, pc->q, pc->scal, 0, s);
   if (side) {
     cudaEventRecord(pc->ev_fork, s);
     cudaStreamWaitEvent(side, pc->ev_fork, 0);
-    launch_star_solve(pc, pc->r, done, side);
+    launch_star_solve(pc, rc, pc->q, pc->scal, done, side);
     cudaEventRecord(pc->ev_join, side);
   } else {
-    launch_star_solve(pc, pc->r, done, s);
+    launch_star_solve(pc, rc, pc->q, pc->scal, done, s);
   }
+  launch_update(pc, pc->x, rc, rn, pc->p, pc->q, pc->scal, 0, s);
   launch_coarse_apply(pc, nullptr, pc->zc, done, s);  // restriction fused
   if (side) cudaStreamWaitEvent(s, pc->ev_join, 0);
-  launch_combine(pc, pc->r, pc->z, 1, 1, 1, s);
+  launch_combine(pc, rn, pc->z, 1, 1, 1, s);
 }
 
-constexpr int CHUNK = 8;
+constexpr int CHUNK = 8;  // even: a chunk leaves the residual in pc->r
+static_assert(CHUNK % 2 == 0, "the residual buffers alternate per iteration");
 
 // the chunk of iterations as a CUDA graph (captured once per preconditioner)
 static int chunk_graph(spnet_pc_s* pc, cudaStream_t s) {
@@ -534,7 +592,7 @@ static int chunk_graph(spnet_pc_s* pc, cudaStream_t s) {
   cudaGraph_t g = nullptr;
   SPNET_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   const long long before = launch_count();
-  for (int it = 0; it < CHUNK; ++it) iteration(pc, s, pc->side);
+  for (int it = 0; it < CHUNK; ++it) iteration(pc, s, pc->side, it & 1);
   pc->graph_launches = (int)(launch_count() - before);
   add_launches(-pc->graph_launches);  // captured, not launched
   cudaError_t e = cudaStreamEndCapture(s, &g);
@@ -551,7 +609,7 @@ static int chunk_graph(spnet_pc_s* pc, cudaStream_t s) {
 static int run_chunk(spnet_pc_s* pc, cudaStream_t s) {
   if (profiling_on()) {
     // eager launches so that every kernel can be timed with its own events
-    for (int it = 0; it < CHUNK; ++it) iteration(pc, s, nullptr);
+    for (int it = 0; it < CHUNK; ++it) iteration(pc, s, nullptr, it & 1);
     return SPNET_OK;
   }
   SPNET_TRY(chunk_graph(pc, s));
@@ -644,7 +702,7 @@ int pc_restrict_free(spnet_pc_s* pc, const double* r_free, double* rc) {
   cudaStream_t s = pc->op->stream;
   to_pc(pc, r_free, pc->vtmp);
   if (pc->m0 == 0) return SPNET_OK;
-  launch_update(pc, nullptr, pc->vtmp, nullptr, nullptr, pc->scal, 1, s, 1);
+  launch_update(pc, nullptr, pc->vtmp, nullptr, nullptr, nullptr, pc->scal, 1, s, 1);
   launch_restrict(pc, rc, nullptr, s);
   SPNET_CUDA_TRY(cudaGetLastError());
   return SPNET_OK;

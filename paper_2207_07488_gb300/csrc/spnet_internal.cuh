@@ -161,6 +161,7 @@ struct spnet_pc_s {
   int32_t* sorder = nullptr;       // [solve_blocks*solve_wpb] star of each warp slot, -1: idle
   // work vectors (pc order)
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *b = nullptr;
+  double* r2 = nullptr;            // second residual buffer (the iterations alternate)
   double *rc = nullptr, *zc = nullptr, *partial = nullptr, *vtmp = nullptr;
   void* w = nullptr;               // [sum_s] star results in the solve precision (float or double)
   double* epart = nullptr;         // [n_elem*nc*ndof] Q1-weighted corner sums of r
@@ -278,7 +279,9 @@ int pc_galerkin(spnet_pc_s* pc, double* A0_dense);
 
 // starfact.cu
 int pc_factor_stars(spnet_pc_s* pc);
-void launch_star_solve(spnet_pc_s* pc, const double* r, const int* done, cudaStream_t s);
+// stars on r, or (q set: a PCG step) on r - alpha q with alpha from the SpMV's partials
+void launch_star_solve(spnet_pc_s* pc, const double* r, const double* q, const spnet::Scal* sc, const int* done,
+                       cudaStream_t s);
 
 // coarse.cu
 int pc_coarse_invert(spnet_pc_s* pc, double* A0_dense);
