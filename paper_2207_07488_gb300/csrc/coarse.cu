@@ -149,13 +149,14 @@ __global__ void __launch_bounds__(256) k_pivot_inverse(const T* tiles, int nt, i
   store_pivot(d, kb, P);
 }
 
-// R[t][c] = Z[k0 + t][c] (the pivot rows, zero past m0), Tm = P R; rows of
-// length ldr.  A block takes 16 columns; thread (g, c) reads column c's kb
-// pivot-row entries and forms rows 4g..4g+3 of R and of P R for it.
+// Tm = P R with R the pivot rows Z[k0 + t][:] (rows of length ldr).  The first
+// step reads them from the tiles and writes R (zero past m0 and past kb);
+// later steps find R written by the previous sweep.  A block takes 16
+// columns; thread (g, c) forms rows 4g..4g+3 of P R for column c.
 template <class T>
 __global__ void __launch_bounds__(256) k_panel(const T* __restrict__ tiles, int nt, int64_t m0, int64_t ldr, int k0,
                                                int kb, const T* __restrict__ P, T* __restrict__ R,
-                                               T* __restrict__ Tm) {
+                                               T* __restrict__ Tm, int from_tiles) {
   __shared__ T sP[NB][NB + 1];
   for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) sP[q / NB][q % NB] = P[q];
   __syncthreads();
@@ -163,16 +164,20 @@ __global__ void __launch_bounds__(256) k_panel(const T* __restrict__ tiles, int 
   const int64_t c = (int64_t)blockIdx.x * 16 + (threadIdx.x & 15);
   if (c >= ldr) return;
   T col[NB];
+  if (from_tiles) {
 #pragma unroll
-  for (int t = 0; t < NB; ++t) col[t] = (t < kb && c < m0) ? zat(tiles, nt, k0 + t, c) : (T)0;
+    for (int t = 0; t < NB; ++t) col[t] = (t < kb && c < m0) ? zat(tiles, nt, k0 + t, c) : (T)0;
+  } else {
+#pragma unroll
+    for (int t = 0; t < NB; ++t) col[t] = R[(int64_t)t * ldr + c];
+  }
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int t = 4 * g + u;
     T acc = 0;
 #pragma unroll
     for (int v = 0; v < NB; ++v) acc += sP[t][v] * col[v];
-    // all NB rows: rows past kb (the last, partial pivot block) are zero
-    R[(int64_t)t * ldr + c] = (t < kb && c < m0) ? zat(tiles, nt, k0 + t, c) : (T)0;
+    if (from_tiles) R[(int64_t)t * ldr + c] = (t < kb && c < m0) ? zat(tiles, nt, k0 + t, c) : (T)0;
     Tm[(int64_t)t * ldr + c] = acc;
   }
 }
@@ -226,13 +231,16 @@ __device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
 //   a == kp:           Tm[:, b]                          (P Z_Kb)
 //   b == kp:           Tm[:, a]^T                        (Z_aK P, by symmetry)
 // The upper-right sub-tile of a diagonal storage tile also writes its
-// transpose into the lower-left one.  Block 0 updates the next pivot block
+// transpose into the lower-left one.  The sub-tiles of row kp + 1 (and, as
+// transposes, of column kp + 1) also write their new values into Rn, the
+// pivot rows of the next step.  Block 0 updates the next pivot block
 // (kp + 1, kp + 1) and then inverts it into Pn: the next step needs no
 // separate pivot kernel, and its work hides behind the other blocks.
 template <class T>
 __global__ void __launch_bounds__(256) k_sweep(T* __restrict__ tiles, int nt, int n64, int64_t m0, int64_t ldr,
                                                int k0, const T* __restrict__ P, const T* __restrict__ R,
-                                               const T* __restrict__ Tm, T* __restrict__ Pn, int* flags) {
+                                               const T* __restrict__ Tm, T* __restrict__ Pn, T* __restrict__ Rn,
+                                               int* flags) {
   extern __shared__ __align__(16) char sm_sweep[];  // R and Tm slices, NB x NB each
   T (*sR)[NB] = reinterpret_cast<T (*)[NB]>(sm_sweep);
   T (*sT)[NB] = reinterpret_cast<T (*)[NB]>(sm_sweep + sizeof(T) * NB * NB);
@@ -307,6 +315,16 @@ __global__ void __launch_bounds__(256) k_sweep(T* __restrict__ tiles, int nt, in
       st4(zl + (4 * tx + v) * CT + 4 * ty, col);
     }
   }
+  if (has_next && a == kp + 1) {  // pivot rows of the next step, row by row
+#pragma unroll
+    for (int u = 0; u < 4; ++u) st4(Rn + (int64_t)(4 * ty + u) * ldr + j0 + 4 * tx, d[u]);
+  } else if (has_next && b == kp + 1) {  // ... and from the column above them, transposed
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const T col[4] = {d[0][v], d[1][v], d[2][v], d[3][v]};
+      st4(Rn + (int64_t)(4 * tx + v) * ldr + i0 + 4 * ty, col);
+    }
+  }
   if (has_next && blockIdx.x == 0) {  // the next pivot block, already updated: invert it
     __shared__ T rowp[2][NB], colp[2][NB];
     const int kbn = (int)((m0 - k0 - NB) < NB ? (m0 - k0 - NB) : NB);
@@ -342,9 +360,9 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
   pc->ctiles_n = nt;
   T *P = nullptr, *R = nullptr, *Tm = nullptr;
   SPNET_TRY(tmp.get(&P, 2 * NB * NB));
-  SPNET_TRY(tmp.get(&R, NB * ldr));
+  SPNET_TRY(tmp.get(&R, 2 * NB * ldr));  // pivot rows of this step and of the next
   SPNET_TRY(tmp.get(&Tm, NB * ldr));
-  SPNET_CUDA_TRY(cudaMemsetAsync(R, 0, sizeof(T) * NB * ldr, s));
+  SPNET_CUDA_TRY(cudaMemsetAsync(R, 0, sizeof(T) * 2 * NB * ldr, s));
   SPNET_CUDA_TRY(cudaMemsetAsync(Tm, 0, sizeof(T) * NB * ldr, s));
   note_launch();
   k_tiles_from_A0<T><<<(unsigned)nti, 256, 0, s>>>(A0, m0, nt, tiles);
@@ -367,11 +385,13 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
     const int kb = (int)((m0 - k0) < NB ? (m0 - k0) : NB);
     T* Pc = P + (step & 1) * NB * NB;
     T* Pn = P + ((step + 1) & 1) * NB * NB;
+    T* Rc = R + (step & 1) * NB * ldr;
+    T* Rn = R + ((step + 1) & 1) * NB * ldr;
     note_launch();
-    k_panel<T><<<(unsigned)(ldr / 16), 256, 0, s>>>(tiles, nt, m0, ldr, k0, kb, Pc, R, Tm);
+    k_panel<T><<<(unsigned)(ldr / 16), 256, 0, s>>>(tiles, nt, m0, ldr, k0, kb, Pc, Rc, Tm, step == 0 ? 1 : 0);
     note_launch();
     ProfScope ps(KID_SWEEP, s);
-    k_sweep<T><<<subtiles, 256, sweep_smem, s>>>(tiles, nt, n64, m0, ldr, k0, Pc, R, Tm, Pn, pc->op->dflags);
+    k_sweep<T><<<subtiles, 256, sweep_smem, s>>>(tiles, nt, n64, m0, ldr, k0, Pc, Rc, Tm, Pn, Rn, pc->op->dflags);
   }
   note_launch();
   k_negate<T><<<4 * num_sms(), 256, 0, s>>>(tiles, nti * CT * CT);

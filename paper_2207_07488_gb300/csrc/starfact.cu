@@ -311,35 +311,72 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
       W.colstart[npos] = ncol;
       __syncwarp();
       compact_all(W, n, lane);
-      // fill among the neighbours of each eliminated node (serial, lane-parallel lookups)
+      // fill among the neighbours of each eliminated node: every pair (a, b) of
+      // a column of this round, 32 pairs at a time.  Lanes test adjacency in
+      // parallel; pairs repeated inside a batch are merged; new list slots go
+      // by rank among the lanes that extend the same list (deterministic).  A
+      // list that would pass CAP entries switches the rest to the dense core.
       bool full = false;
-      for (int pos = lev_start; pos < npos; ++pos) {
-        const int cs = W.colstart[pos], ce = W.colstart[pos + 1];
-        for (int ai = cs; ai < ce; ++ai) {
-          for (int bi = ai + 1; bi < ce; ++bi) {
-            const int a = W.colent[ai], b = W.colent[bi];
+      {
+        int total = 0;  // pairs of the round; prefix per position in W.rstart
+        for (int base = lev_start; base < npos; base += 32) {
+          const int pos = base + lane;
+          int c = 0;
+          if (pos < npos) {
+            const int d = W.colstart[pos + 1] - W.colstart[pos];
+            c = d * (d - 1) / 2;
+          }
+          const int incl = warp_incl_scan(c, lane);
+          if (pos < npos) W.rstart[pos - lev_start] = total + incl - c;
+          total += __shfl_sync(FULL, incl, 31);
+        }
+        __syncwarp();
+        const int nl = npos - lev_start;
+        for (int p0 = 0; p0 < total; p0 += 32) {
+          const int p = p0 + lane;
+          int a = -1, b = -1;
+          if (p < total) {
+            int lo = 0, hi = nl - 1;  // position of pair p: last prefix <= p
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (W.rstart[mid] <= p) lo = mid;
+              else hi = mid - 1;
+            }
+            const int pos = lev_start + lo;
+            int l = p - W.rstart[lo];
+            const int cs = W.colstart[pos], d = W.colstart[pos + 1] - cs;
+            int ai = 0;
+            while (l >= d - 1 - ai) {
+              l -= d - 1 - ai;
+              ++ai;
+            }
+            a = W.colent[cs + ai];
+            b = W.colent[cs + ai + 1 + l];
             const int da = W.deg[a];
             bool found = false;
-            for (int q = lane; q < da; q += 32) found |= (W.nbr[(int64_t)a * CAP + q] == b);
-            found = __any_sync(FULL, found);
-            if (!found) {
-              if (lane == 0) {
-                int db = W.deg[b];
-                if (da < CAP && db < CAP) {
-                  W.nbr[(int64_t)a * CAP + da] = (uint16_t)b;
-                  W.deg[a] = da + 1;
-                  W.nbr[(int64_t)b * CAP + db] = (uint16_t)a;
-                  W.deg[b] = db + 1;
-                } else {
-                  full = true;
-                }
-              }
-              __syncwarp();
+            for (int q = 0; q < da; ++q) found |= W.nbr[(int64_t)a * CAP + q] == b;
+            if (found) a = b = -1;
+          }
+          const unsigned key = a < 0 ? 0xffffffffu : ((unsigned)min(a, b) << 16) | (unsigned)max(a, b);
+          const unsigned same = __match_any_sync(FULL, key);
+          const bool ins = a >= 0 && __ffs(same) - 1 == lane;
+#pragma unroll
+          for (int side = 0; side < 2; ++side) {  // b into the list of a, then a into the list of b
+            const int x = side == 0 ? a : b, y = side == 0 ? b : a;
+            const unsigned grp = __match_any_sync(FULL, ins ? (unsigned)x : 0xffffffffu);
+            const int rank = __popc(grp & ((1u << lane) - 1u));
+            const int dx = ins ? W.deg[x] : 0;
+            __syncwarp();
+            if (ins) {
+              if (dx + rank < CAP) W.nbr[(int64_t)x * CAP + dx + rank] = (uint16_t)y;
+              else full = true;
+              if (rank == 0) W.deg[x] = min(dx + __popc(grp), CAP);
             }
+            __syncwarp();
           }
         }
+        full = __any_sync(FULL, full);
       }
-      full = __shfl_sync(FULL, (int)full, 0) != 0;
       nlev++;
       if (full) dense = true;
     }
