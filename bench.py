@@ -1,19 +1,27 @@
-"""Throughput of full network solves on GB300 (one JSON line on stdout).
+"""Served throughput and latency of full network solves on GB300 (one JSON line).
 
-A step is one pass of the whole path over one synthetic network already in
-device memory: assembly of K from the edge list, the free-dof operator, the
-preconditioner set-up (host elements and Q1 values, coarse dofs, Galerkin
-matrix and its inverse, star orderings and factors) and PCG to a relative
-residual of 1e-8.  The workload is the 3D scalar diffusion network: 40000
-fibers of length 0.1 in the unit cube, contacts below 0.004, u = 0 at x < 0.01
-and u = 1 at x > 0.99, mesh width H = 1/16, stars at interior mesh nodes.
+A request is one whole solve of a synthetic network given in host memory: the
+copy of the edge list, coordinates, Dirichlet data and right-hand side to the
+device, the assembly of K, the free-dof operator, the preconditioner set-up
+(host elements and Q1 values, coarse dofs, Galerkin matrix and its inverse,
+star orderings and factors) and PCG to a relative residual of 1e-8, then the
+copy of the solution back.  The workload is the 3D scalar diffusion network:
+40000 fibers of length 0.1 in the unit cube, contacts below 0.004, u = 0 at
+x < 0.01 and u = 1 at x > 0.99, mesh width H = 1/16, stars at interior mesh
+nodes (two seeded replicates, alternating).
 
-Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
-on the library's stream; between steps (outside the events) a 512 MiB buffer
-is written to flush the L2.  `value` = K / (sum of step times).  `e2e` repeats
-the same steps through the C ABI with host buffers (pinned), the host/device
-copies inside the timed region.  Under torchrun every rank solves its own
-networks (replicas, no collective) and rank 0 reports the aggregate.
+Requests are served by the library's server (spnet_server_*): up to
+--inflight requests run at once, each on its own stream, their work
+overlapping on the GPU.  W warm-up requests, then K timed requests submitted
+at once: `value` = K / (device span from the first request's start to the
+last one's end, CUDA events).  The latency percentiles come from a second run
+of K requests arriving as a Poisson process at 0.9 of that throughput
+(arrival -> solution in host memory).  `fp64_plain` is plain FP64 PCG, one
+request at a time, on the same path; `single_stream` is the mixed path one
+request at a time with device-resident inputs (CUDA events around each
+request, L2 flushed between requests).  `e2e` is the served run timed on the
+host clock, copies included.  Under torchrun every rank serves its own
+requests (replicas, no collective) and rank 0 reports the aggregate.
 
 --impl reference times the CPU FP64 oracle on the same workload (the reference
 implementation of this build; see the design notes).
@@ -50,8 +58,9 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--inflight", type=int, default=4)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -240,19 +249,50 @@ def run_gb300(args, rank, world, local):
             op.close()
         return times, last
 
-    # warm-up, then the timed device-resident steps (CUDA graphs, no instrumentation)
-    timed(0, args.warmup)
+    def serve(n, inflight, precision, rate=None):
+        """n requests through a server; all at once, or Poisson arrivals at `rate` per second."""
+        sv = spnet.Server(max_inflight=inflight)
+        rng = np.random.default_rng(1234)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n)) if rate else np.zeros(n)
+        t0 = time.perf_counter()
+        tickets = []
+        for k in range(n):
+            while rate and time.perf_counter() - t0 < arrivals[k]:
+                time.sleep(5e-5)
+            tickets.append(sv.submit(probs[k % len(probs)], precision=precision, rtol=1e-8))
+        out = [sv.wait(t) for t in tickets]
+        t1 = time.perf_counter()
+        sv.close()
+        for _, res in out:
+            if res["status"] != 0 or res["relres"] > 1e-8:
+                raise RuntimeError(f"request failed: {res}")
+        span_ms = max(r["device_end_ms"] for _, r in out) - min(r["device_start_ms"] for _, r in out)
+        lat = np.array([r["latency_ms"] for _, r in out])
+        return dict(n=n, span_ms=span_ms, wall_s=t1 - t0, lat=lat,
+                    iters=max(r["iterations"] for _, r in out), relres=max(r["relres"] for _, r in out))
+
+    # warm-up (served and single-stream), then the timed served requests
+    serve(args.warmup, args.inflight, prec)
+    timed(0, 1)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     l0 = spnet.launch_count()
-    t_wall0 = time.perf_counter()
-    times, last = timed(args.steps, 0)
-    t_wall = time.perf_counter() - t_wall0
+    sat = serve(args.steps, args.inflight, prec)
     l1 = spnet.launch_count()
     clk = clocks.stop()
+    torch.cuda.synchronize()
+    # latency at 0.9 of the saturated throughput (Poisson arrivals)
+    rate = 0.9 * sat["n"] / (sat["span_ms"] / 1e3)
+    pois = serve(args.steps, args.inflight, prec, rate=rate)
+    # plain FP64 PCG, one request at a time, on the same path
+    n_fp = max(2, min(4, args.steps))
+    serve(1, 1, spnet.PREC_FP64)
+    fp = serve(n_fp, 1, spnet.PREC_FP64)
+    # the mixed path one request at a time, device-resident inputs, L2 flushed between requests
+    times, last = timed(min(args.steps, 5), 0)
     torch.cuda.synchronize()
     # a profiled pass over the same steps: every kernel launch timed with CUDA
     # events on its own stream (eager launches, so that each kernel has its events)
@@ -262,36 +302,16 @@ def run_gb300(args, rank, world, local):
     spnet.profile_enable(False)
     prof = spnet.profile_read()
     torch.cuda.synchronize()
-    # e2e: host buffers (pinned), copies inside the timed region
+    # e2e: the served run on the host clock (host arrays in and out, copies included)
     e2e = None
     if not args.no_e2e:
-        host = []
-        for p in probs:
-            net = p.net
-            cap = p.ndof * p.ndof * (net.n_nodes + 2 * net.n_edges)
-
-            def pinned(a, dt):
-                t = torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()
-                return t.numpy()
-
-            host.append(dict(
-                edges=pinned(net.edges, np.int64), coef=pinned(net.cond, np.float64),
-                coords=pinned(net.coords, np.float64), dd=pinned(p.dirichlet_dofs, np.int64),
-                f=pinned(p.f, np.float64), g=pinned(p.dirichlet_vals, np.float64),
-                rp=pinned(np.zeros(net.n_nodes * p.ndof + 1), np.int64),
-                col=pinned(np.zeros(cap), np.int32), val=pinned(np.zeros(cap), np.float64)))
-        ht, hlast = timed(args.steps, 1, host)
         p = probs[0]
-        oi = hlast[0]
         h2d = (p.net.n_edges * 24 + p.net.n_nodes * p.net.dim * 8
                + p.dirichlet_dofs.size * 8 + p.n_dof * 8 + p.dirichlet_vals.size * 8)
-        # the assembled CSR goes down to the host and back up to the operator
-        nnz_k = (p.net.n_nodes + 2 * p.net.n_edges) * p.ndof ** 2
-        csr = (p.n_dof + 1) * 8 + nnz_k * 12
-        e2e = {"value": len(ht) / (sum(ht) / 1e3), "unit": "solves/s",
-               "h2d_bytes_per_step": int(h2d + csr), "d2h_bytes_per_step": int(csr + p.n_dof * 8)}
-    return dict(times=times, last=last, prof=prof, launches=l1 - l0, clocks=clk, e2e=e2e,
-                desc=desc, t_wall=t_wall, prof_steps=len(ptimes), prof_ms=sum(ptimes))
+        e2e = {"value": sat["n"] / sat["wall_s"], "unit": "solves/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(p.n_dof * 8)}
+    return dict(sat=sat, pois=pois, fp=fp, times=times, last=last, prof=prof, launches=l1 - l0,
+                clocks=clk, e2e=e2e, desc=desc, prof_steps=len(ptimes), prof_ms=sum(ptimes))
 
 
 def cpu_oracle_sample(problem, iters_full, sample_iters=3):
@@ -331,12 +351,13 @@ def main():
         iters = REF_ITERS.get(args.workload)
         times, desc_s = [], ""
         for k in range(args.warmup + args.steps):
-            t, desc_s = cpu_oracle_sample(prob, iters)
+            t, desc_s = cpu_oracle_sample(prob, iters, sample_iters=2)
             if k >= args.warmup:
                 times.append(t)
         v = len(times) / sum(times)
         line = {
-            "impl": "reference", "metric": "solves/s at rel-res 1e-8", "value": v, "unit": "solves/s",
+            "impl": "reference", "metric": "solves/s at rel-res 1e-8 (served; p50/p99 latency)", "value": v,
+            "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -348,15 +369,16 @@ def main():
         print(json.dumps(line))
         return
     r = run_gb300(args, rank, world, local)
-    times = r["times"]
-    tot = sum(times) / 1e3
+    sat, pois, fp = r["sat"], r["pois"], r["fp"]
+    tot = sat["span_ms"] / 1e3
     if world > 1:
         import torch
         import torch.distributed as dist
         t = torch.tensor([tot], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot = float(t.item())
-    value = world * len(times) / tot
+    value = world * sat["n"] / tot
+    times = r["times"]
     oi, pi, st, kb = r["last"]
     prof = r["prof"]
     # dominant iteration kernel by device time inside the timed region
@@ -382,18 +404,34 @@ def main():
     share = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0] > 0}
     share["profiled_pass"] = {"steps": r["prof_steps"], "ms": round(r["prof_ms"], 3),
                               "note": "eager launches, each timed with CUDA events"}
+    lat = pois["lat"]
     line = {
-        "metric": "solves/s at rel-res 1e-8", "value": value, "unit": "solves/s", "n_gpus": world,
-        "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "metric": "solves/s at rel-res 1e-8 (served; p50/p99 latency)", "value": value, "unit": "solves/s",
+        "n_gpus": world, "steps": sat["n"], "warmup": args.warmup, "ms_per_step": 1e3 * tot / sat["n"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": r["desc"], "precision": args.precision, "n_free": int(oi.n_free),
+        "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                       "p99": round(float(np.percentile(lat, 99)), 3),
+                       "arrivals": f"Poisson at {0.9 * sat['n'] / (sat['span_ms'] / 1e3):.1f}/s "
+                                   f"(0.9 of the served throughput), {pois['n']} requests, "
+                                   "arrival -> solution in host memory",
+                       "solves_per_s": round(pois["n"] / pois["wall_s"], 3)},
+        "fp64_plain": {"value": round(fp["n"] / (fp["span_ms"] / 1e3), 4), "unit": "solves/s",
+                       "ms_per_solve": round(fp["span_ms"] / fp["n"], 3), "requests": fp["n"],
+                       "iterations": int(fp["iters"]), "relres": fp["relres"],
+                       "note": "FP64 factors, coarse inverse and local solves; one request at a time"},
+        "single_stream": {"value": round(len(times) / (sum(times) / 1e3), 3), "unit": "solves/s",
+                          "ms_per_solve": round(sum(times) / len(times), 3),
+                          "note": "mixed, one request at a time, inputs on the device, L2 flushed between"},
+        "config": {"workload": r["desc"], "precision": args.precision, "inflight": args.inflight,
+                   "n_free": int(oi.n_free),
                    "nnz": int(oi.nnz_ff), "m0": int(pi.m0), "stars": int(pi.n_stars),
                    "sum_star": int(pi.sum_star), "factor_nnz": int(pi.factor_nnz),
                    "max_star": int(pi.max_star), "total_levels": int(pi.total_levels),
                    "max_levels": int(pi.max_levels), "setup_ms_last": round(pi.setup_ms, 3),
-                   "iterations": int(st.iterations), "relres": st.relres,
-                   "l2": "512 MiB buffer written between steps (outside the timed events)",
+                   "iterations": int(sat["iters"]), "relres": sat["relres"],
+                   "l2": "inputs larger than L2: each request holds several hundred MB on the device",
+                   "timing": "device span of the served requests (CUDA events), all submitted at once",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"], "kernels": share,

@@ -179,6 +179,66 @@ int pcg_solve(spnet_op_t op, spnet_pc_t pc, int nrhs, const double* f, const dou
 int spnet_op_destroy(spnet_op_t op);
 int spnet_pc_destroy(spnet_pc_t pc);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of solve requests.
+ *
+ * The paper solves one network at a time; this is the service around the
+ * same solver (assembly, build_network_operator, setup_preconditioner,
+ * pcg_solve per request).  A server runs up to max_inflight requests at once,
+ * each on its own CUDA stream and host thread; requests wait in submission
+ * order and are admitted when a slot is free and the device memory the
+ * request is estimated to need fits the budget (the free device memory at
+ * creation less reserve_bytes, less the estimates of the running requests).
+ * The admitted requests' work overlaps on the GPU.  Every kernel reduces in a
+ * fixed order, so a request's result does not depend on what else runs.
+ * ------------------------------------------------------------------------- */
+typedef struct spnet_server_s* spnet_server_t;
+
+typedef struct {
+  int model;                     /* SPNET_MODEL_SCALAR or SPNET_MODEL_TRUSS3 */
+  int dim;                       /* 2 or 3 */
+  int64_t n_nodes, n_edges;
+  const int64_t* edges;          /* [2*n_edges] node ids (i, j) */
+  const double* coef;            /* [n_edges] edge coefficients (as spnet_assemble) */
+  const double* dirs;            /* [3*n_edges] unit edge directions (TRUSS3), else NULL */
+  const double* coords;          /* [n_nodes*dim] */
+  double domain_hi[3];           /* Omega = [0, domain_hi[0]] x ... */
+  int64_t n_dirichlet;
+  const int64_t* dirichlet_dofs; /* [n_dirichlet] strictly ascending */
+  int nrhs;                      /* right-hand sides of this request, >= 1 */
+  const double* f;               /* [nrhs*n_dof] */
+  const double* g;               /* [nrhs*n_dirichlet] Dirichlet values */
+  double* x;                     /* [nrhs*n_dof] out: u_hat = u + g on all dofs */
+  double H;                      /* coarse mesh width (as setup_preconditioner) */
+  int gamma_faces[3];            /* per component (first ndof used), as setup_preconditioner */
+  spnet_options opts;            /* as setup_preconditioner */
+  double rtol;                   /* relative residual target */
+  int maxit;
+  int reserved[7];
+} spnet_request;
+
+typedef struct {
+  int status;               /* SPNET_OK, or the error code of the failed step */
+  int iterations;           /* largest CG step count over the request's right-hand sides */
+  double relres;            /* largest recomputed relative residual */
+  double queue_ms;          /* submission -> admission (host clock) */
+  double latency_ms;        /* submission -> solutions in host memory (host clock) */
+  double device_start_ms;   /* device time of the request's first and last work, from */
+  double device_end_ms;     /*   an origin fixed when the server was created (CUDA events) */
+  char message[256];        /* the error message when status != SPNET_OK */
+} spnet_result;
+
+/* spnet_server_create -- start max_inflight (1..64) workers on the current device. */
+int spnet_server_create(int max_inflight, int64_t reserve_bytes, spnet_server_t* out);
+/* spnet_server_submit -- queue a request (host arrays, borrowed until spnet_server_wait
+ * returns for it); *ticket identifies it.  Errors: BAD_INPUT (malformed request). */
+int spnet_server_submit(spnet_server_t server, const spnet_request* request, int64_t* ticket);
+/* spnet_server_wait -- block until the request is done; its result (the solutions are in
+ * request->x).  A request that failed reports its error in result->status/message. */
+int spnet_server_wait(spnet_server_t server, int64_t ticket, spnet_result* result);
+/* spnet_server_destroy -- finish every queued request, stop the workers, free the server. */
+int spnet_server_destroy(spnet_server_t server);
+
 /* spnet_last_error -- copy the calling thread's last error message (NUL-terminated). */
 int spnet_last_error(char* buf, size_t len);
 

@@ -11,6 +11,7 @@
 // The sweeps and the product run in FP64 or, for the mixed-precision
 // preconditioner, in FP32.
 #include <climits>
+#include <atomic>
 #include <cmath>
 
 #include "spnet_internal.cuh"
@@ -372,7 +373,7 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
   const unsigned subtiles = (unsigned)n_upper_tiles(n64);
   const size_t sweep_smem = 2 * sizeof(T) * NB * NB;
   if (sweep_smem > 48 * 1024) {
-    static bool attr_set[64] = {};  // per device; the size depends only on T
+    static std::atomic<bool> attr_set[64];  // per device; the size depends only on T
     int dev = 0;
     SPNET_CUDA_TRY(cudaGetDevice(&dev));
     dev &= 63;
@@ -412,9 +413,8 @@ int pc_coarse_invert(spnet_pc_s* pc, double* A0) {
 // stored tile reads it once and uses it twice:
 //   row sums     Z_IJ r_J   -> part[I][J]   (the contribution of column block J to z_I)
 //   column sums  Z_IJ^T r_I -> part[J][I]   (I < J: the contribution of row block I to z_J)
-// Every part[R][K] has one writer.  A counter per row block R counts the parts
-// written; the block that writes the last one sums part[R][0..nt-1] in K order
-// (deterministic) into z_c and resets the counter for the next application.
+// Every part[R][K] has one writer; a second kernel sums part[R][0..nt-1] in K
+// order into z_c (deterministic).
 // ---------------------------------------------------------------------------
 template <class T>
 struct Vec4 {
@@ -459,14 +459,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_coarse_symv(con
                                                      const double* __restrict__ rc,
                                                      const double* __restrict__ epart,
                                                      const int32_t* __restrict__ rtab,
-                                                     T* __restrict__ part,
-                                                     unsigned* __restrict__ cnt, double* __restrict__ zc,
-                                                     const int* done) {
+                                                     T* __restrict__ part, const int* done) {
   constexpr int RW = CT / 8;                  // rows per warp
   constexpr int RB = 8;                       // rows loaded per batch
   __shared__ T sI[CT], sJ[CT];
   __shared__ T scol[8][CT];
-  __shared__ int red[2];
   pdl_wait();
   pdl_trigger();
   if (done && *done) return;
@@ -521,51 +518,51 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_coarse_symv(con
       part[((int64_t)J * nt + I) * CT + threadIdx.x] = sum;
     }
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    red[0] = atomicAdd(&cnt[I], 1u) == (unsigned)(nt - 1) ? 1 : 0;
-    red[1] = (I != J && atomicAdd(&cnt[J], 1u) == (unsigned)(nt - 1)) ? 1 : 0;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    if (!red[side]) continue;  // uniform over the block
-    __threadfence();
-    const int R = side == 0 ? I : J;
-    if (threadIdx.x < CT) {
-      const int64_t i = (int64_t)R * CT + threadIdx.x;
-      const T* pr = part + (int64_t)R * nt * CT + threadIdx.x;
-      double sum = 0.0;
-      // eight independent loads in flight, summed in K order
-      for (int K0 = 0; K0 < nt; K0 += 8) {
-        T v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = K0 + u < nt ? __ldcg(pr + (int64_t)(K0 + u) * CT) : T(0);
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (K0 + u < nt) sum += (double)v[u];
-      }
-      if (i < m0) zc[i] = sum;
-    }
-    if (threadIdx.x == 0) cnt[R] = 0u;
-  }
 }
 
-// z_c = A_0^{-1} r_c; with rc == null, r_c = R_0 r is formed from the element
-// corner sums of the last update (restriction fused into the product)
+// z_c[i] = sum over K of part[R][K][i - 128 R] in K order, R = i / 128
+// (one thread per coarse dof; eight loads in flight)
+template <class T>
+__global__ void __launch_bounds__(256) k_coarse_reduce(int nt, int64_t m0, const T* __restrict__ part,
+                                                       double* __restrict__ zc, const int* done) {
+  pdl_wait();
+  pdl_trigger();
+  if (done && *done) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m0) return;
+  const int64_t R = i / CT;
+  const T* pr = part + R * nt * CT + (i - R * CT);
+  double sum = 0.0;
+  for (int K0 = 0; K0 < nt; K0 += 8) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = K0 + u < nt ? pr[(int64_t)(K0 + u) * CT] : T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (K0 + u < nt) sum += (double)v[u];
+  }
+  zc[i] = sum;
+}
+
 void launch_coarse_apply(spnet_pc_s* pc, const double* rc, double* zc, const int* done,
                          cudaStream_t s) {
   if (pc->m0 == 0) return;
   const unsigned tiles = (unsigned)n_upper_tiles(pc->ctiles_n);
   note_launch();
+  note_launch();  // the product and its row reduction
   ProfScope ps(KID_COARSE, s);
-  if (pc->precision == SPNET_PREC_FP64)
+  const unsigned rblocks = (unsigned)((pc->m0 + 255) / 256);
+  if (pc->precision == SPNET_PREC_FP64) {
     launch_pdl(k_coarse_symv<double>, tiles, 256, 0, s, (const double*)pc->ctiles, pc->ctiles_n, (int64_t)pc->m0,
-               rc, (const double*)pc->epart, (const int32_t*)pc->rtab, (double*)pc->cpart, pc->ccnt, zc, done);
-  else
+               rc, (const double*)pc->epart, (const int32_t*)pc->rtab, (double*)pc->cpart, done);
+    launch_pdl(k_coarse_reduce<double>, rblocks, 256, 0, s, pc->ctiles_n, (int64_t)pc->m0,
+               (const double*)pc->cpart, zc, done);
+  } else {
     launch_pdl(k_coarse_symv<float>, tiles, 256, 0, s, (const float*)pc->ctiles, pc->ctiles_n, (int64_t)pc->m0,
-               rc, (const double*)pc->epart, (const int32_t*)pc->rtab, (float*)pc->cpart, pc->ccnt, zc, done);
+               rc, (const double*)pc->epart, (const int32_t*)pc->rtab, (float*)pc->cpart, done);
+    launch_pdl(k_coarse_reduce<float>, rblocks, 256, 0, s, pc->ctiles_n, (int64_t)pc->m0, (const float*)pc->cpart,
+               zc, done);
+  }
 }
 
 // rtab[ci][cp]: offset of the corner sum of the element at position cp around
@@ -596,8 +593,6 @@ static int prepare_product(spnet_pc_s* pc) {
   const int nt = pc->ctiles_n;
   T* part = nullptr;
   SPNET_TRY(pc->mem.get(&part, (int64_t)nt * nt * CT));
-  SPNET_TRY(pc->mem.get(&pc->ccnt, nt));
-  SPNET_CUDA_TRY(cudaMemsetAsync(pc->ccnt, 0, sizeof(unsigned) * nt, s));
   const int64_t nmc = (int64_t)pc->n_mesh * pc->ndof;
   if ((int64_t)pc->n_elem * pc->nc * pc->ndof > INT32_MAX)
     return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: too many element corner sums for 32-bit offsets");

@@ -152,7 +152,7 @@ __global__ void k_residual(int64_t N, const double* b, const double* q, double* 
 }
 
 // ---------------------------------------------------------------------------
-// spmv_dir: p = z + beta p, q = A z + beta q, block partials of (p, q)
+// spmv_dir: p = z + beta p, q = A z + beta q, partials of (p, q); last block: alpha
 // ---------------------------------------------------------------------------
 template <int L>
 __global__ void __launch_bounds__(256) k_spmv_dir(int64_t n, const int64_t* __restrict__ ptr,
@@ -198,7 +198,15 @@ __global__ void __launch_bounds__(256) k_spmv_dir(int64_t n, const int64_t* __re
       dot = fma(pn, qn, dot);
     }
   }
-  block_partial(dot, partial, sh);  // summed by every block of the update (alpha)
+  block_partial(dot, partial, sh);
+  if (last_block(&sc->cnt[0])) {  // alpha = (r, z) / (p, q), for the update and the star solves
+    const double pq = block_sum(partial, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      sc->pq = pq;
+      sc->alpha = sc->rz / pq;
+      sc->cnt[0] = 0;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -214,15 +222,13 @@ __global__ void __launch_bounds__(256, ND == 1 ? 4 : 2) k_update(int n_elem, int
                                                 const double* __restrict__ r, double* __restrict__ rout,
                                                 const double* __restrict__ p,
                                                 const double* __restrict__ q, double* __restrict__ epart,
-                                                const double* __restrict__ ppq, int npq, double* partial,
-                                                Scal* sc, int mode) {
+                                                double* partial, Scal* sc, int mode) {
   constexpr int D = NC == 4 ? 2 : 3;
   __shared__ double sh[32];
   pdl_wait();
   pdl_trigger();
   if (mode == 0 && sc->done) return;
-  // alpha = (r, z) / (p, q): every block sums the SpMV's partials in the same order
-  const double alpha = mode == 0 ? sc->rz / block_sum(ppq, npq, sh) : 0.0;
+  const double alpha = mode == 0 ? sc->alpha : 0.0;
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -454,8 +460,7 @@ template <int NC, int ND, class CT>
 static void launch_update_t(spnet_pc_s* pc, const CT* xi, double* x, const double* r, double* rout,
                             const double* p, const double* q, Scal* sc, int mode, cudaStream_t s) {
   launch_pdl(k_update<NC, ND, CT>, elem_grid(pc, 8), 256, 0, s, pc->n_elem, pc->N, (const int32_t*)pc->elem_ptr,
-             (const int8_t*)pc->comp_of, xi, x, r, rout, p, q, pc->epart, (const double*)pc->pspmv,
-             pc->spmv_blocks, pc->partial + pc->PG, sc, mode);
+             (const int8_t*)pc->comp_of, xi, x, r, rout, p, q, pc->epart, pc->partial + pc->PG, sc, mode);
 }
 
 template <class CT>

@@ -132,7 +132,6 @@ struct spnet_pc_s {
   int32_t* cidx = nullptr;     // [n_mesh*ndof]
   void* ctiles = nullptr;      // A_0^{-1} (float or double by precision): its upper 128 x 128 tiles, packed
   void* cpart = nullptr;       // [nt*nt*CT] per row block and tile column: partial products
-  unsigned* ccnt = nullptr;    // [nt] parts written per row block (zero between applications)
   int ctiles_n = 0;            // nt: tiles per dimension
   int32_t* rtab = nullptr;     // [m0*8] offsets of the corner sums that make up each r_c entry
   double* A0 = nullptr;        // [m0*m0] copy of A_0 if m0 <= A0_KEEP

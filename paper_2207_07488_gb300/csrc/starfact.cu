@@ -19,6 +19,7 @@
 // kept in FP64 and rounded to FP32 for the mixed-precision solve.
 #include <algorithm>
 #include <climits>
+#include <atomic>
 #include <cmath>
 #include <queue>
 
@@ -752,44 +753,20 @@ __device__ __forceinline__ T scan_step(T v, int o, int dl) {
   return dl >= o ? v + t : v;
 }
 
-// block sum of n partials, fixed order, eight loads in flight (every thread gets it)
-__device__ double partial_sum(const double* part, int n) {
-  __shared__ double sh[32];
-  double s = 0.0;
-  for (int i0 = threadIdx.x; i0 < n; i0 += 8 * (int)blockDim.x) {
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = i0 + u * (int)blockDim.x;
-      v[u] = i < n ? __ldcg(part + i) : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) s += v[u];
-  }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-  __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-  __syncthreads();
-  return t;
-}
-
 // slot (block, warp) -> star: sorder[blockIdx.x * wpb + warp], -1 for an idle slot.
-// With q set (a PCG step) the right-hand side is the new residual r - alpha q,
-// alpha = rz / (p, q) from the SpMV's partials, formed exactly as the update
-// forms it; otherwise r itself.
+// With q set (a PCG step) the right-hand side is the new residual r - alpha q
+// (alpha from the SpMV), formed exactly as the update forms it; otherwise r.
 template <class T>
 __global__ void __launch_bounds__(256) k_star_stream(int wpb, int ymax, const int32_t* __restrict__ sorder,
                                                      const StarHdr* __restrict__ hdr, const char* __restrict__ recs,
                                                      const uint16_t* __restrict__ iperm, const double* __restrict__ r,
-                                                     const double* __restrict__ q, const double* __restrict__ ppq,
-                                                     int npq, const Scal* sc, T* __restrict__ w, const int* done) {
+                                                     const double* __restrict__ q, const Scal* sc,
+                                                     T* __restrict__ w, const int* done) {
   extern __shared__ int4 smem4[];
   pdl_wait();
   pdl_trigger();
   if (done && *done) return;
-  const double alpha = q ? sc->rz / partial_sum(ppq, npq) : 0.0;
+  const double alpha = q ? sc->alpha : 0.0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int s = sorder[blockIdx.x * wpb + wid];
   if (s < 0) return;  // no block-wide barrier follows
@@ -899,12 +876,12 @@ void launch_star_solve(spnet_pc_s* pc, const double* r, const double* q, const S
   const unsigned grid = (unsigned)pc->solve_blocks;
   if (pc->precision == SPNET_PREC_FP64)
     k_star_stream<double><<<grid, wpb * 32, pc->solve_smem, s>>>(
-        wpb, pc->max_star, pc->sorder, (const StarHdr*)pc->shdr, pc->srec, pc->iperm_star, r, q, pc->pspmv,
-        pc->spmv_blocks, sc, (double*)pc->w, done);
+        wpb, pc->max_star, pc->sorder, (const StarHdr*)pc->shdr, pc->srec, pc->iperm_star, r, q, sc,
+        (double*)pc->w, done);
   else
     k_star_stream<float><<<grid, wpb * 32, pc->solve_smem, s>>>(
-        wpb, pc->max_star, pc->sorder, (const StarHdr*)pc->shdr, pc->srec, pc->iperm_star, r, q, pc->pspmv,
-        pc->spmv_blocks, sc, (float*)pc->w, done);
+        wpb, pc->max_star, pc->sorder, (const StarHdr*)pc->shdr, pc->srec, pc->iperm_star, r, q, sc,
+        (float*)pc->w, done);
 }
 
 // headers, inverse permutations and entry streams of all stars
@@ -944,7 +921,7 @@ static int pack_streams(spnet_pc_s* pc, DevArena& tmp, const std::vector<int32_t
   int wpb = (int)(STREAM_SMEM / wb);
   wpb = wpb > 8 ? 8 : wpb;
   if (wpb < 1) return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: a star too large for the solve's shared memory");
-  static bool attr_set[64][2] = {};
+  static std::atomic<bool> attr_set[64][2];  // per device and precision (workers may race: setting twice is harmless)
   int dev = 0;
   SPNET_CUDA_TRY(cudaGetDevice(&dev));
   dev &= 63;
@@ -1039,7 +1016,7 @@ int pc_factor_stars(spnet_pc_s* pc) {
   if (warps > pc->S) warps = pc->S;
   warps = (warps + 3) / 4 * 4;
   if (hot_in_smem) {
-    static bool attr_set[64] = {};
+    static std::atomic<bool> attr_set[64];  // per device
     int dev = 0;
     SPNET_CUDA_TRY(cudaGetDevice(&dev));
     dev &= 63;

@@ -19,6 +19,8 @@ ERRORS = {
     -1: "BAD_INPUT", -2: "NOT_SPD", -3: "NO_MEMORY", -4: "NO_CONVERGENCE", -5: "TIMEOUT",
     -6: "CUDA", -7: "UNSUPPORTED", -8: "BAD_H",
 }
+ERR_BAD_INPUT, ERR_NOT_SPD, ERR_NO_MEMORY, ERR_NO_CONVERGENCE = -1, -2, -3, -4
+ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED, ERR_BAD_H = -5, -6, -7, -8
 MEM_HOST, MEM_DEVICE = 0, 1
 MODEL_SCALAR, MODEL_TRUSS3 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
@@ -32,6 +34,7 @@ EXPORTED = [
     "spnet_pc_get_info", "spnet_spmv", "spnet_pc_apply", "spnet_pc_restrict", "spnet_pc_coarse",
     "spnet_pc_prolong", "spnet_pc_stars", "spnet_pc_export", "spnet_launch_count",
     "spnet_profile_enable", "spnet_profile_read", "spnet_profile_reset", "spnet_pc_restrict_static",
+    "spnet_server_create", "spnet_server_submit", "spnet_server_wait", "spnet_server_destroy",
 ]
 KERNELS = ["spmv", "update", "restrict", "stars", "coarse", "combine", "direction",
            "star_symbolic", "star_numeric", "sweep", "galerkin"]
@@ -46,6 +49,21 @@ class SpnetError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("star_set", C.c_int), ("flexible", C.c_int),
                 ("max_restarts", C.c_int), ("reserved", C.c_int * 12)]
+
+
+class Request(C.Structure):
+    _fields_ = [("model", C.c_int), ("dim", C.c_int), ("n_nodes", C.c_int64), ("n_edges", C.c_int64),
+                ("edges", C.c_void_p), ("coef", C.c_void_p), ("dirs", C.c_void_p), ("coords", C.c_void_p),
+                ("domain_hi", C.c_double * 3), ("n_dirichlet", C.c_int64), ("dirichlet_dofs", C.c_void_p),
+                ("nrhs", C.c_int), ("f", C.c_void_p), ("g", C.c_void_p), ("x", C.c_void_p),
+                ("H", C.c_double), ("gamma_faces", C.c_int * 3), ("opts", Options), ("rtol", C.c_double),
+                ("maxit", C.c_int), ("reserved", C.c_int * 7)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("relres", C.c_double),
+                ("queue_ms", C.c_double), ("latency_ms", C.c_double), ("device_start_ms", C.c_double),
+                ("device_end_ms", C.c_double), ("message", C.c_char * 256)]
 
 
 class Stats(C.Structure):
@@ -394,3 +412,89 @@ def pcg_solve(op: Operator, pc: Preconditioner, f, g, x0=None, rtol=1e-8, maxit=
     if rc != OK and (rc != -4 or raise_on_noconv):
         _check(rc)
     return x, [stats[k] for k in range(nrhs)]
+
+
+class Server:
+    """spnet_server_*: continuous batching of solve requests (host arrays in, host solutions out).
+
+    submit() copies nothing: the arrays of a request are kept alive here until
+    wait() returns its solutions.
+    """
+
+    def __init__(self, max_inflight=4, reserve_bytes=2 << 30):
+        self._lib = load()
+        self.handle = C.c_void_p()
+        _check(self._lib.spnet_server_create(int(max_inflight), C.c_int64(int(reserve_bytes)),
+                                             C.byref(self.handle)))
+        self._live = {}
+
+    def submit(self, problem, f=None, g=None, precision=PREC_MIXED, rtol=1e-8, maxit=2000,
+               star_set=None, flexible=-1, max_restarts=2):
+        """Queue one request for `problem` (a networks.Problem); f: (n_dof,) or (nrhs, n_dof),
+        default problem.f; g likewise over the Dirichlet dofs, default problem.dirichlet_vals."""
+        net = problem.net
+        f = problem.f if f is None else f
+        f = np.ascontiguousarray(np.atleast_2d(np.asarray(f, np.float64)))
+        nrhs = f.shape[0]
+        g = problem.dirichlet_vals if g is None else g
+        g = np.ascontiguousarray(np.broadcast_to(np.atleast_2d(np.asarray(g, np.float64)),
+                                                 (nrhs, len(problem.dirichlet_dofs))))
+        x = np.zeros((nrhs, problem.n_dof), np.float64)
+        edges = np.ascontiguousarray(net.edges, np.int64)
+        scalar = problem.model == "scalar"
+        coef = np.ascontiguousarray(net.cond if scalar else net.stiff, np.float64)
+        dirs = None if scalar else np.ascontiguousarray(net.dirs, np.float64)
+        coords = np.ascontiguousarray(net.coords, np.float64)
+        dd = np.ascontiguousarray(problem.dirichlet_dofs, np.int64)
+        q = Request()
+        q.model = MODEL_SCALAR if scalar else MODEL_TRUSS3
+        q.dim = net.dim
+        q.n_nodes = net.n_nodes
+        q.n_edges = net.n_edges
+        q.edges = edges.ctypes.data
+        q.coef = coef.ctypes.data
+        q.dirs = dirs.ctypes.data if dirs is not None else None
+        q.coords = coords.ctypes.data
+        for a in range(3):
+            q.domain_hi[a] = float(net.domain[a]) if a < net.dim else 1.0
+        q.n_dirichlet = len(dd)
+        q.dirichlet_dofs = dd.ctypes.data if len(dd) else None
+        q.nrhs = nrhs
+        q.f = f.ctypes.data
+        q.g = g.ctypes.data if g.size else x.ctypes.data
+        q.x = x.ctypes.data
+        q.H = float(problem.H)
+        for a, v in enumerate((list(problem.gamma_faces) + [0, 0, 0])[:3]):
+            q.gamma_faces[a] = int(v)
+        q.opts.precision = precision
+        ss = problem.star_set if star_set is None else star_set
+        q.opts.star_set = ss if isinstance(ss, int) else (STARS_ALL if ss == "all" else STARS_INTERIOR)
+        q.opts.flexible = flexible
+        q.opts.max_restarts = max_restarts
+        q.rtol = float(rtol)
+        q.maxit = int(maxit)
+        ticket = C.c_int64(0)
+        _check(self._lib.spnet_server_submit(self.handle, C.byref(q), C.byref(ticket)))
+        self._live[ticket.value] = (q, edges, coef, dirs, coords, dd, f, g, x)
+        return ticket.value
+
+    def wait(self, ticket):
+        """Block until the request is done: (x of shape (nrhs, n_dof), result dict)."""
+        res = Result()
+        _check(self._lib.spnet_server_wait(self.handle, C.c_int64(ticket), C.byref(res)))
+        live = self._live.pop(ticket)
+        out = {k: getattr(res, k) for k in ("status", "iterations", "relres", "queue_ms", "latency_ms",
+                                              "device_start_ms", "device_end_ms")}
+        out["message"] = res.message.decode(errors="replace")
+        return live[-1], out
+
+    def close(self):
+        if self.handle:
+            self._lib.spnet_server_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
