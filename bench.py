@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--inflight", type=int, default=4)
+    ap.add_argument("--mode", default="served", choices=["served", "single"],
+                    help="single: only the one-request-at-a-time measurement (for profiling runs)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -271,6 +273,17 @@ def run_gb300(args, rank, world, local):
         return dict(n=n, span_ms=span_ms, wall_s=t1 - t0, lat=lat,
                     iters=max(r["iterations"] for _, r in out), relres=max(r["relres"] for _, r in out))
 
+    if args.mode == "single":  # one request at a time only (the command profiling runs use)
+        timed(0, args.warmup)
+        times, last = timed(args.steps, 0)
+        spnet.profile_reset()
+        spnet.profile_enable(True)
+        ptimes, _ = timed(min(args.steps, 2), 0)
+        spnet.profile_enable(False)
+        one = dict(n=len(times), span_ms=sum(times), wall_s=sum(times) / 1e3, lat=np.array(times),
+                   iters=int(last[2].iterations), relres=last[2].relres)
+        return dict(sat=one, pois=one, fp=one, times=times, last=last, prof=spnet.profile_read(), launches=0,
+                    clocks=None, e2e=None, desc=desc, prof_steps=len(ptimes), prof_ms=sum(ptimes))
     # warm-up (served and single-stream), then the timed served requests
     serve(args.warmup, args.inflight, prec)
     timed(0, 1)
