@@ -71,7 +71,13 @@ typedef struct {
   int flexible;      /* 1: Polak-Ribiere beta (r, z - z_old)/(r_old, z_old); 0: textbook
                         beta; -1: flexible iff precision is MIXED (default -1) */
   int max_restarts;  /* restarts from the recomputed residual (default 2) */
-  int reserved[12];
+  int batch_rhs;     /* right-hand sides pcg_solve steps together: 0 or 1 one at a time
+                        (default); 2..32 blocks of up to that many (fewer where the largest
+                        star's solve vector for that many does not fit a block's shared
+                        memory), each right-hand side with its own scalars and stop test;
+                        the matrix, the star factors and the coarse tiles are read once
+                        per block */
+  int reserved[11];
 } spnet_options;
 
 typedef struct {
@@ -263,6 +269,17 @@ int spnet_pc_restrict(spnet_pc_t pc, const double* r, double* rc, int mem);
 int spnet_pc_coarse(spnet_pc_t pc, const double* rc, double* zc, int mem);
 int spnet_pc_prolong(spnet_pc_t pc, const double* zc, double* z, int mem);
 int spnet_pc_stars(spnet_pc_t pc, const double* r, double* z, int mem);
+
+/* spnet_pc_apply_batch -- z_j = B r_j for k right-hand sides at once (1 <= k <= 32),
+ * the form of spnet_pc_apply that pcg_solve uses when it steps right-hand sides
+ * together (Sections 4.1-4.2 applied to each r_j on its own).  r, z [k*n_free]:
+ * one right-hand side after another, each in free order; host or device memory
+ * by mem.  which: 0 the whole of B; 1 the coarse term R_0^T A_0^{-1} R_0 r only;
+ * 2 the star term sum_j E_j A_j^{-1} E_j^T r only.  Errors: BAD_INPUT (null
+ * pointer, k, which or mem out of range), UNSUPPORTED (the largest star's solve
+ * vector for k right-hand sides exceeds a block's shared memory), CUDA.
+ */
+int spnet_pc_apply_batch(spnet_pc_t pc, int k, const double* r, double* z, int which, int mem);
 
 /* spnet_pc_export -- copy set-up data to host memory (for inspection).
  * what: SPNET_EXPORT_ELEMENTS   int32 [n_free]     linear host element of each free dof

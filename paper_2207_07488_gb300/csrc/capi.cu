@@ -30,6 +30,8 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
     return fail(SPNET_ERR_BAD_INPUT, "setup_preconditioner: unknown precision");
   if (o.star_set != SPNET_STARS_INTERIOR && o.star_set != SPNET_STARS_ALL)
     return fail(SPNET_ERR_BAD_INPUT, "setup_preconditioner: unknown star set");
+  if (o.batch_rhs < 0 || o.batch_rhs > 32)
+    return fail(SPNET_ERR_BAD_INPUT, "setup_preconditioner: batch_rhs must be in 0..32");
   spnet_pc_s* pc = new spnet_pc_s();
   pc->op = op;
   pc->mem.stream = op->stream;
@@ -37,6 +39,7 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
   pc->star_set = o.star_set;
   pc->flexible = o.flexible < 0 ? (o.precision == SPNET_PREC_MIXED ? 1 : 0) : (o.flexible ? 1 : 0);
   pc->max_restarts = o.max_restarts < 0 ? 0 : o.max_restarts;
+  pc->batch_rhs = o.batch_rhs < 1 ? 1 : o.batch_rhs;
   pc->d = op->dim;
   pc->nc = 1 << op->dim;
   pc->ndof = op->ndof;
@@ -307,6 +310,41 @@ int spnet_pc_apply(spnet_pc_t pc, const double* r, double* z, int mem) {
   cudaGetLastError();  // start from a clean error state
   if (!pc || !r || !z) return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_apply: null argument");
   return with_free_vectors(pc, r, pc->N, z, pc->N, mem, apply_all);
+}
+
+int spnet_pc_apply_batch(spnet_pc_t pc, int k, const double* r, double* z, int which, int mem) {
+  cudaGetLastError();  // start from a clean error state
+  if (!pc || !r || !z) return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_apply_batch: null argument");
+  if (k < 1 || k > 32) return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_apply_batch: k must be in 1..32");
+  if (which < 0 || which > 2) return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_apply_batch: which must be 0, 1 or 2");
+  if (mem != SPNET_MEM_HOST && mem != SPNET_MEM_DEVICE)
+    return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_apply_batch: bad mem flag");
+  if ((int64_t)k > star_batch_max_k(pc))
+    return fail(SPNET_ERR_UNSUPPORTED, "spnet_pc_apply_batch: the largest star's solve vector for k right-hand "
+                                       "sides exceeds a block's shared memory");
+  cudaStream_t s = pc->op->stream;
+  const int64_t n = (int64_t)k * pc->N;
+  DevArena tmp;
+  tmp.stream = s;
+  struct Guard {
+    DevArena& a;
+    ~Guard() { a.free_all(); }
+  } guard{tmp};
+  const double* din = r;
+  double* dout = z;
+  if (mem == SPNET_MEM_HOST) {
+    double *a = nullptr, *b = nullptr;
+    SPNET_TRY(tmp.get(&a, n > 0 ? n : 1));
+    SPNET_TRY(tmp.get(&b, n > 0 ? n : 1));
+    SPNET_TRY(copy_in(r, a, sizeof(double) * n, mem, s));
+    din = a;
+    dout = b;
+  }
+  SPNET_TRY(pc_apply_batch_free(pc, k, din, dout, which));
+  if (mem == SPNET_MEM_HOST) SPNET_TRY(copy_out(dout, z, sizeof(double) * n, mem, s));
+  SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+  SPNET_CUDA_TRY(cudaGetLastError());
+  return SPNET_OK;
 }
 
 int spnet_pc_stars(spnet_pc_t pc, const double* r, double* z, int mem) {

@@ -565,6 +565,190 @@ void launch_coarse_apply(spnet_pc_s* pc, const double* rc, double* zc, const int
   }
 }
 
+// ---------------------------------------------------------------------------
+// The coarse solve for k right-hand sides at once (k <= 32): Z_c = A_0^{-1}
+// R_0 R with blocks [coarse dof][k].  One block per stored tile stages the
+// tile (rows padded), the restricted right-hand sides of its row block and of
+// its column block in shared memory, and forms Z_IJ R_J (part [I][J]) and, off
+// the diagonal, Z_IJ^T R_I (part [J][I]).  A thread owns UR rows (interleaved
+// across the lanes: no bank conflicts on the padded tile) times JR
+// right-hand sides and sums each over the tile's 128 columns in order, so a
+// result does not depend on k.  A second kernel sums the parts of each row in
+// tile order.  The tile is read once for all k.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline size_t coarse_batch_smem(int vb, int kp) {
+  return (size_t)vb * (CT * (CT + 1) + 2 * CT * kp);
+}
+
+template <int KP>
+struct BatchTile {
+  static constexpr int JR = KP < 4 ? KP : 4;                       // right-hand sides per thread
+  static constexpr int UR = CT * KP / (256 * JR) > 1 ? CT * KP / (256 * JR) : 1;  // rows per thread
+  static constexpr int TPG = CT / UR;                              // threads per group of JR columns
+  static constexpr int ACTIVE = TPG * (KP / JR);                   // threads with work (<= 256)
+};
+
+template <class T, int KP>
+__global__ void __launch_bounds__(256) k_coarse_batch(const T* __restrict__ tiles, int nt, int64_t m0, int k,
+                                                      const double* __restrict__ EP, const int32_t* __restrict__ rtab,
+                                                      T* __restrict__ part, const int* done) {
+  using BT = BatchTile<KP>;
+  extern __shared__ __align__(16) char sm_cb[];
+  T (*Zs)[CT + 1] = reinterpret_cast<T (*)[CT + 1]>(sm_cb);
+  T* sI = reinterpret_cast<T*>(sm_cb + sizeof(T) * CT * (CT + 1));
+  T* sJ = sI + CT * KP;
+  pdl_wait();
+  pdl_trigger();
+  if (done && *done) return;
+  int I, J;
+  upper_tile(blockIdx.x, nt, &I, &J);
+  const T* Zt = tiles + (int64_t)blockIdx.x * CT * CT;
+  for (int q = threadIdx.x; q < CT * CT; q += blockDim.x) Zs[q / CT][q % CT] = Zt[q];
+  // restricted right-hand sides: sum over the corner sums around the coarse dof's mesh node
+  for (int q = threadIdx.x; q < 2 * CT * KP; q += blockDim.x) {
+    const int side = q / (CT * KP), u = (q / KP) % CT, j = q % KP;
+    const int64_t ci = (int64_t)(side == 0 ? I : J) * CT + u;
+    T v = T(0);
+    if (ci < m0 && j < k) {
+      double sum = 0.0;
+#pragma unroll
+      for (int cp = 0; cp < 8; ++cp) {
+        const int off = rtab[8 * ci + cp];
+        if (off >= 0) sum += EP[(int64_t)off * k + j];
+      }
+      v = (T)sum;
+    }
+    (side == 0 ? sI : sJ)[u * KP + j] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x >= BT::ACTIVE) return;  // no barrier follows
+  const int g = threadIdx.x / BT::TPG, ut = threadIdx.x % BT::TPG;
+  const int j0 = g * BT::JR;
+  {  // part[I][J][u][j] = sum_c Z[u][c] R_J[c][j]
+    T acc[BT::UR][BT::JR];
+#pragma unroll
+    for (int a = 0; a < BT::UR; ++a)
+#pragma unroll
+      for (int b = 0; b < BT::JR; ++b) acc[a][b] = T(0);
+    for (int c = 0; c < CT; ++c) {
+      T rv[BT::JR];
+#pragma unroll
+      for (int b = 0; b < BT::JR; ++b) rv[b] = sJ[c * KP + j0 + b];
+#pragma unroll
+      for (int a = 0; a < BT::UR; ++a) {
+        const T z = Zs[ut + a * BT::TPG][c];
+#pragma unroll
+        for (int b = 0; b < BT::JR; ++b) acc[a][b] = fma(z, rv[b], acc[a][b]);
+      }
+    }
+    T* out = part + ((int64_t)I * nt + J) * CT * KP;
+#pragma unroll
+    for (int a = 0; a < BT::UR; ++a)
+#pragma unroll
+      for (int b = 0; b < BT::JR; ++b) out[(ut + a * BT::TPG) * KP + j0 + b] = acc[a][b];
+  }
+  if (I != J) {  // part[J][I][c][j] = sum_u Z[u][c] R_I[u][j]
+    T acc[BT::UR][BT::JR];
+#pragma unroll
+    for (int a = 0; a < BT::UR; ++a)
+#pragma unroll
+      for (int b = 0; b < BT::JR; ++b) acc[a][b] = T(0);
+    for (int u = 0; u < CT; ++u) {
+      T rv[BT::JR];
+#pragma unroll
+      for (int b = 0; b < BT::JR; ++b) rv[b] = sI[u * KP + j0 + b];
+#pragma unroll
+      for (int a = 0; a < BT::UR; ++a) {
+        const T z = Zs[u][ut + a * BT::TPG];
+#pragma unroll
+        for (int b = 0; b < BT::JR; ++b) acc[a][b] = fma(z, rv[b], acc[a][b]);
+      }
+    }
+    T* out = part + ((int64_t)J * nt + I) * CT * KP;
+#pragma unroll
+    for (int a = 0; a < BT::UR; ++a)
+#pragma unroll
+      for (int b = 0; b < BT::JR; ++b) out[(ut + a * BT::TPG) * KP + j0 + b] = acc[a][b];
+  }
+}
+
+// zc[i][j] = sum over K of part[R][K][i - 128 R][j] in K order, R = i / 128
+template <class T>
+__global__ void __launch_bounds__(256) k_coarse_batch_reduce(int nt, int64_t m0, int k, int kp,
+                                                             const T* __restrict__ part, double* __restrict__ zc,
+                                                             const int* done) {
+  pdl_wait();
+  pdl_trigger();
+  if (done && *done) return;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= m0 * k) return;
+  const int64_t i = q / k;
+  const int j = (int)(q % k);
+  const int64_t R = i / CT;
+  const T* pr = part + (R * nt * CT + (i - R * CT)) * kp + j;
+  double sum = 0.0;
+  for (int K0 = 0; K0 < nt; K0 += 8) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = K0 + u < nt ? pr[(int64_t)(K0 + u) * CT * kp] : T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (K0 + u < nt) sum += (double)v[u];
+  }
+  zc[q] = sum;
+}
+
+// bytes of the parts of the k-right-hand-side coarse product
+size_t coarse_batch_part_bytes(const spnet_pc_s* pc, int k) {
+  const int kp = k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
+  const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
+  return (size_t)vb * pc->ctiles_n * pc->ctiles_n * CT * kp;
+}
+
+template <class T, int KP>
+static int coarse_batch_t(spnet_pc_s* pc, const double* EP, int k, double* ZC, void* part, const int* done,
+                          cudaStream_t s) {
+  static std::atomic<bool> attr_set[64];  // per device
+  int dev = 0;
+  SPNET_CUDA_TRY(cudaGetDevice(&dev));
+  dev &= 63;
+  const size_t smem = coarse_batch_smem((int)sizeof(T), KP);
+  if (!attr_set[dev]) {
+    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_coarse_batch<T, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set[dev] = true;
+  }
+  const unsigned tiles = (unsigned)n_upper_tiles(pc->ctiles_n);
+  const unsigned rblocks = (unsigned)((pc->m0 * k + 255) / 256);
+  launch_pdl(k_coarse_batch<T, KP>, tiles, 256, smem, s, (const T*)pc->ctiles, pc->ctiles_n, (int64_t)pc->m0, k, EP,
+             (const int32_t*)pc->rtab, (T*)part, done);
+  launch_pdl(k_coarse_batch_reduce<T>, rblocks, 256, 0, s, pc->ctiles_n, (int64_t)pc->m0, k, KP, (const T*)part, ZC,
+             done);
+  return SPNET_OK;
+}
+
+template <class T>
+static int coarse_batch_p(spnet_pc_s* pc, const double* EP, int k, double* ZC, void* part, const int* done,
+                          cudaStream_t s) {
+  if (k <= 1) return coarse_batch_t<T, 1>(pc, EP, k, ZC, part, done, s);
+  if (k <= 2) return coarse_batch_t<T, 2>(pc, EP, k, ZC, part, done, s);
+  if (k <= 4) return coarse_batch_t<T, 4>(pc, EP, k, ZC, part, done, s);
+  if (k <= 8) return coarse_batch_t<T, 8>(pc, EP, k, ZC, part, done, s);
+  if (k <= 16) return coarse_batch_t<T, 16>(pc, EP, k, ZC, part, done, s);
+  return coarse_batch_t<T, 32>(pc, EP, k, ZC, part, done, s);
+}
+
+// ZC [m0][k] = A_0^{-1} R_0 R from the element corner sums EP [corner entries][k]
+int launch_coarse_batch(spnet_pc_s* pc, const double* EP, int k, double* ZC, void* part, const int* done,
+                        cudaStream_t s) {
+  if (pc->m0 == 0) return SPNET_OK;
+  if (k < 1 || k > 32) return fail(SPNET_ERR_BAD_INPUT, "coarse solve: 1..32 right-hand sides at once");
+  note_launch();
+  note_launch();  // the product and its row reduction
+  ProfScope ps(KID_COARSE, s);
+  if (pc->precision == SPNET_PREC_FP64) return coarse_batch_p<double>(pc, EP, k, ZC, part, done, s);
+  return coarse_batch_p<float>(pc, EP, k, ZC, part, done, s);
+}
+
 // rtab[ci][cp]: offset of the corner sum of the element at position cp around
 // the mesh node of coarse dof ci (corner nc-1-cp of that element), -1 if none
 __global__ void k_restrict_table(int64_t nmc, Mesh m, int ndof, const int32_t* __restrict__ cidx,

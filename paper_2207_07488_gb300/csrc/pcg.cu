@@ -23,80 +23,6 @@ namespace spnet {
 #define GRID_STRIDE(i, n) \
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
-// block sum of one value per thread into out[blockIdx.x]; fixed order
-__device__ __forceinline__ void block_partial(double v, double* out, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    out[blockIdx.x] = t;
-  }
-  __syncthreads();
-}
-
-// true in the block that finishes last (its partials and everyone's are visible)
-__device__ __forceinline__ bool last_block(unsigned* cnt) {
-  __shared__ bool is_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (is_last) __threadfence();
-  return is_last;
-}
-
-// a thread's share of the sum of n partials: part[tid], part[tid + B], ... in
-// that order, eight L2 loads in flight (the partials were written by other
-// blocks or by the previous kernel)
-__device__ __forceinline__ double thread_share(const double* part, int n) {
-  double s = 0.0;
-  constexpr int U = 8;
-  for (int i0 = threadIdx.x; i0 < n; i0 += U * (int)blockDim.x) {
-    double v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = i0 + u * (int)blockDim.x;
-      v[u] = i < n ? __ldcg(part + i) : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) s += v[u];
-  }
-  return s;
-}
-
-// sum of n partials by one block in a fixed order (result valid in every thread)
-__device__ __forceinline__ double block_sum(const double* part, int n, double* sh) {
-  double s = thread_share(part, n);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-  __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-  __syncthreads();
-  return t;
-}
-
-// three such sums at once (sh holds 3 * 32 doubles)
-__device__ __forceinline__ void block_sum3(const double* p0, int n0, const double* p1, int n1, const double* p2,
-                                           int n2, double* sh, double* out) {
-  double s[3] = {thread_share(p0, n0), thread_share(p1, n1), thread_share(p2, n2)};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
-    if ((threadIdx.x & 31) == 0) sh[32 * k + (threadIdx.x >> 5)] = s[k];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[32 * k + w];
-    out[k] = t;
-  }
-  __syncthreads();
-}
-
 // b = f_I - K_ID g (Section 3), in pc order
 __global__ void k_build_rhs(int64_t N, const int32_t* perm, const int64_t* free_dofs, const double* f,
                             const int64_t* fdp, const int32_t* fdc, const double* fdv, const double* g,
@@ -737,6 +663,26 @@ int pcg_run(spnet_op_s* op, spnet_pc_s* pc, int nrhs, const double* f, const dou
     df = a;
     dg = b;
     dx = c;
+  }
+  const int kmax = star_batch_max_k(pc);
+  const int kb = pc->batch_rhs < kmax ? pc->batch_rhs : kmax;
+  if (nrhs >= 2 && kb >= 2) {  // blocks of right-hand sides stepped together
+    int worst = SPNET_OK;
+    for (int k0 = 0; k0 < nrhs; k0 += kb) {
+      const int kk = nrhs - k0 < kb ? nrhs - k0 : kb;
+      const double* fk = df + (int64_t)k0 * nd;
+      const double* gk = dg + (int64_t)k0 * ndir;
+      double* xk = dx + (int64_t)k0 * nd;
+      spnet_stats* sk = stats ? stats + k0 : nullptr;
+      const int rc = kk >= 2 ? pcg_batch_run(op, pc, kk, fk, gk, xk, use_x0, rtol, maxit, sk)
+                             : pcg_run(op, pc, 1, fk, gk, xk, use_x0, rtol, maxit, SPNET_MEM_DEVICE, sk);
+      if (rc == SPNET_ERR_NO_CONVERGENCE) worst = rc;
+      else if (rc != SPNET_OK) return rc;
+    }
+    if (mem == SPNET_MEM_HOST) SPNET_TRY(copy_out(dx, x, sizeof(double) * nrhs * nd, mem, s));
+    SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+    if (worst != SPNET_OK) return fail(worst, "pcg_solve: maxit reached before rtol");
+    return SPNET_OK;
   }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);

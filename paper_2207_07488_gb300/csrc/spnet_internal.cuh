@@ -111,6 +111,7 @@ struct spnet_pc_s {
   spnet_op_s* op = nullptr;
   spnet::DevArena mem;
   int precision = SPNET_PREC_MIXED, star_set = SPNET_STARS_INTERIOR, flexible = 1, max_restarts = 2;
+  int batch_rhs = 1;            // right-hand sides pcg_solve steps together
   int d = 0, ndof = 1, nc = 4;  // nc = 2^d corners
   int gamma[3] = {0, 0, 0};     // Dirichlet face bitmask per component
   int nH[3] = {1, 1, 1};
@@ -158,6 +159,7 @@ struct spnet_pc_s {
   int solve_blocks = 0;            // blocks of the solve (a multiple of the SM count)
   size_t solve_smem = 0;           // its dynamic shared memory per block
   int32_t* sorder = nullptr;       // [solve_blocks*solve_wpb] star of each warp slot, -1: idle
+  int32_t* star_desc = nullptr;    // [S] stars by solve cost, largest first
   // work vectors (pc order)
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *b = nullptr;
   double* r2 = nullptr;            // second residual buffer (the iterations alternate)
@@ -278,6 +280,14 @@ int pc_galerkin(spnet_pc_s* pc, double* A0_dense);
 
 // starfact.cu
 int pc_factor_stars(spnet_pc_s* pc);
+// star solves for k <= 32 right-hand sides at once (R, W: [dofs][k]); W in the solve precision
+int launch_star_batch(spnet_pc_s* pc, const double* R, int k, void* W, const int* done, cudaStream_t s);
+// the largest block width (a power of two <= 32) whose star solve fits a block's shared memory
+int star_batch_max_k(const spnet_pc_s* pc);
+// coarse solve for k <= 32 right-hand sides at once: ZC [m0][k] from the corner sums EP [entries][k]
+size_t coarse_batch_part_bytes(const spnet_pc_s* pc, int k);
+int launch_coarse_batch(spnet_pc_s* pc, const double* EP, int k, double* ZC, void* part, const int* done,
+                        cudaStream_t s);
 // stars on r, or (q set: a PCG step) on r - alpha q with alpha from the SpMV's partials
 void launch_star_solve(spnet_pc_s* pc, const double* r, const double* q, const spnet::Scal* sc, const int* done,
                        cudaStream_t s);
@@ -300,6 +310,23 @@ void from_pc(spnet_pc_s* pc, const double* pc_vec, double* free_vec);
 int export_item(spnet_pc_s* pc, int what, void* host_buf);
 int pcg_run(spnet_op_s* op, spnet_pc_s* pc, int nrhs, const double* f, const double* g, double* x,
             int use_x0, double rtol, int maxit, int mem, spnet_stats* stats);
+__global__ void k_build_rhs(int64_t N, const int32_t* perm, const int64_t* free_dofs, const double* f,
+                            const int64_t* fdp, const int32_t* fdc, const double* fdv, const double* g,
+                            double* b);
+__global__ void k_x0_from_dofs(int64_t N, const int32_t* perm, const int64_t* free_dofs, const double* x,
+                               double* xp);
+__global__ void k_expand(int64_t n_dof, const int64_t* free_of, const int32_t* iperm, const double* xp,
+                         const double* g, double* out);
+__global__ void k_residual(int64_t N, const double* b, const double* q, double* r, double* partial,
+                           double* out, unsigned* cnt);
+
+// batch.cu: k (2..32) right-hand sides stepped together; device arrays f [k][n_dof],
+// g [k][n_dir], x [k][n_dof]; stats [k] host
+int pcg_batch_run(spnet_op_s* op, spnet_pc_s* pc, int k, const double* f, const double* g, double* x,
+                  int use_x0, double rtol, int maxit, spnet_stats* stats);
+// z_j = B r_j (which 0), the coarse term (1) or the star term (2) for k <= 32 residuals;
+// r, z device [k][n_free] in free order
+int pc_apply_batch_free(spnet_pc_s* pc, int k, const double* r, double* z, int which);
 
 // Butterfly reduce-scatter of K per-lane values (K a power of two, K <= 32):
 // K-1 + log2(32/K) shuffles instead of 5K.  Afterwards lane L holds the warp
@@ -385,5 +412,79 @@ template <int N>
 struct Pow2 {
   static constexpr int value = N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : 32;
 };
+
+// block sum of one value per thread into out[blockIdx.x]; fixed order
+__device__ __forceinline__ void block_partial(double v, double* out, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    out[blockIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// true in the block that finishes last (its partials and everyone's are visible)
+__device__ __forceinline__ bool last_block(unsigned* cnt) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+// a thread's share of the sum of n partials: part[tid], part[tid + B], ... in
+// that order, eight L2 loads in flight (the partials were written by other
+// blocks or by the previous kernel)
+__device__ __forceinline__ double thread_share(const double* part, int n) {
+  double s = 0.0;
+  constexpr int U = 8;
+  for (int i0 = threadIdx.x; i0 < n; i0 += U * (int)blockDim.x) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      v[u] = i < n ? __ldcg(part + i) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) s += v[u];
+  }
+  return s;
+}
+
+// sum of n partials by one block in a fixed order (result valid in every thread)
+__device__ __forceinline__ double block_sum(const double* part, int n, double* sh) {
+  double s = thread_share(part, n);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  __syncthreads();
+  return t;
+}
+
+// three such sums at once (sh holds 3 * 32 doubles)
+__device__ __forceinline__ void block_sum3(const double* p0, int n0, const double* p1, int n1, const double* p2,
+                                           int n2, double* sh, double* out) {
+  double s[3] = {thread_share(p0, n0), thread_share(p1, n1), thread_share(p2, n2)};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    if ((threadIdx.x & 31) == 0) sh[32 * k + (threadIdx.x >> 5)] = s[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[32 * k + w];
+    out[k] = t;
+  }
+  __syncthreads();
+}
 
 }  // namespace spnet

@@ -884,6 +884,165 @@ void launch_star_solve(spnet_pc_s* pc, const double* r, const double* q, const S
         (float*)pc->w, done);
 }
 
+// ---------------------------------------------------------------------------
+// Star solves for k right-hand sides at once (k <= 32): one warp per star,
+// lane j owns right-hand side j.  The warp streams the same window records as
+// the one-right-hand-side solve, but walks each window's 32 slots in order:
+// every lane adds coefficient * y[column][j] to its running sum and, at a
+// segment end, writes the sum to its row and starts the next one.  The
+// right-hand sides do not interact, so no scan and no barrier between levels
+// is needed; the factor bytes read once serve all k.
+// R, W: [dofs][k] (right-hand side fastest); y in shared memory [n][kp].
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int64_t batch_warp_bytes(int vb, int ymax, int kp) {
+  return (int64_t)RING_W * rec_bytes(vb) + align_up((int64_t)vb * ymax * kp, 16) + align_up(2ll * ymax, 16) +
+         (int64_t)sizeof(StarHdr);
+}
+
+template <class T>
+__global__ void __launch_bounds__(32) k_star_batch(int k, int kp, int ymax, const int32_t* __restrict__ order,
+                                                   const StarHdr* __restrict__ hdr, const char* __restrict__ recs,
+                                                   const uint16_t* __restrict__ iperm,
+                                                   const double* __restrict__ R, T* __restrict__ W,
+                                                   const int* done) {
+  extern __shared__ int4 smem4[];
+  pdl_wait();
+  pdl_trigger();
+  if (done && *done) return;
+  const int lane = threadIdx.x;
+  const int s = order[blockIdx.x];
+  constexpr int RB = REC_COEF + WIN * (int)sizeof(T);
+  constexpr unsigned RING_BYTES = (unsigned)(RING_W * RB);
+  char* ring = (char*)smem4;
+  T* y = (T*)(ring + RING_BYTES);
+  uint16_t* ip = (uint16_t*)((char*)y + align_up((int64_t)sizeof(T) * ymax * kp, 16));
+  StarHdr* h = (StarHdr*)((char*)ip + align_up(2ll * ymax, 16));
+  if (lane < (int)(sizeof(StarHdr) / 4)) ((int32_t*)h)[lane] = __ldg(((const int32_t*)(hdr + s)) + lane);
+  __syncwarp();
+  const int64_t wb = h->wbase;
+  const int n = h->n, nw = h->ne;
+  const bool copier = lane * 16 < RB;
+  const char* src = recs + h->eoff * RB + lane * 16;
+  const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring);
+  unsigned dst = ring_s + lane * 16;
+  int F = 0;
+  for (; F < nw && F < RING_W; ++F) {
+    if (copier) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    src += RB;
+    dst += RB;
+  }
+  if (dst - ring_s - lane * 16 >= RING_BYTES) dst -= RING_BYTES;
+  int eo[8], es[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    eo[c] = h->eo[c];
+    es[c] = h->es[c];
+  }
+  // gather: y[position][j] = R[pc index][j], eight local dofs in flight
+  const bool act = lane < k;
+  for (int t0 = 0; t0 < n; t0 += 8) {
+    double rv[8];
+    int pv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u;
+      rv[u] = 0.0;
+      pv[u] = 0;
+      if (t < n) {
+        int base = es[0] - eo[0];
+#pragma unroll
+        for (int c = 1; c < 8; ++c) base = t >= eo[c] ? es[c] - eo[c] : base;
+        pv[u] = __ldg(&iperm[wb + t]);
+        if (act) rv[u] = __ldg(&R[(int64_t)(base + t) * k + lane]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u;
+      if (t < n) {
+        y[pv[u] * kp + lane] = (T)rv[u];  // lanes past k hold zeros
+        if (lane == 0) ip[t] = (uint16_t)pv[u];
+      }
+    }
+  }
+  __syncwarp();
+  const char* rec = ring;
+  const char* const ring_end = ring + RING_BYTES;
+  T acc = T(0);
+  for (int w = 0; w < nw; ++w) {
+    if (F == w + RING_W) asm volatile("cp.async.wait_group %0;\n" ::"n"(RING_W - 1) : "memory");
+    else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+    const uint2 d = *(const uint2*)rec;
+    const uint16_t* col = (const uint16_t*)(rec + REC_HDR);
+    const T* coef = (const T*)(rec + REC_COEF);
+#pragma unroll 8
+    for (int sl = 0; sl < WIN; ++sl) {
+      const int c = col[sl];
+      acc = fma(coef[sl], y[c * kp + lane], acc);
+      if ((d.x >> sl) & 1u) {  // uniform: the slot ends a row's segment (its diagonal)
+        y[c * kp + lane] = acc;
+        acc = T(0);
+      }
+    }
+    if (!(d.y & 0x100u)) acc = T(0);  // no segment continues into the next window
+    __syncwarp();
+    rec += RB;
+    if (rec == ring_end) rec = ring;
+    if (F < nw) {  // refill the slot just consumed
+      if (copier) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+      src += RB;
+      dst += RB;
+      if (dst - ring_s - lane * 16 >= RING_BYTES) dst -= RING_BYTES;
+      ++F;
+    }
+  }
+  if (act)
+    for (int t = 0; t < n; ++t) W[(wb + t) * k + lane] = y[ip[t] * kp + lane];
+}
+
+int star_batch_max_k(const spnet_pc_s* pc) {
+  const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
+  int kp = 32;
+  while (kp > 1 && batch_warp_bytes(vb, pc->max_star, kp) > 227 * 1024) kp >>= 1;
+  return kp;
+}
+
+int launch_star_batch(spnet_pc_s* pc, const double* R, int k, void* W, const int* done, cudaStream_t s) {
+  if (pc->S == 0) return SPNET_OK;
+  if (k < 1 || k > 32) return fail(SPNET_ERR_BAD_INPUT, "star solves: 1..32 right-hand sides at once");
+  const int kp = k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
+  const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
+  const size_t smem = (size_t)batch_warp_bytes(vb, pc->max_star, kp);
+  if (smem > 227 * 1024)
+    return fail(SPNET_ERR_UNSUPPORTED, "star solves: the largest star and " + std::to_string(k) +
+                                           " right-hand sides exceed a block's shared memory");
+  static std::atomic<bool> attr_set[64][2];  // per device and precision
+  int dev = 0;
+  SPNET_CUDA_TRY(cudaGetDevice(&dev));
+  dev &= 63;
+  if (!attr_set[dev][vb == 8 ? 1 : 0]) {
+    if (vb == 8)
+      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    else
+      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr_set[dev][vb == 8 ? 1 : 0] = true;
+  }
+  note_launch();
+  ProfScope ps(KID_STARS, s);
+  if (vb == 8)
+    launch_pdl(k_star_batch<double>, pc->S, 32, smem, s, k, kp, pc->max_star, (const int32_t*)pc->star_desc,
+               (const StarHdr*)pc->shdr, (const char*)pc->srec, (const uint16_t*)pc->iperm_star, R, (double*)W,
+               done);
+  else
+    launch_pdl(k_star_batch<float>, pc->S, 32, smem, s, k, kp, pc->max_star, (const int32_t*)pc->star_desc,
+               (const StarHdr*)pc->shdr, (const char*)pc->srec, (const uint16_t*)pc->iperm_star, R, (float*)W,
+               done);
+  return SPNET_OK;
+}
+
 // headers, inverse permutations and entry streams of all stars
 static int pack_streams(spnet_pc_s* pc, DevArena& tmp, const std::vector<int32_t>& lev,
                         const std::vector<int32_t>& nz) {
@@ -977,6 +1136,8 @@ static int pack_streams(spnet_pc_s* pc, DevArena& tmp, const std::vector<int32_t
     slot[(size_t)b * wpb + fill[b]++] = i;
     if (fill[b] < wpb) heap.push({top.first + cost[i], b});
   }
+  SPNET_TRY(pc->mem.get(&pc->star_desc, S));  // stars by cost, largest first (multi-right-hand-side solves)
+  SPNET_CUDA_TRY(cudaMemcpyAsync(pc->star_desc, ord.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
   SPNET_TRY(pc->mem.get(&pc->sorder, slot.size()));
   SPNET_CUDA_TRY(cudaMemcpyAsync(pc->sorder, slot.data(), sizeof(int32_t) * slot.size(), cudaMemcpyHostToDevice, s));
   pc->solve_wpb = wpb;

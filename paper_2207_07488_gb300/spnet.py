@@ -35,6 +35,7 @@ EXPORTED = [
     "spnet_pc_prolong", "spnet_pc_stars", "spnet_pc_export", "spnet_launch_count",
     "spnet_profile_enable", "spnet_profile_read", "spnet_profile_reset", "spnet_pc_restrict_static",
     "spnet_server_create", "spnet_server_submit", "spnet_server_wait", "spnet_server_destroy",
+    "spnet_pc_apply_batch",
 ]
 KERNELS = ["spmv", "update", "restrict", "stars", "coarse", "combine", "direction",
            "star_symbolic", "star_numeric", "sweep", "galerkin"]
@@ -48,7 +49,7 @@ class SpnetError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("star_set", C.c_int), ("flexible", C.c_int),
-                ("max_restarts", C.c_int), ("reserved", C.c_int * 12)]
+                ("max_restarts", C.c_int), ("batch_rhs", C.c_int), ("reserved", C.c_int * 11)]
 
 
 class Request(C.Structure):
@@ -125,6 +126,11 @@ def load(build_if_missing: bool = True):
     lib.spnet_profile_enable.argtypes = [i32]
     lib.spnet_profile_read.argtypes = [i32, C.POINTER(i64), C.POINTER(dbl)]
     lib.spnet_profile_reset.argtypes = []
+    lib.spnet_pc_apply_batch.argtypes = [P, i32, P, P, i32, i32]
+    lib.spnet_server_create.argtypes = [i32, i64, C.POINTER(P)]
+    lib.spnet_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(i64)]
+    lib.spnet_server_wait.argtypes = [P, i64, C.POINTER(Result)]
+    lib.spnet_server_destroy.argtypes = [P]
     for name in EXPORTED:
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -299,12 +305,13 @@ class Preconditioner:
     """setup_preconditioner: the two-level additive Schwarz preconditioner."""
 
     def __init__(self, op: Operator, H, gamma_faces, precision=PREC_MIXED, star_set=STARS_INTERIOR,
-                 flexible=-1, max_restarts=2):
+                 flexible=-1, max_restarts=2, batch_rhs=1):
         self._lib = op._lib
         self.op = op
         self.handle = C.c_void_p()
         o = Options()
         o.precision, o.star_set, o.flexible, o.max_restarts = precision, star_set, flexible, max_restarts
+        o.batch_rhs = batch_rhs
         gf = (C.c_int * 3)(*(list(gamma_faces) + [0, 0, 0])[:3])
         _check(self._lib.setup_preconditioner(op.handle, float(H), gf, C.byref(o),
                                               C.byref(self.handle)))
@@ -332,6 +339,16 @@ class Preconditioner:
 
     def stars(self, r):
         return self._vec_call(self._lib.spnet_pc_stars, r, self.op.info.n_free)
+
+    def apply_batch(self, R, which=0):
+        """spnet_pc_apply_batch: z_j = B r_j (which 0), the coarse term (1) or the star
+        term (2) for the rows r_j of R, shape (k, n_free), 1 <= k <= 32, in one pass."""
+        R = np.ascontiguousarray(np.atleast_2d(np.asarray(R, np.float64)))
+        k, _ = R.shape
+        Z = np.zeros(R.shape)
+        _check(self._lib.spnet_pc_apply_batch(self.handle, int(k), C.c_void_p(R.ctypes.data),
+                                              C.c_void_p(Z.ctypes.data), int(which), MEM_HOST))
+        return Z
 
     def restrict(self, r):
         return self._vec_call(self._lib.spnet_pc_restrict, r, self.info.m0)
@@ -429,7 +446,7 @@ class Server:
         self._live = {}
 
     def submit(self, problem, f=None, g=None, precision=PREC_MIXED, rtol=1e-8, maxit=2000,
-               star_set=None, flexible=-1, max_restarts=2):
+               star_set=None, flexible=-1, max_restarts=2, batch_rhs=1):
         """Queue one request for `problem` (a networks.Problem); f: (n_dof,) or (nrhs, n_dof),
         default problem.f; g likewise over the Dirichlet dofs, default problem.dirichlet_vals."""
         net = problem.net
@@ -471,6 +488,7 @@ class Server:
         q.opts.star_set = ss if isinstance(ss, int) else (STARS_ALL if ss == "all" else STARS_INTERIOR)
         q.opts.flexible = flexible
         q.opts.max_restarts = max_restarts
+        q.opts.batch_rhs = batch_rhs
         q.rtol = float(rtol)
         q.maxit = int(maxit)
         ticket = C.c_int64(0)

@@ -35,3 +35,22 @@ def test_library_reports_errors_without_a_gpu():
     rc = lib.setup_preconditioner(None, 0.5, None, None, ctypes.byref(ctypes.c_void_p()))
     assert rc == -1
     assert "null operator" in spnet.last_error()
+
+
+def test_every_entry_point_has_argument_types():
+    # without argtypes ctypes passes Python ints as C int: a 64-bit pointer would be cut to 32 bits
+    lib = spnet.load()
+    for name in spnet.EXPORTED:
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert fn.restype is ctypes.c_int, name
+
+
+def test_argument_types_match_the_header():
+    # each declaration's parameter count in the header equals the binding's argtypes
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    lib = spnet.load()
+    for name, params in re.findall(r"^\s*int\s+([a-z_0-9]+)\s*\(([^)]*)\)\s*;", src, flags=re.M):
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(getattr(lib, name).argtypes) == n, name
