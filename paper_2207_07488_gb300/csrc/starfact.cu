@@ -891,7 +891,8 @@ void launch_star_solve(spnet_pc_s* pc, const double* r, const double* q, const S
 // every lane adds coefficient * y[column][j] to its running sum and, at a
 // segment end, writes the sum to its row and starts the next one.  The
 // right-hand sides do not interact, so no scan and no barrier between levels
-// is needed; the factor bytes read once serve all k.
+// is needed; the factor bytes read once serve all k.  Lanes kp..31 (kp: k
+// rounded up to a power of two) only help stream the records.
 // R, W: [dofs][k] (right-hand side fastest); y in shared memory [n][kp].
 // ---------------------------------------------------------------------------
 __host__ __device__ inline int64_t batch_warp_bytes(int vb, int ymax, int kp) {
@@ -939,8 +940,9 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int kp, int ymax, cons
     eo[c] = h->eo[c];
     es[c] = h->es[c];
   }
-  // gather: y[position][j] = R[pc index][j], eight local dofs in flight
-  const bool act = lane < k;
+  // gather: y[position][j] = R[pc index][j], eight local dofs in flight.
+  // Lanes kp..31 have no column of y and touch none of it.
+  const bool act = lane < k, own = lane < kp;
   for (int t0 = 0; t0 < n; t0 += 8) {
     double rv[8];
     int pv[8];
@@ -961,7 +963,7 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int kp, int ymax, cons
     for (int u = 0; u < 8; ++u) {
       const int t = t0 + u;
       if (t < n) {
-        y[pv[u] * kp + lane] = (T)rv[u];  // lanes past k hold zeros
+        if (own) y[pv[u] * kp + lane] = (T)rv[u];  // lanes k..kp-1 hold zeros
         if (lane == 0) ip[t] = (uint16_t)pv[u];
       }
     }
@@ -977,13 +979,19 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int kp, int ymax, cons
     const uint2 d = *(const uint2*)rec;
     const uint16_t* col = (const uint16_t*)(rec + REC_HDR);
     const T* coef = (const T*)(rec + REC_COEF);
-#pragma unroll 8
-    for (int sl = 0; sl < WIN; ++sl) {
-      const int c = col[sl];
-      acc = fma(coef[sl], y[c * kp + lane], acc);
-      if ((d.x >> sl) & 1u) {  // uniform: the slot ends a row's segment (its diagonal)
-        y[c * kp + lane] = acc;
-        acc = T(0);
+    if (own) {
+      // A window holds rows of one level only, so none of its slots reads a
+      // value the window writes: load all 32 first, then sum and store.
+      T yv[WIN];
+#pragma unroll
+      for (int sl = 0; sl < WIN; ++sl) yv[sl] = y[col[sl] * kp + lane];
+#pragma unroll
+      for (int sl = 0; sl < WIN; ++sl) {
+        acc = fma(coef[sl], yv[sl], acc);
+        if ((d.x >> sl) & 1u) {  // the slot ends a row's segment (its diagonal)
+          y[col[sl] * kp + lane] = acc;
+          acc = T(0);
+        }
       }
     }
     if (!(d.y & 0x100u)) acc = T(0);  // no segment continues into the next window
