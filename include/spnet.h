@@ -275,9 +275,11 @@ int spnet_pc_stars(spnet_pc_t pc, const double* r, double* z, int mem);
  * together (Sections 4.1-4.2 applied to each r_j on its own).  r, z [k*n_free]:
  * one right-hand side after another, each in free order; host or device memory
  * by mem.  which: 0 the whole of B; 1 the coarse term R_0^T A_0^{-1} R_0 r only;
- * 2 the star term sum_j E_j A_j^{-1} E_j^T r only.  Errors: BAD_INPUT (null
- * pointer, k, which or mem out of range), UNSUPPORTED (the largest star's solve
- * vector for k right-hand sides exceeds a block's shared memory), CUDA.
+ * 2 the star term sum_j E_j A_j^{-1} E_j^T r only.  Where the largest star's
+ * solve vector for k right-hand sides does not fit a block's shared memory, the
+ * right-hand sides go in several passes of the widest block that does.  Errors:
+ * BAD_INPUT (null pointer, k, which or mem out of range), UNSUPPORTED (the
+ * largest star alone exceeds a block's shared memory), CUDA.
  */
 int spnet_pc_apply_batch(spnet_pc_t pc, int k, const double* r, double* z, int which, int mem);
 

@@ -319,9 +319,6 @@ int spnet_pc_apply_batch(spnet_pc_t pc, int k, const double* r, double* z, int w
   if (which < 0 || which > 2) return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_apply_batch: which must be 0, 1 or 2");
   if (mem != SPNET_MEM_HOST && mem != SPNET_MEM_DEVICE)
     return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_apply_batch: bad mem flag");
-  if ((int64_t)k > star_batch_max_k(pc))
-    return fail(SPNET_ERR_UNSUPPORTED, "spnet_pc_apply_batch: the largest star's solve vector for k right-hand "
-                                       "sides exceeds a block's shared memory");
   cudaStream_t s = pc->op->stream;
   const int64_t n = (int64_t)k * pc->N;
   DevArena tmp;
@@ -340,7 +337,12 @@ int spnet_pc_apply_batch(spnet_pc_t pc, int k, const double* r, double* z, int w
     din = a;
     dout = b;
   }
-  SPNET_TRY(pc_apply_batch_free(pc, k, din, dout, which));
+  // passes of at most the block width whose star solve fits a block's shared memory
+  const int kmax = star_batch_max_k(pc);
+  for (int k0 = 0; k0 < k; k0 += kmax) {
+    const int kk = k - k0 < kmax ? k - k0 : kmax;
+    SPNET_TRY(pc_apply_batch_free(pc, kk, din + (int64_t)k0 * pc->N, dout + (int64_t)k0 * pc->N, which));
+  }
   if (mem == SPNET_MEM_HOST) SPNET_TRY(copy_out(dout, z, sizeof(double) * n, mem, s));
   SPNET_CUDA_TRY(cudaStreamSynchronize(s));
   SPNET_CUDA_TRY(cudaGetLastError());
