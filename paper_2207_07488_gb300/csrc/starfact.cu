@@ -885,38 +885,117 @@ void launch_star_solve(spnet_pc_s* pc, const double* r, const double* q, const S
 }
 
 // ---------------------------------------------------------------------------
-// Star solves for k right-hand sides at once (k <= 32): one warp per star,
-// lane j owns right-hand side j.  The warp streams the same window records as
-// the one-right-hand-side solve, but walks each window's 32 slots in order:
-// every lane adds coefficient * y[column][j] to its running sum and, at a
-// segment end, writes the sum to its row and starts the next one.  The
-// right-hand sides do not interact, so no scan and no barrier between levels
-// is needed; the factor bytes read once serve all k.  Lanes kp..31 (kp: k
-// rounded up to a power of two) only help stream the records.
-// R, W: [dofs][k] (right-hand side fastest); y in shared memory [n][kp].
+// Star solves for k right-hand sides at once (k <= 32).  Each star is solved
+// by kp / JW warps (kp: k rounded up to a power of two; JW = min(kp, 8)), one
+// warp per block, each owning JW right-hand sides.  A warp streams the same
+// window records as the one-right-hand-side solve; its lanes are (slot group
+// q, right-hand side j): lane (q, j) sums slots q*JW .. q*JW + JW - 1 of each
+// window for column j, a segmented scan over the 32 / JW groups (shuffles)
+// joins the parts of a segment cut by a group boundary, and the sum of a
+// segment still open at the window's end is carried into the next window.
+// A window holds rows of one level only, so none of its slots reads a value
+// the window writes: all its values are loaded before any sum is stored.
+// The right-hand sides do not interact, the factor bytes are read from L2 by
+// the kp / JW warps of a star together, and the sums of a column do not depend
+// on the other columns or on k (for a given JW).
+// R, W: [dofs][k] (right-hand side fastest); y in shared memory [n][JW].
 // ---------------------------------------------------------------------------
-__host__ __device__ inline int64_t batch_warp_bytes(int vb, int ymax, int kp) {
-  return (int64_t)RING_W * rec_bytes(vb) + align_up((int64_t)vb * ymax * kp, 16) + align_up(2ll * ymax, 16) +
+constexpr int BRING = 8;  // windows in flight per warp
+
+__host__ __device__ inline int batch_jw(int kp) { return kp < 8 ? kp : 8; }
+
+__host__ __device__ inline int64_t batch_warp_bytes(int vb, int ymax, int jw) {
+  return (int64_t)BRING * rec_bytes(vb) + align_up((int64_t)vb * ymax * jw, 16) + align_up(2ll * ymax, 16) +
          (int64_t)sizeof(StarHdr);
 }
 
-template <class T>
-__global__ void __launch_bounds__(32) k_star_batch(int k, int kp, int ymax, const int32_t* __restrict__ order,
+// the column indices of slots s0 .. s0 + SPL - 1 of a record (one vector load)
+template <int SPL>
+__device__ __forceinline__ void load_cols(const char* rec, int s0, int (&c)[SPL]) {
+  const char* p = rec + REC_HDR + 2 * s0;
+  if constexpr (SPL == 8) {
+    const uint4 v = *(const uint4*)p;
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      c[2 * i] = (int)(w[i] & 0xffffu);
+      c[2 * i + 1] = (int)(w[i] >> 16);
+    }
+  } else if constexpr (SPL == 4) {
+    const uint2 v = *(const uint2*)p;
+    c[0] = (int)(v.x & 0xffffu);
+    c[1] = (int)(v.x >> 16);
+    c[2] = (int)(v.y & 0xffffu);
+    c[3] = (int)(v.y >> 16);
+  } else if constexpr (SPL == 2) {
+    const unsigned v = *(const unsigned*)p;
+    c[0] = (int)(v & 0xffffu);
+    c[1] = (int)(v >> 16);
+  } else {
+    c[0] = *(const uint16_t*)p;
+  }
+}
+
+// their coefficients (vector loads)
+template <int SPL>
+__device__ __forceinline__ void load_coefs(const char* rec, int s0, float (&a)[SPL]) {
+  const float* p = (const float*)(rec + REC_COEF) + s0;
+  if constexpr (SPL >= 4) {
+#pragma unroll
+    for (int i = 0; i < SPL / 4; ++i) {
+      const float4 v = ((const float4*)p)[i];
+      a[4 * i] = v.x;
+      a[4 * i + 1] = v.y;
+      a[4 * i + 2] = v.z;
+      a[4 * i + 3] = v.w;
+    }
+  } else if constexpr (SPL == 2) {
+    const float2 v = *(const float2*)p;
+    a[0] = v.x;
+    a[1] = v.y;
+  } else {
+    a[0] = p[0];
+  }
+}
+
+template <int SPL>
+__device__ __forceinline__ void load_coefs(const char* rec, int s0, double (&a)[SPL]) {
+  const double* p = (const double*)(rec + REC_COEF) + s0;
+  if constexpr (SPL >= 2) {
+#pragma unroll
+    for (int i = 0; i < SPL / 2; ++i) {
+      const double2 v = ((const double2*)p)[i];
+      a[2 * i] = v.x;
+      a[2 * i + 1] = v.y;
+    }
+  } else {
+    a[0] = p[0];
+  }
+}
+
+template <class T, int JW>
+__global__ void __launch_bounds__(32) k_star_batch(int k, int groups, int ymax, const int32_t* __restrict__ order,
                                                    const StarHdr* __restrict__ hdr, const char* __restrict__ recs,
                                                    const uint16_t* __restrict__ iperm,
                                                    const double* __restrict__ R, T* __restrict__ W,
                                                    const int* done) {
+  constexpr int QN = 32 / JW;    // slot groups of a window
+  constexpr int SPL = WIN / QN;  // slots per lane (= JW)
+  constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ int4 smem4[];
   pdl_wait();
   pdl_trigger();
   if (done && *done) return;
   const int lane = threadIdx.x;
-  const int s = order[blockIdx.x];
+  const int q = lane / JW, j = lane % JW;
+  const int s = order[blockIdx.x / groups];
+  const int jj = (blockIdx.x % groups) * JW + j;  // this lane's right-hand side
+  const bool act = jj < k;
   constexpr int RB = REC_COEF + WIN * (int)sizeof(T);
-  constexpr unsigned RING_BYTES = (unsigned)(RING_W * RB);
+  constexpr unsigned RING_BYTES = (unsigned)(BRING * RB);
   char* ring = (char*)smem4;
   T* y = (T*)(ring + RING_BYTES);
-  uint16_t* ip = (uint16_t*)((char*)y + align_up((int64_t)sizeof(T) * ymax * kp, 16));
+  uint16_t* ip = (uint16_t*)((char*)y + align_up((int64_t)sizeof(T) * ymax * JW, 16));
   StarHdr* h = (StarHdr*)((char*)ip + align_up(2ll * ymax, 16));
   if (lane < (int)(sizeof(StarHdr) / 4)) ((int32_t*)h)[lane] = __ldg(((const int32_t*)(hdr + s)) + lane);
   __syncwarp();
@@ -927,7 +1006,7 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int kp, int ymax, cons
   const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring);
   unsigned dst = ring_s + lane * 16;
   int F = 0;
-  for (; F < nw && F < RING_W; ++F) {
+  for (; F < nw && F < BRING; ++F) {
     if (copier) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     src += RB;
@@ -940,15 +1019,14 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int kp, int ymax, cons
     eo[c] = h->eo[c];
     es[c] = h->es[c];
   }
-  // gather: y[position][j] = R[pc index][j], eight local dofs in flight.
-  // Lanes kp..31 have no column of y and touch none of it.
-  const bool act = lane < k, own = lane < kp;
-  for (int t0 = 0; t0 < n; t0 += 8) {
-    double rv[8];
-    int pv[8];
+  // gather: y[position][j] = R[pc index][jj]; the lanes of a slot group take one local dof
+  constexpr int GU = 4;
+  for (int t0 = 0; t0 < n; t0 += QN * GU) {
+    double rv[GU];
+    int pv[GU];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int t = t0 + u;
+    for (int u = 0; u < GU; ++u) {
+      const int t = t0 + u * QN + q;
       rv[u] = 0.0;
       pv[u] = 0;
       if (t < n) {
@@ -956,45 +1034,72 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int kp, int ymax, cons
 #pragma unroll
         for (int c = 1; c < 8; ++c) base = t >= eo[c] ? es[c] - eo[c] : base;
         pv[u] = __ldg(&iperm[wb + t]);
-        if (act) rv[u] = __ldg(&R[(int64_t)(base + t) * k + lane]);
+        if (act) rv[u] = __ldg(&R[(int64_t)(base + t) * k + jj]);
       }
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int t = t0 + u;
+    for (int u = 0; u < GU; ++u) {
+      const int t = t0 + u * QN + q;
       if (t < n) {
-        if (own) y[pv[u] * kp + lane] = (T)rv[u];  // lanes k..kp-1 hold zeros
-        if (lane == 0) ip[t] = (uint16_t)pv[u];
+        y[pv[u] * JW + j] = (T)rv[u];  // right-hand sides past k hold zeros
+        if (j == 0) ip[t] = (uint16_t)pv[u];
       }
     }
   }
   __syncwarp();
   const char* rec = ring;
   const char* const ring_end = ring + RING_BYTES;
-  T acc = T(0);
+  const int s0 = q * SPL;
+  T carry = T(0);  // the open segment's sum from the previous window (column j)
   for (int w = 0; w < nw; ++w) {
-    if (F == w + RING_W) asm volatile("cp.async.wait_group %0;\n" ::"n"(RING_W - 1) : "memory");
+    if (F == w + BRING) asm volatile("cp.async.wait_group %0;\n" ::"n"(BRING - 1) : "memory");
     else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncwarp();
     const uint2 d = *(const uint2*)rec;
-    const uint16_t* col = (const uint16_t*)(rec + REC_HDR);
-    const T* coef = (const T*)(rec + REC_COEF);
-    if (own) {
-      // A window holds rows of one level only, so none of its slots reads a
-      // value the window writes: load all 32 first, then sum and store.
-      T yv[WIN];
+    int c[SPL];
+    T a[SPL], yv[SPL];
+    load_cols<SPL>(rec, s0, c);
+    load_coefs<SPL>(rec, s0, a);
 #pragma unroll
-      for (int sl = 0; sl < WIN; ++sl) yv[sl] = y[col[sl] * kp + lane];
+    for (int i = 0; i < SPL; ++i) yv[i] = y[c[i] * JW + j];
+    // this group's slots: segments that start and end here are stored at once
+    T acc = T(0), head = T(0);
+    int hc = -1;
 #pragma unroll
-      for (int sl = 0; sl < WIN; ++sl) {
-        acc = fma(coef[sl], yv[sl], acc);
-        if ((d.x >> sl) & 1u) {  // the slot ends a row's segment (its diagonal)
-          y[col[sl] * kp + lane] = acc;
-          acc = T(0);
+    for (int i = 0; i < SPL; ++i) {
+      acc = fma(a[i], yv[i], acc);
+      if ((d.x >> (s0 + i)) & 1u) {
+        if (hc < 0) {
+          head = acc;  // the group's first segment end: the segment may have begun earlier
+          hc = c[i];
+        } else {
+          y[c[i] * JW + j] = acc;
         }
+        acc = T(0);
       }
     }
-    if (!(d.y & 0x100u)) acc = T(0);  // no segment continues into the next window
+    // inclusive segmented scan over the groups: v = the open sum leaving group q
+    T v = acc;
+    int f = hc >= 0;
+#pragma unroll
+    for (int dd = 1; dd < QN; dd <<= 1) {
+      const T ov = __shfl_up_sync(FULL, v, dd * JW);
+      const int of = __shfl_up_sync(FULL, f, dd * JW);
+      if (q >= dd) {
+        if (!f) v += ov;
+        f |= of;
+      }
+    }
+    T vin = __shfl_up_sync(FULL, v, JW);
+    int fin = __shfl_up_sync(FULL, f, JW);
+    if (q == 0) {
+      vin = T(0);
+      fin = 0;
+    }
+    if (hc >= 0) y[hc * JW + j] = (fin ? vin : vin + carry) + head;
+    const T vl = __shfl_sync(FULL, v, (QN - 1) * JW + j);
+    const int fl = __shfl_sync(FULL, f, (QN - 1) * JW + j);
+    carry = (d.y & 0x100u) ? (fl ? vl : vl + carry) : T(0);
     __syncwarp();
     rec += RB;
     if (rec == ring_end) rec = ring;
@@ -1008,47 +1113,55 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int kp, int ymax, cons
     }
   }
   if (act)
-    for (int t = 0; t < n; ++t) W[(wb + t) * k + lane] = y[ip[t] * kp + lane];
+    for (int t = q; t < n; t += QN) W[(wb + t) * k + jj] = y[ip[t] * JW + j];
 }
 
 int star_batch_max_k(const spnet_pc_s* pc) {
   const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
   int kp = 32;
-  while (kp > 1 && batch_warp_bytes(vb, pc->max_star, kp) > 227 * 1024) kp >>= 1;
+  while (kp > 1 && batch_warp_bytes(vb, pc->max_star, batch_jw(kp)) > 227 * 1024) kp >>= 1;
   return kp;
+}
+
+template <class T, int JW>
+static int star_batch_t(spnet_pc_s* pc, const double* R, int k, int kp, T* W, const int* done, cudaStream_t s) {
+  const size_t smem = (size_t)batch_warp_bytes((int)sizeof(T), pc->max_star, JW);
+  if (smem > 227 * 1024)
+    return fail(SPNET_ERR_UNSUPPORTED, "star solves: the largest star's solve vector for " + std::to_string(k) +
+                                           " right-hand sides exceeds a block's shared memory");
+  static std::atomic<bool> attr_set[64];  // per device
+  int dev = 0;
+  SPNET_CUDA_TRY(cudaGetDevice(&dev));
+  dev &= 63;
+  if (!attr_set[dev]) {
+    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_batch<T, JW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr_set[dev] = true;
+  }
+  const int groups = kp / JW;
+  launch_pdl(k_star_batch<T, JW>, (unsigned)(pc->S * groups), 32, smem, s, k, groups, pc->max_star,
+             (const int32_t*)pc->star_desc, (const StarHdr*)pc->shdr, (const char*)pc->srec,
+             (const uint16_t*)pc->iperm_star, R, W, done);
+  return SPNET_OK;
+}
+
+template <class T>
+static int star_batch_p(spnet_pc_s* pc, const double* R, int k, int kp, T* W, const int* done, cudaStream_t s) {
+  switch (batch_jw(kp)) {
+    case 1: return star_batch_t<T, 1>(pc, R, k, kp, W, done, s);
+    case 2: return star_batch_t<T, 2>(pc, R, k, kp, W, done, s);
+    case 4: return star_batch_t<T, 4>(pc, R, k, kp, W, done, s);
+    default: return star_batch_t<T, 8>(pc, R, k, kp, W, done, s);
+  }
 }
 
 int launch_star_batch(spnet_pc_s* pc, const double* R, int k, void* W, const int* done, cudaStream_t s) {
   if (pc->S == 0) return SPNET_OK;
   if (k < 1 || k > 32) return fail(SPNET_ERR_BAD_INPUT, "star solves: 1..32 right-hand sides at once");
   const int kp = k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
-  const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
-  const size_t smem = (size_t)batch_warp_bytes(vb, pc->max_star, kp);
-  if (smem > 227 * 1024)
-    return fail(SPNET_ERR_UNSUPPORTED, "star solves: the largest star and " + std::to_string(k) +
-                                           " right-hand sides exceed a block's shared memory");
-  static std::atomic<bool> attr_set[64][2];  // per device and precision
-  int dev = 0;
-  SPNET_CUDA_TRY(cudaGetDevice(&dev));
-  dev &= 63;
-  if (!attr_set[dev][vb == 8 ? 1 : 0]) {
-    if (vb == 8)
-      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    else
-      SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr_set[dev][vb == 8 ? 1 : 0] = true;
-  }
   note_launch();
   ProfScope ps(KID_STARS, s);
-  if (vb == 8)
-    launch_pdl(k_star_batch<double>, pc->S, 32, smem, s, k, kp, pc->max_star, (const int32_t*)pc->star_desc,
-               (const StarHdr*)pc->shdr, (const char*)pc->srec, (const uint16_t*)pc->iperm_star, R, (double*)W,
-               done);
-  else
-    launch_pdl(k_star_batch<float>, pc->S, 32, smem, s, k, kp, pc->max_star, (const int32_t*)pc->star_desc,
-               (const StarHdr*)pc->shdr, (const char*)pc->srec, (const uint16_t*)pc->iperm_star, R, (float*)W,
-               done);
-  return SPNET_OK;
+  if (pc->precision == SPNET_PREC_FP64) return star_batch_p<double>(pc, R, k, kp, (double*)W, done, s);
+  return star_batch_p<float>(pc, R, k, kp, (float*)W, done, s);
 }
 
 // headers, inverse permutations and entry streams of all stars
