@@ -108,8 +108,11 @@ __global__ void __launch_bounds__(256) k_bspmm_dir(int64_t n, int k, int kp, con
   }
 }
 
-// one warp per element; mode 0: X += alpha P, R -= alpha Q; mode 1: R as is.
-// Partials of |r_j|^2; corner sums EP[(e, corner, comp)][j] of phi_c r_j.
+// one warp per element, lanes (row r, column j); mode 0: X += alpha P, R -= alpha Q;
+// mode 1: R as is.  Partials of |r_j|^2; corner sums EP[(e, corner, comp)][j] of
+// phi_c r_j.  A lane takes BU of the element's dofs at a time, every load first.
+constexpr int BU = 4;
+
 template <int NC, int ND, class CT>
 __global__ void __launch_bounds__(256) k_bupdate(int n_elem, int64_t N, int k, int kp,
                                                  const int32_t* __restrict__ elem_ptr,
@@ -135,29 +138,47 @@ __global__ void __launch_bounds__(256) k_bupdate(int n_elem, int64_t N, int k, i
     for (int t = 0; t < NC * ND; ++t) acc[t] = CT(0);
     const int a0 = elem_ptr[e], a1 = elem_ptr[e + 1];
     if (act) {
-      for (int i = a0 + r; i < a1; i += rows) {
-        const int64_t o = (int64_t)i * k + j;
-        double v;
-        if (mode == 0) {
-          X[o] = fma(alpha, P[o], X[o]);
-          v = fma(-alpha, Q[o], R[o]);
-          R[o] = v;
-        } else {
-          v = R[o];
+      for (int i0 = a0 + r; i0 < a1; i0 += rows * BU) {
+        bool ok[BU];
+        int ii[BU], cm[BU];
+        double xv[BU], pv[BU], qv[BU], rv[BU];
+        CT t[BU][3];
+#pragma unroll
+        for (int u = 0; u < BU; ++u) {
+          ii[u] = i0 + u * rows;
+          ok[u] = ii[u] < a1;
+          const int i = ok[u] ? ii[u] : a0;
+          const int64_t o = (int64_t)i * k + j;
+          rv[u] = R[o];
+          if (mode == 0) {
+            xv[u] = X[o];
+            pv[u] = P[o];
+            qv[u] = Q[o];
+          }
+#pragma unroll
+          for (int a = 0; a < 3; ++a) t[u][a] = a < D ? __ldg(&xi[(int64_t)a * N + i]) : CT(0);
+          cm[u] = ND == 1 ? 0 : comp_of[i];
         }
-        rr = fma(v, v, rr);
-        CT t[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) t[a] = a < D ? xi[(int64_t)a * N + i] : CT(0);
-        CT w[NC];
-        q1_from_xi<NC>(t, w);
-        const int cm = ND == 1 ? 0 : comp_of[i];
-        const CT vc = (CT)v;
+        for (int u = 0; u < BU; ++u) {
+          if (!ok[u]) continue;
+          const int64_t o = (int64_t)ii[u] * k + j;
+          double v = rv[u];
+          if (mode == 0) {
+            X[o] = fma(alpha, pv[u], xv[u]);
+            v = fma(-alpha, qv[u], v);
+            R[o] = v;
+          }
+          rr = fma(v, v, rr);
+          CT w[NC];
+          q1_from_xi<NC>(t[u], w);
+          const CT vc = (CT)v;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const CT wv = w[c] * vc;
+          for (int c = 0; c < NC; ++c) {
+            const CT wv = w[c] * vc;
 #pragma unroll
-          for (int b2 = 0; b2 < ND; ++b2) acc[c * ND + b2] += b2 == cm ? wv : CT(0);
+            for (int b2 = 0; b2 < ND; ++b2) acc[c * ND + b2] += b2 == cm[u] ? wv : CT(0);
+          }
         }
       }
     }
@@ -211,32 +232,48 @@ __global__ void __launch_bounds__(256) k_bcombine(int n_elem, int64_t N, int k, 
 #pragma unroll
     for (int c = 0; c < NC; ++c) sb[c] = with_stars ? (int)estar[e * NC + c] : -1;
     const int a0 = elem_ptr[e], a1 = elem_ptr[e + 1];
-    for (int i = a0 + r; i < a1; i += rows) {
-      CT t[3];
+    for (int i0 = a0 + r; i0 < a1; i0 += rows * BU) {
+      bool ok[BU];
+      int ii[BU], cm[BU];
+      CT t[BU][3], wv[BU][NC];
+      double rv[BU], zo[BU];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) t[a] = a < D ? xi[(int64_t)a * N + i] : CT(0);
-      CT w[NC];
-      q1_from_xi<NC>(t, w);
-      const int cm = ND == 1 ? 0 : comp_of[i];
-      const int off = i - a0;
-      CT v = CT(0);
+      for (int u = 0; u < BU; ++u) {
+        ii[u] = i0 + u * rows;
+        ok[u] = ii[u] < a1;
+        const int i = ok[u] ? ii[u] : a0;
+        const int off = i - a0;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        CT zv = zcv[c * ND];
+        for (int a = 0; a < 3; ++a) t[u][a] = a < D ? __ldg(&xi[(int64_t)a * N + i]) : CT(0);
+        cm[u] = ND == 1 ? 0 : comp_of[i];
 #pragma unroll
-        for (int b2 = 1; b2 < ND; ++b2) zv = b2 == cm ? zcv[c * ND + b2] : zv;
-        v = fma(w[c], zv, v);
+        for (int c = 0; c < NC; ++c) wv[u][c] = sb[c] >= 0 ? (CT)__ldg(&W[(int64_t)(sb[c] + off) * k + j]) : CT(0);
+        const int64_t o = (int64_t)i * k + j;
+        rv[u] = dots ? __ldg(&R[o]) : 0.0;
+        zo[u] = dots ? Z[o] : 0.0;
       }
 #pragma unroll
-      for (int c = 0; c < NC; ++c)
-        if (sb[c] >= 0) v += (CT)W[(int64_t)(sb[c] + off) * k + j];
-      const int64_t o = (int64_t)i * k + j;
-      const double vd = (double)v;
-      if (dots) {
-        s1 = fma(R[o], vd, s1);
-        s2 = fma(R[o], Z[o], s2);
+      for (int u = 0; u < BU; ++u) {
+        if (!ok[u]) continue;
+        CT w[NC];
+        q1_from_xi<NC>(t[u], w);
+        CT v = CT(0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          CT zv = zcv[c * ND];
+#pragma unroll
+          for (int b2 = 1; b2 < ND; ++b2) zv = b2 == cm[u] ? zcv[c * ND + b2] : zv;
+          v = fma(w[c], zv, v);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v += wv[u][c];
+        const double vd = (double)v;
+        if (dots) {
+          s1 = fma(rv[u], vd, s1);
+          s2 = fma(rv[u], zo[u], s2);
+        }
+        Z[(int64_t)ii[u] * k + j] = vd;
       }
-      Z[o] = vd;
     }
   }
   if (!dots) return;

@@ -1020,7 +1020,7 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int groups, int ymax, 
     es[c] = h->es[c];
   }
   // gather: y[position][j] = R[pc index][jj]; the lanes of a slot group take one local dof
-  constexpr int GU = 4;
+  constexpr int GU = 16;
   for (int t0 = 0; t0 < n; t0 += QN * GU) {
     double rv[GU];
     int pv[GU];
