@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--replicates", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-multi-rhs", action="store_true")
     return ap.parse_args()
 
 
@@ -295,6 +296,37 @@ def run_gb300(args, rank, world, local):
         return dict(n=n, span_ms=span_ms, wall_s=t1 - t0, lat=lat,
                     iters=max(r["iterations"] for _, r in out), relres=max(r["relres"] for _, r in out))
 
+    def multi_rhs(k=32, n_one=8):
+        """k load cases on one network: a block of k right-hand sides stepped together
+        (batch_rhs = k) against n_one of them one at a time, same operator and set-up."""
+        p = probs[0]
+        rng = np.random.default_rng(77)
+        F = torch.from_numpy(rng.uniform(0.0, 1.0, size=(k, p.n_dof))).to(dev)
+        G = torch.from_numpy(np.ascontiguousarray(np.tile(p.dirichlet_vals, (k, 1)))).to(dev)
+        op = spnet.Operator.from_problem(p)
+        out = {}
+        for width, n in ((k, k), (1, n_one)):
+            pc = spnet.Preconditioner(op, p.H, p.gamma_faces, precision=prec, batch_rhs=width)
+            spnet.pcg_solve(op, pc, F[:n], G[:n])  # warm-up: graph capture, kernel attributes
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = spnet.pcg_solve(op, pc, F[:n], G[:n])
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if not all(s.converged for s in st):
+                raise RuntimeError("multi-right-hand-side solve did not converge")
+            out[width] = dict(value=n / dt, iters=[int(min(s.iterations for s in st)),
+                                                   int(max(s.iterations for s in st))],
+                              relres=max(s.relres for s in st))
+            pc.close()
+        op.close()
+        return {"k": k, "value": round(out[k]["value"], 3), "unit": "solves/s",
+                "one_at_a_time": round(out[1]["value"], 3), "iterations": out[k]["iters"],
+                "relres": out[k]["relres"],
+                "note": (f"{k} load cases f ~ U(0,1) on the first network, one pcg_solve with batch_rhs={k} "
+                         f"against {n_one} of them with batch_rhs=1; solve only (operator and set-up "
+                         "excluded), device arrays, host clock around the call")}
+
     if args.mode == "single":  # one request at a time only (the command profiling runs use)
         timed(0, args.warmup)
         times, last = timed(args.steps, 0)
@@ -345,8 +377,9 @@ def run_gb300(args, rank, world, local):
                + p.dirichlet_dofs.size * 8 + p.n_dof * 8 + p.dirichlet_vals.size * 8)
         e2e = {"value": sat["n"] / sat["wall_s"], "unit": "solves/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(p.n_dof * 8)}
+    mrhs = None if args.no_multi_rhs else multi_rhs()
     return dict(sat=sat, pois=pois, fp=fp, times=times, last=last, prof=prof, launches=l1 - l0,
-                clocks=clk, e2e=e2e, desc=desc, prof_steps=len(ptimes), prof_ms=sum(ptimes))
+                clocks=clk, e2e=e2e, desc=desc, prof_steps=len(ptimes), prof_ms=sum(ptimes), mrhs=mrhs)
 
 
 def cpu_oracle_sample(problem, iters_full, sample_iters=3):
@@ -457,6 +490,7 @@ def main():
                        "ms_per_solve": round(fp["span_ms"] / fp["n"], 3), "requests": fp["n"],
                        "iterations": int(fp["iters"]), "relres": fp["relres"],
                        "note": "FP64 factors, coarse inverse and local solves; one request at a time"},
+        "multi_rhs": r.get("mrhs"),
         "single_stream": {"value": round(len(times) / (sum(times) / 1e3), 3), "unit": "solves/s",
                           "ms_per_solve": round(sum(times) / len(times), 3),
                           "note": "mixed, one request at a time, inputs on the device, L2 flushed between"},
