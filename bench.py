@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multi-rhs", action="store_true")
+    ap.add_argument("--stream-requests", type=int, default=128,
+                    help="requests of the serving-stream measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -327,6 +329,64 @@ def run_gb300(args, rank, world, local):
                          f"against {n_one} of them with batch_rhs=1; solve only (operator and set-up "
                          "excluded), device arrays, host clock around the call")}
 
+    def stream_c4(n_req, inflight, n_fp):
+        """The serving stream: n_req requests from the seeded request generator (2D or 3D,
+        500..20000 fibres, about 300 nodes per coarse element, 1..16 right-hand sides, each
+        request's right-hand sides stepped together), all at once and as Poisson arrivals;
+        plain FP64 PCG (one request and one right-hand side at a time) on the first n_fp."""
+        reqs = [nw.request_problem(4000 + i) for i in range(n_req)]
+
+        def run(items, precision, batched, inflight_, rate=None, keep=0):
+            sv = spnet.Server(max_inflight=inflight_)
+            rng = np.random.default_rng(4321)
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(items))) if rate else np.zeros(len(items))
+            t0 = time.perf_counter()
+            tickets = []
+            for k, (p, F) in enumerate(items):
+                while rate and time.perf_counter() - t0 < arrivals[k]:
+                    time.sleep(5e-5)
+                tickets.append(sv.submit(p, f=F, precision=precision, rtol=1e-8,
+                                         batch_rhs=min(16, F.shape[0]) if batched else 1))
+            out = []
+            for k, t in enumerate(tickets):
+                x, res = sv.wait(t)
+                if res["status"] != 0 or res["relres"] > 1e-8:
+                    raise RuntimeError(f"stream request {k} failed: {res}")
+                out.append((x if k < keep else None, res))
+            t1 = time.perf_counter()
+            sv.close()
+            span_ms = max(r["device_end_ms"] for _, r in out) - min(r["device_start_ms"] for _, r in out)
+            return dict(n=len(items), rhs=int(sum(F.shape[0] for _, F in items)), span_ms=span_ms,
+                        wall_s=t1 - t0, lat=np.array([r["latency_ms"] for _, r in out]),
+                        xs=[x for x, _ in out[:keep]], relres=max(r["relres"] for _, r in out))
+
+        run(reqs[:4], prec, True, inflight)  # warm-up
+        sat = run(reqs, prec, True, inflight, keep=n_fp)
+        rate = 0.9 * sat["n"] / (sat["span_ms"] / 1e3)
+        pois = run(reqs, prec, True, inflight, rate=rate)
+        fp = run(reqs[:n_fp], spnet.PREC_FP64, False, 1, keep=n_fp)
+        relerr = max(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+                     for a, b in zip(sat["xs"], fp["xs"]))
+        nodes = [p.net.n_nodes for p, _ in reqs]
+        return {
+            "requests": sat["n"], "rhs": sat["rhs"],
+            "value": round(sat["rhs"] / (sat["span_ms"] / 1e3), 3), "unit": "solves/s (right-hand sides)",
+            "requests_per_s": round(sat["n"] / (sat["span_ms"] / 1e3), 3),
+            "latency_ms": {"p50": round(float(np.percentile(pois["lat"], 50)), 3),
+                           "p99": round(float(np.percentile(pois["lat"], 99)), 3),
+                           "arrivals": f"Poisson at {rate:.1f} requests/s (0.9 of the saturated rate)"},
+            "fp64_plain": {"value": round(fp["rhs"] / (fp["span_ms"] / 1e3), 3), "unit": "solves/s (right-hand sides)",
+                           "requests": fp["n"], "rhs": fp["rhs"],
+                           "note": "the first requests, one at a time, one right-hand side at a time, FP64"},
+            "relres_max": max(sat["relres"], pois["relres"]),
+            "relerr_vs_fp64_max": relerr,
+            "nodes": {"min": int(min(nodes)), "median": int(np.median(nodes)), "max": int(max(nodes))},
+            "inflight": inflight,
+            "note": ("value: right-hand sides over the device span of the saturated pass (all submitted at "
+                     "once); requests from networks.request_problem(4000 + i); latency arrival -> solution "
+                     "in host memory"),
+        }
+
     if args.mode == "single":  # one request at a time only (the command profiling runs use)
         timed(0, args.warmup)
         times, last = timed(args.steps, 0)
@@ -378,8 +438,10 @@ def run_gb300(args, rank, world, local):
         e2e = {"value": sat["n"] / sat["wall_s"], "unit": "solves/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(p.n_dof * 8)}
     mrhs = None if args.no_multi_rhs else multi_rhs()
+    c4 = stream_c4(args.stream_requests, args.inflight, min(8, args.stream_requests)) if args.stream_requests else None
     return dict(sat=sat, pois=pois, fp=fp, times=times, last=last, prof=prof, launches=l1 - l0,
-                clocks=clk, e2e=e2e, desc=desc, prof_steps=len(ptimes), prof_ms=sum(ptimes), mrhs=mrhs)
+                clocks=clk, e2e=e2e, desc=desc, prof_steps=len(ptimes), prof_ms=sum(ptimes), mrhs=mrhs,
+                stream=c4)
 
 
 def cpu_oracle_sample(problem, iters_full, sample_iters=3):
@@ -491,6 +553,7 @@ def main():
                        "iterations": int(fp["iters"]), "relres": fp["relres"],
                        "note": "FP64 factors, coarse inverse and local solves; one request at a time"},
         "multi_rhs": r.get("mrhs"),
+        "stream_c4": r.get("stream"),
         "single_stream": {"value": round(len(times) / (sum(times) / 1e3), 3), "unit": "solves/s",
                           "ms_per_solve": round(sum(times) / len(times), 3),
                           "note": "mixed, one request at a time, inputs on the device, L2 flushed between"},

@@ -70,6 +70,10 @@ int64_t request_estimate(const spnet_request* r) {
   const int corners = 1 << r->dim;
   int64_t b = 48 * nnz + n_dof * (256 + 96 * (int64_t)corners) + 20 * m0 * m0;
   b += (int64_t)r->nrhs * n_dof * 24 + r->n_edges * 48 + (64ll << 20);
+  // right-hand sides stepped together: five block vectors, the star results (about eight
+  // entries per dof) and the coarse product's parts, for the block width
+  const int64_t kb = r->nrhs < r->opts.batch_rhs ? r->nrhs : r->opts.batch_rhs;
+  if (kb >= 2) b += kb * n_dof * (40 + 64) + 2 * m0 * m0 + kb * 16 * m0;
   return b;
 }
 

@@ -89,6 +89,28 @@ def test_several_right_hand_sides_in_one_request():
     assert np.array_equal(x, ref)
 
 
+def test_batched_right_hand_sides_alone_and_in_the_mix():
+    # a request whose right-hand sides are stepped together (batch_rhs) runs the
+    # batched kernels; its result is that of the direct calls, alone and in the mix
+    p = _small3d()
+    rng = np.random.default_rng(6)
+    F = rng.uniform(0.0, 1.0, size=(6, p.n_dof))
+    G = np.broadcast_to(p.dirichlet_vals, (6, len(p.dirichlet_vals)))
+    op = spnet.Operator.from_problem(p)
+    pc = spnet.Preconditioner(op, p.H, p.gamma_faces, precision=spnet.PREC_MIXED, batch_rhs=6)
+    ref, st = spnet.pcg_solve(op, pc, F, G, rtol=1e-8)
+    assert all(s.converged for s in st)
+    sv = spnet.Server(max_inflight=3)
+    tickets = [sv.submit(_small3d(seed=7, n=2500)), sv.submit(p, f=F, batch_rhs=6), sv.submit(_truss()),
+               sv.submit(p, f=F, batch_rhs=6)]
+    out = [sv.wait(t) for t in tickets]
+    sv.close()
+    for x, res in out:
+        assert res["status"] == 0, res["message"]
+    np.testing.assert_array_equal(out[1][0], ref)
+    np.testing.assert_array_equal(out[3][0], ref)
+
+
 def test_a_failing_request_does_not_disturb_the_others():
     good = _small3d()
     bad = _small3d(seed=3)
