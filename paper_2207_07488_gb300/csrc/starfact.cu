@@ -29,8 +29,9 @@ namespace spnet {
 
 constexpr int CAP = 32;          // adjacency slots per node during elimination
 constexpr int SWITCH_DEG = 24;   // minimum degree above which the rest is dense
-constexpr int CORE_MAX = 256;    // largest dense block handled
-constexpr int CORE_ENTRIES = CORE_MAX * (CORE_MAX - 1) / 2;
+constexpr int CORE_FIRST = 256;  // dense block capacity of the first attempt (raised 4x on overflow)
+
+__host__ __device__ inline int64_t core_entries(int core_max) { return (int64_t)core_max * (core_max - 1) / 2; }
 
 // A star's blob: a compact "solve section" (all the triangular solves read)
 // followed by a set-up section.  Values of the solve section are FP64 or FP32
@@ -82,6 +83,7 @@ struct StarArgs {
   int64_t hot;     // hot bytes per warp
   int hot_in_smem; // 1: hot arrays in dynamic shared memory
   int nmax;
+  int core_max;    // largest dense block the scratch holds
   char* pool;
   int64_t pool_cap;
   unsigned long long* pool_top;
@@ -95,7 +97,7 @@ struct StarArgs {
 
 struct Scratch {
   uint16_t* nbr;     // [nmax*CAP]
-  uint16_t* colent;  // [nmax*CAP + CORE_ENTRIES]
+  uint16_t* colent;  // [nmax*CAP + core_entries(core_max)]
   int32_t* deg;      // [nmax]
   int32_t* state;    // [nmax]: -1 alive, else elimination position
   int32_t* posnode;  // [nmax]
@@ -112,14 +114,14 @@ __host__ __device__ inline int64_t hot_bytes(int nmax) {
   return align_up(2ll * nmax * CAP, 16) + align_up(8ll * nmax, 16) + align_up((int64_t)nmax, 16);
 }
 
-__host__ __device__ inline int64_t cold_bytes(int nmax) {
-  int64_t o = 2ll * ((int64_t)nmax * CAP + CORE_ENTRIES);
+__host__ __device__ inline int64_t cold_bytes(int nmax, int core_max) {
+  int64_t o = 2ll * ((int64_t)nmax * CAP + core_entries(core_max));
   o = align_up(o, 8);
   o += 4ll * (nmax + 1) * 6;
   return align_up(o, 256);
 }
 
-__device__ inline Scratch carve(char* cold, char* hot, int nmax) {
+__device__ inline Scratch carve(char* cold, char* hot, int nmax, int core_max) {
   Scratch s;
   int64_t o = 0;
   s.nbr = (uint16_t*)(hot + o);   o = align_up(o + 2ll * nmax * CAP, 16);
@@ -127,7 +129,7 @@ __device__ inline Scratch carve(char* cold, char* hot, int nmax) {
   s.state = (int32_t*)(hot + o);  o = align_up(o + 4ll * nmax, 16);
   s.sel = (uint8_t*)(hot + o);
   o = 0;
-  s.colent = (uint16_t*)(cold + o); o += 2ll * ((int64_t)nmax * CAP + CORE_ENTRIES);
+  s.colent = (uint16_t*)(cold + o); o += 2ll * ((int64_t)nmax * CAP + core_entries(core_max));
   o = align_up(o, 8);
   s.posnode = (int32_t*)(cold + o);  o += 4ll * (nmax + 1);
   s.colstart = (int32_t*)(cold + o); o += 4ll * (nmax + 1);
@@ -220,8 +222,8 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
   const int lane = threadIdx.x & 31;
   const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   char* cold = A.scratch + wg * A.stride;
-  char* hot = A.hot_in_smem ? sm_hot + (threadIdx.x >> 5) * A.hot : cold + cold_bytes(A.nmax);
-  const Scratch W = carve(cold, hot, A.nmax);
+  char* hot = A.hot_in_smem ? sm_hot + (threadIdx.x >> 5) * A.hot : cold + cold_bytes(A.nmax, A.core_max);
+  const Scratch W = carve(cold, hot, A.nmax, A.core_max);
   const unsigned FULL = 0xffffffffu;
   for (;;) {
     int s = 0;
@@ -396,7 +398,7 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
         npos += __popc(b);
       }
       const int c = n - core0;
-      if (c > CORE_MAX || ncol + c * (c - 1) / 2 > A.nmax * CAP + CORE_ENTRIES) {
+      if (c > A.core_max || ncol + core_entries(c) > (int64_t)A.nmax * CAP + core_entries(A.core_max)) {
         if (lane == 0) atomicOr(A.flags, FLAG_STAR_BIG);
         continue;
       }
@@ -1284,20 +1286,14 @@ int pc_factor_stars(spnet_pc_s* pc) {
     ~Guard() { a.free_all(); }
   } guard{tmp};
   const int nmax = pc->max_star;
+  if (nmax > 65535) return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: a star beyond 65535 dofs");
   const int64_t hot = hot_bytes(nmax);
   // hot arrays in shared memory when four warps' worth fit in 200 KiB, one
   // block of four warps per SM at least; otherwise everything in global scratch
   const int hot_in_smem = 4 * hot <= 200 * 1024 ? 1 : 0;
-  const int64_t stride = cold_bytes(nmax) + (hot_in_smem ? 0 : align_up(hot, 256));
   int wpb_blocks = hot_in_smem ? (int)((200 * 1024) / (4 * hot)) : 4;  // blocks per SM
   if (wpb_blocks < 1) wpb_blocks = 1;
   if (wpb_blocks > 4) wpb_blocks = 4;
-  int64_t warps = (int64_t)4 * wpb_blocks * num_sms();
-  int64_t budget = (int64_t)1 << 30;
-  if (warps * stride > budget) warps = budget / stride;
-  if (warps < 4) warps = 4;
-  if (warps > pc->S) warps = pc->S;
-  warps = (warps + 3) / 4 * 4;
   if (hot_in_smem) {
     static std::atomic<bool> attr_set[64];  // per device
     int dev = 0;
@@ -1308,8 +1304,23 @@ int pc_factor_stars(spnet_pc_s* pc) {
       attr_set[dev] = true;
     }
   }
+  // per-warp scratch for a dense block of core_max nodes; warps within a 1 GiB budget
+  int core_max = nmax < CORE_FIRST ? nmax : CORE_FIRST;
+  int64_t stride = 0, warps = 0;
   char* scratch = nullptr;
-  SPNET_TRY(tmp.get(&scratch, warps * stride));
+  auto size_scratch = [&]() -> int {
+    stride = cold_bytes(nmax, core_max) + (hot_in_smem ? 0 : align_up(hot, 256));
+    warps = (int64_t)4 * wpb_blocks * num_sms();
+    const int64_t budget = (int64_t)1 << 30;
+    if (warps * stride > budget) warps = budget / stride;
+    if (warps < 4) warps = 4;
+    if (warps > pc->S) warps = pc->S;
+    warps = (warps + 3) / 4 * 4;
+    if (scratch) tmp.release(scratch);
+    scratch = nullptr;
+    return tmp.get(&scratch, warps * stride);
+  };
+  SPNET_TRY(size_scratch());
   int* counters = nullptr;  // [0] next star, [2..3] pool top (u64)
   SPNET_TRY(tmp.get(&counters, 4));
   SPNET_TRY(pc->mem.get(&pc->star_off, pc->S));
@@ -1318,7 +1329,7 @@ int pc_factor_stars(spnet_pc_s* pc) {
   // pool estimate: per dof 28 bytes + ~4 factor entries of 32 bytes, per star 64
   int64_t cap = pc->sum_s * (28 + 4 * 32) + (int64_t)pc->S * 64 + (1 << 20);
   int* flags = pc->op->dflags;
-  for (int attempt = 0; attempt < 4; ++attempt) {
+  for (int attempt = 0; attempt < 8; ++attempt) {
     if (pc->pool) pc->mem.release(pc->pool);
     pc->pool = nullptr;
     SPNET_TRY(pc->mem.get(&pc->pool, cap));
@@ -1340,6 +1351,7 @@ int pc_factor_stars(spnet_pc_s* pc) {
     A.hot = hot;
     A.hot_in_smem = hot_in_smem;
     A.nmax = nmax;
+    A.core_max = core_max;
     A.pool = pc->pool;
     A.pool_cap = cap;
     A.pool_top = (unsigned long long*)(counters + 2);
@@ -1358,6 +1370,12 @@ int pc_factor_stars(spnet_pc_s* pc) {
     SPNET_CUDA_TRY(cudaStreamSynchronize(s));
     if (h & FLAG_POOL) {
       cap *= 3;
+      continue;
+    }
+    if ((h & FLAG_STAR_BIG) && !(h & ~(FLAG_STAR_BIG | FLAG_POOL)) && core_max < nmax) {
+      // a dense block beyond the scratch: again with four times the capacity
+      core_max = core_max * 4 < nmax ? core_max * 4 : nmax;
+      SPNET_TRY(size_scratch());
       continue;
     }
     if (h) return check_flags(flags, s, "setup_preconditioner (star structure)");
