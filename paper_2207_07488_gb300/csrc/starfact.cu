@@ -522,38 +522,56 @@ __global__ void __launch_bounds__(128) k_star_numeric(int S, char* pool, const i
     double* colv = rowv + nnz;
     double* invd = colv + nnz;
     bool bad = false;
-    for (int l = 0; l < nlev; ++l) {
-      for (int v = lvl[l] + lane; v < (int)lvl[l + 1]; v += 32) {
-        const int gv = gidx[v];
-        double d = k_entry(kptr, kcol, kval, gv, gv);
-        for (uint32_t q = rowptr[v]; q < rowptr[v + 1]; ++q) d -= rowv[q] * rowv[q];
-        if (!(d > 0.0)) {
-          bad = true;
-          d = 1.0;
-        }
-        const double inv = 1.0 / sqrt(d);
-        invd[v] = inv;
-        const uint32_t rv0 = rowptr[v], rv1 = rowptr[v + 1];
-        for (uint32_t q = colptr[v]; q < colptr[v + 1]; ++q) {
-          const int i = colidx[q];
-          double a = k_entry(kptr, kcol, kval, gv, gidx[i]);
-          uint32_t kv = rv0, ki = rowptr[i];
-          const uint32_t ki1 = rowptr[i + 1];
-          while (kv < rv1 && ki < ki1) {
-            const int uv = rowidx[kv], ui = rowidx[ki];
-            if (uv == ui) {
-              a -= rowv[kv] * rowv[ki];
-              ++kv;
-              ++ki;
-            } else if (uv < ui) {
-              ++kv;
-            } else {
-              ++ki;
-            }
+    // L_iv = (K_iv - sum_k L_vk L_ik) / L_vv for the entries of column v: a
+    // merge of the sparse rows v and i (only earlier levels meet there)
+    auto entries = [&](int v, int gv, double inv, uint32_t q0, uint32_t q1, uint32_t dq) {
+      const uint32_t rv0 = rowptr[v], rv1 = rowptr[v + 1];
+      for (uint32_t q = q0; q < q1; q += dq) {
+        const int i = colidx[q];
+        double a = k_entry(kptr, kcol, kval, gv, gidx[i]);
+        uint32_t kv = rv0, ki = rowptr[i];
+        const uint32_t ki1 = rowptr[i + 1];
+        while (kv < rv1 && ki < ki1) {
+          const int uv = rowidx[kv], ui = rowidx[ki];
+          if (uv == ui) {
+            a -= rowv[kv] * rowv[ki];
+            ++kv;
+            ++ki;
+          } else if (uv < ui) {
+            ++kv;
+          } else {
+            ++ki;
           }
-          const double lval = a * inv;
-          colv[q] = lval;
-          rowv[c2r[q]] = lval;
+        }
+        const double lval = a * inv;
+        colv[q] = lval;
+        rowv[c2r[q]] = lval;
+      }
+    };
+    auto pivot = [&](int v, int gv) {
+      double d = k_entry(kptr, kcol, kval, gv, gv);
+      for (uint32_t q = rowptr[v]; q < rowptr[v + 1]; ++q) d -= rowv[q] * rowv[q];
+      if (!(d > 0.0)) {
+        bad = true;
+        d = 1.0;
+      }
+      return 1.0 / sqrt(d);
+    };
+    for (int l = 0; l < nlev; ++l) {
+      const int v0 = lvl[l], v1 = lvl[l + 1];
+      if (v1 - v0 >= 32) {  // a wide level: a column per lane
+        for (int v = v0 + lane; v < v1; v += 32) {
+          const int gv = gidx[v];
+          const double inv = pivot(v, gv);
+          invd[v] = inv;
+          entries(v, gv, inv, colptr[v], colptr[v + 1], 1);
+        }
+      } else {  // a narrow level (the dense block): its columns in turn, their entries across the lanes
+        for (int v = v0; v < v1; ++v) {
+          const int gv = gidx[v];
+          const double inv = pivot(v, gv);  // every lane the same sum
+          if (lane == 0) invd[v] = inv;
+          entries(v, gv, inv, colptr[v] + lane, colptr[v + 1], 32);
         }
       }
       __syncwarp();
