@@ -501,12 +501,16 @@ __device__ inline double k_entry(const int64_t* kptr, const int32_t* kcol, const
   return 0.0;
 }
 
-__global__ void __launch_bounds__(128) k_star_numeric(int S, char* pool, const int64_t* star_off,
-                                                      const int64_t* kptr, const int32_t* kcol,
-                                                      const double* kval, int vbytes, int* flags) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
+// One block per star (NT threads): a wide level gives a column to each thread,
+// a narrow one (the dense block: one node per level) takes its columns in
+// turn with their entries across the threads; a barrier ends each level.
+constexpr int NT = 128;
+
+__global__ void __launch_bounds__(NT) k_star_numeric(int S, char* pool, const int64_t* star_off,
+                                                     const int64_t* kptr, const int32_t* kcol,
+                                                     const double* kval, int vbytes, int* flags) {
+  const int tid = threadIdx.x;
+  for (int64_t s = blockIdx.x; s < S; s += gridDim.x) {
     char* blob = pool + star_off[s];
     const int32_t* hdr = (const int32_t*)blob;
     const int n = hdr[0], nlev = hdr[1], nnz = hdr[2];
@@ -559,28 +563,29 @@ __global__ void __launch_bounds__(128) k_star_numeric(int S, char* pool, const i
     };
     for (int l = 0; l < nlev; ++l) {
       const int v0 = lvl[l], v1 = lvl[l + 1];
-      if (v1 - v0 >= 32) {  // a wide level: a column per lane
-        for (int v = v0 + lane; v < v1; v += 32) {
+      if (v1 - v0 >= NT / 4) {  // a wide level: a column per thread
+        for (int v = v0 + tid; v < v1; v += NT) {
           const int gv = gidx[v];
           const double inv = pivot(v, gv);
           invd[v] = inv;
           entries(v, gv, inv, colptr[v], colptr[v + 1], 1);
         }
-      } else {  // a narrow level (the dense block): its columns in turn, their entries across the lanes
+      } else {  // a narrow level: its columns in turn, their entries across the threads
         for (int v = v0; v < v1; ++v) {
           const int gv = gidx[v];
-          const double inv = pivot(v, gv);  // every lane the same sum
-          if (lane == 0) invd[v] = inv;
-          entries(v, gv, inv, colptr[v] + lane, colptr[v + 1], 32);
+          const double inv = pivot(v, gv);  // every thread the same sum
+          if (tid == 0) invd[v] = inv;
+          entries(v, gv, inv, colptr[v] + tid, colptr[v + 1], NT);
         }
       }
-      __syncwarp();
+      __syncthreads();
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, FLAG_NOT_SPD);
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(flags, FLAG_NOT_SPD);
     if (vbytes == 4) {
       float* r32 = (float*)(blob + L.rowval);
-      for (int q = lane; q < 2 * nnz + n; q += 32) r32[q] = (float)rowv[q];
+      for (int q = tid; q < 2 * nnz + n; q += NT) r32[q] = (float)rowv[q];
     }
+    __syncthreads();
   }
 }
 
@@ -1405,10 +1410,9 @@ int pc_factor_stars(spnet_pc_s* pc) {
     SPNET_CUDA_TRY(cudaStreamSynchronize(s));
     if (h) return check_flags(flags, s, "setup_preconditioner (star pool)");
   }
-  int blocks = (pc->S + 3) / 4;
   note_launch();
   ProfScope ps(KID_STAR_NUMERIC, s);
-  k_star_numeric<<<blocks, 128, 0, s>>>(pc->S, pc->pool, pc->star_off, pc->K.ptr, pc->K.col,
+  k_star_numeric<<<pc->S, NT, 0, s>>>(pc->S, pc->pool, pc->star_off, pc->K.ptr, pc->K.col,
                                          pc->K.val, 8, flags);
   SPNET_CUDA_TRY(cudaGetLastError());
   SPNET_TRY(check_flags(flags, s, "setup_preconditioner (star factorisation)"));
