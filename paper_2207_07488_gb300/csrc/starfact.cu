@@ -1328,7 +1328,9 @@ int pc_factor_stars(spnet_pc_s* pc) {
     }
   }
   // per-warp scratch for a dense block of core_max nodes; warps within a 1 GiB budget
-  int core_max = nmax < CORE_FIRST ? nmax : CORE_FIRST;
+  // (stars beyond 4 CORE_FIRST dofs start at four times the capacity: their
+  // eliminations end in larger blocks and a failed first pass costs a launch)
+  int core_max = nmax <= 4 * CORE_FIRST ? (nmax < CORE_FIRST ? nmax : CORE_FIRST) : 4 * CORE_FIRST;
   int64_t stride = 0, warps = 0;
   char* scratch = nullptr;
   auto size_scratch = [&]() -> int {
