@@ -365,6 +365,7 @@ def run_gb300(args, rank, world, local):
         rate = 0.9 * sat["n"] / (sat["span_ms"] / 1e3)
         pois = run(reqs, prec, True, inflight, rate=rate)
         fp = run(reqs[:n_fp], spnet.PREC_FP64, False, 1, keep=n_fp)
+        same = run(reqs[:n_fp], prec, True, inflight)
         relerr = max(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
                      for a, b in zip(sat["xs"], fp["xs"]))
         nodes = [p.net.n_nodes for p, _ in reqs]
@@ -378,6 +379,9 @@ def run_gb300(args, rank, world, local):
             "fp64_plain": {"value": round(fp["rhs"] / (fp["span_ms"] / 1e3), 3), "unit": "solves/s (right-hand sides)",
                            "requests": fp["n"], "rhs": fp["rhs"],
                            "note": "the first requests, one at a time, one right-hand side at a time, FP64"},
+            "served_same_requests": {"value": round(same["rhs"] / (same["span_ms"] / 1e3), 3),
+                                     "unit": "solves/s (right-hand sides)", "requests": same["n"],
+                                     "note": "the served batched mixed path on the requests of fp64_plain"},
             "relres_max": max(sat["relres"], pois["relres"]),
             "relerr_vs_fp64_max": relerr,
             "nodes": {"min": int(min(nodes)), "median": int(np.median(nodes)), "max": int(max(nodes))},
