@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--inflight", type=int, default=4)
-    ap.add_argument("--mode", default="served", choices=["served", "single"],
+    ap.add_argument("--mode", default="served", choices=["served", "single", "multi_rhs"],
                     help="single: only the one-request-at-a-time measurement (for profiling runs)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
@@ -140,10 +140,33 @@ TRAFFIC_KERNEL = {"stars": "k_star_stream", "spmv": "k_spmv_dir", "update": "k_u
                   "combine": "k_combine", "coarse": "k_coarse_symv"}
 
 
+def kernel_source_sha1(path, name):
+    """sha1 of a kernel's own definition in a source file: from the line that
+    declares `name` as a __global__ function to the brace that closes its body."""
+    import hashlib
+    import re
+    src = open(path).read()
+    m = re.search(r"__global__[^;{]*?\b" + re.escape(name) + r"\s*\(", src)
+    if not m:
+        return None
+    start = src.rfind("\n", 0, m.start()) + 1
+    if src[start:m.start()].strip() == "" and src.rfind("template", 0, start) > src.rfind("\n", 0, start - 1):
+        start = src.rfind("\n", 0, start - 1) + 1  # include a template line just above
+    i = src.index("{", m.end())
+    depth = 0
+    for j in range(i, len(src)):
+        if src[j] == "{":
+            depth += 1
+        elif src[j] == "}":
+            depth -= 1
+            if depth == 0:
+                return hashlib.sha1(src[start:j + 1].encode()).hexdigest()
+    return None
+
+
 def profiled_traffic(kid):
     """DRAM bytes per launch from the committed ncu summary, while the kernel's
-    source file still has the hash recorded with the capture; else None."""
-    import hashlib
+    definition still has the hash recorded with the capture; else None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.md")
     name = TRAFFIC_KERNEL.get(kid)
     if not name or not os.path.exists(path):
@@ -152,7 +175,7 @@ def profiled_traffic(kid):
         parts = [p.strip() for p in line.strip().strip("|").split("|")]
         if len(parts) == 4 and parts[0] == name:
             src = os.path.join(ROOT, parts[2])
-            if os.path.exists(src) and hashlib.sha1(open(src, "rb").read()).hexdigest() == parts[3]:
+            if os.path.exists(src) and kernel_source_sha1(src, name) == parts[3]:
                 return int(parts[1])
     return None
 
@@ -391,6 +414,8 @@ def run_gb300(args, rank, world, local):
                      "in host memory"),
         }
 
+    if args.mode == "multi_rhs":  # the k-right-hand-side measurement only (profiling runs of the batched kernels)
+        return dict(mrhs=multi_rhs())
     if args.mode == "single":  # one request at a time only (the command profiling runs use)
         timed(0, args.warmup)
         times, last = timed(args.steps, 0)
@@ -503,6 +528,10 @@ def main():
         print(json.dumps(line))
         return
     r = run_gb300(args, rank, world, local)
+    if args.mode == "multi_rhs":
+        if rank == 0:
+            print(json.dumps({"mode": "multi_rhs", "workload": WORKLOADS[args.workload][1], "multi_rhs": r["mrhs"]}))
+        return
     sat, pois, fp = r["sat"], r["pois"], r["fp"]
     tot = sat["span_ms"] / 1e3
     if world > 1:
