@@ -501,16 +501,25 @@ __device__ inline double k_entry(const int64_t* kptr, const int32_t* kcol, const
   return 0.0;
 }
 
-// One block per star (NT threads): a wide level gives a column to each thread,
-// a narrow one (the dense block: one node per level) takes its columns in
-// turn with their entries across the threads; a barrier ends each level.
+// A group of TPS threads per star (a warp, four stars to a block; or the whole
+// block of 128 when stars are large): a wide level gives a column to each
+// thread, a narrow one (the dense block: one node per level) takes its columns
+// in turn with their entries across the threads; a barrier ends each level.
 constexpr int NT = 128;
 
+template <int TPS>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (TPS == 32) __syncwarp();
+  else __syncthreads();
+}
+
+template <int TPS>
 __global__ void __launch_bounds__(NT) k_star_numeric(int S, char* pool, const int64_t* star_off,
                                                      const int64_t* kptr, const int32_t* kcol,
                                                      const double* kval, int vbytes, int* flags) {
-  const int tid = threadIdx.x;
-  for (int64_t s = blockIdx.x; s < S; s += gridDim.x) {
+  constexpr int GPB = NT / TPS;  // stars per block at a time
+  const int tid = threadIdx.x % TPS;
+  for (int64_t s = (int64_t)blockIdx.x * GPB + threadIdx.x / TPS; s < S; s += (int64_t)gridDim.x * GPB) {
     char* blob = pool + star_off[s];
     const int32_t* hdr = (const int32_t*)blob;
     const int n = hdr[0], nlev = hdr[1], nnz = hdr[2];
@@ -563,8 +572,8 @@ __global__ void __launch_bounds__(NT) k_star_numeric(int S, char* pool, const in
     };
     for (int l = 0; l < nlev; ++l) {
       const int v0 = lvl[l], v1 = lvl[l + 1];
-      if (v1 - v0 >= NT / 4) {  // a wide level: a column per thread
-        for (int v = v0 + tid; v < v1; v += NT) {
+      if (v1 - v0 >= 32) {  // a wide level: a column per thread
+        for (int v = v0 + tid; v < v1; v += TPS) {
           const int gv = gidx[v];
           const double inv = pivot(v, gv);
           invd[v] = inv;
@@ -575,17 +584,18 @@ __global__ void __launch_bounds__(NT) k_star_numeric(int S, char* pool, const in
           const int gv = gidx[v];
           const double inv = pivot(v, gv);  // every thread the same sum
           if (tid == 0) invd[v] = inv;
-          entries(v, gv, inv, colptr[v] + tid, colptr[v + 1], NT);
+          entries(v, gv, inv, colptr[v] + tid, colptr[v + 1], TPS);
         }
       }
-      __syncthreads();
+      group_sync<TPS>();
     }
-    if (__syncthreads_or(bad) && tid == 0) atomicOr(flags, FLAG_NOT_SPD);
+    const bool any_bad = TPS == 32 ? __any_sync(0xffffffffu, bad) : __syncthreads_or(bad);
+    if (any_bad && tid == 0) atomicOr(flags, FLAG_NOT_SPD);
     if (vbytes == 4) {
       float* r32 = (float*)(blob + L.rowval);
-      for (int q = tid; q < 2 * nnz + n; q += NT) r32[q] = (float)rowv[q];
+      for (int q = tid; q < 2 * nnz + n; q += TPS) r32[q] = (float)rowv[q];
     }
-    __syncthreads();
+    group_sync<TPS>();
   }
 }
 
@@ -1414,8 +1424,13 @@ int pc_factor_stars(spnet_pc_s* pc) {
   }
   note_launch();
   ProfScope ps(KID_STAR_NUMERIC, s);
-  k_star_numeric<<<pc->S, NT, 0, s>>>(pc->S, pc->pool, pc->star_off, pc->K.ptr, pc->K.col,
-                                         pc->K.val, 8, flags);
+  // a warp per star, or a block per star when some star exceeds 1024 dofs
+  if (pc->max_star > 1024)
+    k_star_numeric<NT><<<pc->S, NT, 0, s>>>(pc->S, pc->pool, pc->star_off, pc->K.ptr, pc->K.col, pc->K.val, 8,
+                                            flags);
+  else
+    k_star_numeric<32><<<(pc->S + NT / 32 - 1) / (NT / 32), NT, 0, s>>>(pc->S, pc->pool, pc->star_off, pc->K.ptr,
+                                                                        pc->K.col, pc->K.val, 8, flags);
   SPNET_CUDA_TRY(cudaGetLastError());
   SPNET_TRY(check_flags(flags, s, "setup_preconditioner (star factorisation)"));
   // statistics
