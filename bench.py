@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multi-rhs", action="store_true")
+    ap.add_argument("--no-structural", action="store_true")
     ap.add_argument("--stream-requests", type=int, default=128,
                     help="requests of the serving-stream measurement (0: skip)")
     return ap.parse_args()
@@ -414,6 +415,45 @@ def run_gb300(args, rank, world, local):
                      "in host memory"),
         }
 
+    def structural_c3b():
+        """The structural workload (3 dofs per node) on the 40000-fibre network, H = 1/12: one
+        request at a time, operator + set-up + PCG from host arrays, mixed and plain FP64."""
+        net = nw.fiber_network_3d(40000, 0.1, 0.004, nw.config_seed(3, 0), keep="clamped_x")
+        p = nw.truss_band_problem(net, 1.0 / 12, name="c3b")
+        out = {}
+        for label, pr in (("mixed", spnet.PREC_MIXED), ("fp64", spnet.PREC_FP64)):
+            best = None
+            for _ in range(2):  # the first pass warms up
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                op = spnet.Operator.from_problem(p)
+                pc = spnet.Preconditioner(op, p.H, p.gamma_faces, precision=pr)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                u, st = spnet.pcg_solve(op, pc, p.f, p.dirichlet_vals, rtol=1e-8)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                info = pc.info
+                pc.close()
+                op.close()
+                if not st[0].converged:
+                    raise RuntimeError("structural solve did not converge")
+                best = dict(setup_ms=1e3 * (t1 - t0), pcg_ms=1e3 * (t2 - t1), iters=st[0].iterations,
+                            relres=st[0].relres, u=u)
+            out[label] = best
+        m, f = out["mixed"], out["fp64"]
+        return {"dofs": int(p.n_dof), "stars": int(info.n_stars), "max_star": int(info.max_star),
+                "factor_nnz": int(info.factor_nnz), "m0": int(info.m0),
+                "mixed": {"value": round(1e3 / (m["setup_ms"] + m["pcg_ms"]), 3), "unit": "solves/s",
+                          "setup_ms": round(m["setup_ms"], 1), "pcg_ms": round(m["pcg_ms"], 1),
+                          "iterations": int(m["iters"]), "relres": m["relres"]},
+                "fp64_plain": {"value": round(1e3 / (f["setup_ms"] + f["pcg_ms"]), 3), "unit": "solves/s",
+                               "setup_ms": round(f["setup_ms"], 1), "pcg_ms": round(f["pcg_ms"], 1),
+                               "iterations": int(f["iters"]), "relres": f["relres"]},
+                "relerr_mixed_vs_fp64": float(np.linalg.norm(m["u"] - f["u"]) / np.linalg.norm(f["u"])),
+                "note": ("40000-fibre 3D network, 3 dofs per node, clamped at x < 0.01, u_x = 0.01 at x > 0.99, "
+                         "H = 1/12; one request at a time from host arrays (operator, set-up, PCG), host clock")}
+
     if args.mode == "multi_rhs":  # the k-right-hand-side measurement only (profiling runs of the batched kernels)
         return dict(mrhs=multi_rhs())
     if args.mode == "single":  # one request at a time only (the command profiling runs use)
@@ -467,10 +507,11 @@ def run_gb300(args, rank, world, local):
         e2e = {"value": sat["n"] / sat["wall_s"], "unit": "solves/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(p.n_dof * 8)}
     mrhs = None if args.no_multi_rhs else multi_rhs()
+    c3b = None if args.no_structural else structural_c3b()
     c4 = stream_c4(args.stream_requests, args.inflight, min(8, args.stream_requests)) if args.stream_requests else None
     return dict(sat=sat, pois=pois, fp=fp, times=times, last=last, prof=prof, launches=l1 - l0,
                 clocks=clk, e2e=e2e, desc=desc, prof_steps=len(ptimes), prof_ms=sum(ptimes), mrhs=mrhs,
-                stream=c4)
+                stream=c4, c3b=c3b)
 
 
 def cpu_oracle_sample(problem, iters_full, sample_iters=3):
@@ -587,6 +628,7 @@ def main():
                        "note": "FP64 factors, coarse inverse and local solves; one request at a time"},
         "multi_rhs": r.get("mrhs"),
         "stream_c4": r.get("stream"),
+        "structural_c3b": r.get("c3b"),
         "single_stream": {"value": round(len(times) / (sum(times) / 1e3), 3), "unit": "solves/s",
                           "ms_per_solve": round(sum(times) / len(times), 3),
                           "note": "mixed, one request at a time, inputs on the device, L2 flushed between"},
