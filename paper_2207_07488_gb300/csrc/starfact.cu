@@ -866,8 +866,6 @@ __global__ void __launch_bounds__(256) k_star_stream(int wpb, int ymax, const in
   const char* rec = ring;
   const char* const ring_end = ring + RING_BYTES;
   T carry = T(0);
-  T part = T(0);      // this lane's share of the open segment over windows that end no segment
-  bool pend = false;  // (uniform) part holds something
   for (int k = 0; k < nw; ++k) {
     if (F == k + RING_W) asm volatile("cp.async.wait_group %0;\n" ::"n"(RING_W - 1) : "memory");
     else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -876,35 +874,19 @@ __global__ void __launch_bounds__(256) k_star_stream(int wpb, int ymax, const in
     const int col = ((const uint16_t*)(rec + REC_HDR))[lane];
     const T a = ((const T*)(rec + REC_COEF))[lane];
     const unsigned ends = d.x;
-    if (ends == 0u) {
-      // no segment ends here: all 32 slots belong to one row that continues (a full
-      // window whose carry flag is set), so each lane only adds its product
-      part = fma(a, y[col], part);
-      pend = true;
-    } else {
-      const unsigned steps = d.y & 0xffu;
-      T v = a * y[col];
-      const int dl = lane - (31 - __clz(((ends << 1) | 1u) & le));  // lanes since the segment's first
-      if (steps > 0u) v = scan_step(v, 1, dl);
-      if (steps > 1u) v = scan_step(v, 2, dl);
-      if (steps > 2u) v = scan_step(v, 4, dl);
-      if (steps > 3u) v = scan_step(v, 8, dl);
-      if (steps > 4u) v = scan_step(v, 16, dl);
-      // a segment cut by the previous windows: its partial sums join this window's first segment
-      T cin = carry;
-      if (pend) {  // the lanes' shares, summed in a fixed butterfly order
-        T t = part;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
-        cin += t;
-        part = T(0);
-        pend = false;
-      }
-      if (lane <= dl) v += cin;  // lanes of the first segment (dl == lane there)
-      if ((ends >> lane) & 1u) y[col] = v;
-      carry = T(0);
-      if (d.y & 0x100u) carry = __shfl_sync(FULL, v, 31);
-    }
+    const unsigned steps = d.y & 0xffu;
+    T v = a * y[col];
+    const int dl = lane - (31 - __clz(((ends << 1) | 1u) & le));  // lanes since the segment's first
+    if (steps > 0u) v = scan_step(v, 1, dl);
+    if (steps > 1u) v = scan_step(v, 2, dl);
+    if (steps > 2u) v = scan_step(v, 4, dl);
+    if (steps > 3u) v = scan_step(v, 8, dl);
+    if (steps > 4u) v = scan_step(v, 16, dl);
+    // a segment cut by the previous window: its partial sum joins this window's first segment
+    if (lane <= dl) v += carry;  // lanes of the first segment (dl == lane there)
+    if ((ends >> lane) & 1u) y[col] = v;
+    carry = T(0);
+    if (d.y & 0x100u) carry = __shfl_sync(FULL, v, 31);
     __syncwarp();
     rec += RB;
     if (rec == ring_end) rec = ring;
@@ -1105,9 +1087,7 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int groups, int ymax, 
   const char* rec = ring;
   const char* const ring_end = ring + RING_BYTES;
   const int s0 = q * SPL;
-  T carry = T(0);     // the open segment's sum from the previous window (column j)
-  T part = T(0);      // this lane's share of it over windows that end no segment
-  bool pend = false;  // (uniform) part holds something
+  T carry = T(0);  // the open segment's sum from the previous window (column j)
   for (int w = 0; w < nw; ++w) {
     if (F == w + BRING) asm volatile("cp.async.wait_group %0;\n" ::"n"(BRING - 1) : "memory");
     else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -1119,32 +1099,6 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int groups, int ymax, 
     load_coefs<SPL>(rec, s0, a);
 #pragma unroll
     for (int i = 0; i < SPL; ++i) yv[i] = y[c[i] * JW + j];
-    if (d.x == 0u) {
-      // no segment ends here: every slot belongs to one row that continues
-#pragma unroll
-      for (int i = 0; i < SPL; ++i) part = fma(a[i], yv[i], part);
-      pend = true;
-      __syncwarp();
-      rec += RB;
-      if (rec == ring_end) rec = ring;
-      if (F < nw) {  // refill the slot just consumed
-        if (copier) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        src += RB;
-        dst += RB;
-        if (dst - ring_s - lane * 16 >= RING_BYTES) dst -= RING_BYTES;
-        ++F;
-      }
-      continue;
-    }
-    if (pend) {  // the shares of the column's lanes, summed in a fixed order, join the carry
-      T t = part;
-#pragma unroll
-      for (int o = JW; o < 32; o <<= 1) t += __shfl_xor_sync(FULL, t, o);
-      carry += t;
-      part = T(0);
-      pend = false;
-    }
     // this group's slots: segments that start and end here are stored at once
     T acc = T(0), head = T(0);
     int hc = -1;
