@@ -15,7 +15,6 @@
 // are captured once in a CUDA graph and replayed; the host reads the state
 // only between chunks.
 #include <cmath>
-#include <vector>
 
 #include "spnet_internal.cuh"
 
@@ -252,8 +251,7 @@ __global__ void k_restrict(int n_mesh, Mesh m, int ndof, const double* __restric
 // (r, z_old); last block: beta and, in a PCG step, |r|^2 from the update's
 // partials, the iteration count and the stop test
 template <int NC, int ND, class CT, class WS>
-__global__ void __launch_bounds__(128, ND == 1 ? 7 : 4) k_combine(int n_task, const int2* __restrict__ task,
-                                                 int64_t N, const int32_t* __restrict__ elem_ptr,
+__global__ void __launch_bounds__(128, ND == 1 ? 7 : 4) k_combine(int n_elem, int64_t N, const int32_t* __restrict__ elem_ptr,
                                                  const int8_t* __restrict__ comp_of,
                                                  const CT* __restrict__ xi,
                                                  const int32_t* __restrict__ ecoarse,
@@ -272,9 +270,7 @@ __global__ void __launch_bounds__(128, ND == 1 ? 7 : 4) k_combine(int n_task, co
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double s1 = 0.0, s2 = 0.0;
-  for (int64_t t = gwarp; t < n_task; t += nwarps) {
-    const int2 tk = task[t];  // (element, first dof): at most 32 dofs of one element
-    const int64_t e = tk.x;
+  for (int64_t e = gwarp; e < n_elem; e += nwarps) {
     CT zl = CT(0);
     int sl = -1;  // star bases fit 32 bits (checked at set-up)
     if (lane < NC * ND && with_coarse) {
@@ -287,9 +283,9 @@ __global__ void __launch_bounds__(128, ND == 1 ? 7 : 4) k_combine(int n_task, co
     int sb[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) sb[c] = __shfl_sync(0xffffffffu, sl, c);
-    const int a0 = elem_ptr[e], a1 = min(elem_ptr[e + 1], tk.y + 32);
+    const int a0 = elem_ptr[e], a1 = elem_ptr[e + 1];
     constexpr int U = 1;  // dofs per lane and pass (more would spill under the 64-register bound)
-    for (int i0 = tk.y; i0 < a1; i0 += 32 * U) {
+    for (int i0 = a0; i0 < a1; i0 += 32 * U) {
       // every load (from a valid address) before any use
       int ii[U];
       bool ok[U];
@@ -376,22 +372,6 @@ int pc_elem_tables(spnet_pc_s* pc) {
   k_elem_tables<<<4 * num_sms(), 256, 0, s>>>(pc->n_elem, mesh_of_pc(pc), pc->ndof, pc->cidx, pc->elem_star_off,
                                               pc->star_of_mesh, pc->star_ptr, pc->ecoarse, pc->estar);
   SPNET_CUDA_TRY(cudaGetLastError());
-  // the combine's tasks: each element's dofs in pieces of at most 32 (a warp each),
-  // so that a large element does not set the kernel's length
-  std::vector<int32_t> ep(pc->n_elem + 1);
-  SPNET_CUDA_TRY(cudaMemcpyAsync(ep.data(), pc->elem_ptr, sizeof(int32_t) * (pc->n_elem + 1), cudaMemcpyDeviceToHost, s));
-  SPNET_CUDA_TRY(cudaStreamSynchronize(s));
-  std::vector<int32_t> tasks;
-  for (int e = 0; e < pc->n_elem; ++e)
-    for (int i = ep[e]; i < ep[e + 1]; i += 32) {
-      tasks.push_back(e);
-      tasks.push_back(i);
-    }
-  pc->n_ctask = (int)(tasks.size() / 2);
-  SPNET_TRY(pc->mem.get(&pc->ctask, tasks.size() > 0 ? tasks.size() : 2));
-  if (!tasks.empty())
-    SPNET_CUDA_TRY(cudaMemcpyAsync(pc->ctask, tasks.data(), sizeof(int32_t) * tasks.size(), cudaMemcpyHostToDevice, s));
-  SPNET_CUDA_TRY(cudaStreamSynchronize(s));
   return SPNET_OK;
 }
 
@@ -462,9 +442,8 @@ void launch_restrict(spnet_pc_s* pc, double* rc, const int* done, cudaStream_t s
 template <int NC, int ND, class CT, class WS>
 static void launch_combine_t(spnet_pc_s* pc, const CT* xi, const WS* w, const double* r, double* z,
                              int with_coarse, int with_stars, int dots, cudaStream_t s) {
-  const int need = (pc->n_ctask + 3) / 4;  // a warp per task, four to a block
-  launch_pdl(k_combine<NC, ND, CT, WS>, need < 1 ? 1 : need > pc->PG ? pc->PG : need, 128, 0, s, pc->n_ctask,
-             (const int2*)pc->ctask, pc->N, (const int32_t*)pc->elem_ptr, (const int8_t*)pc->comp_of, xi, (const int32_t*)pc->ecoarse,
+  launch_pdl(k_combine<NC, ND, CT, WS>, elem_grid(pc, 4), 128, 0, s, pc->n_elem, pc->N,
+             (const int32_t*)pc->elem_ptr, (const int8_t*)pc->comp_of, xi, (const int32_t*)pc->ecoarse,
              (const int64_t*)pc->estar, (const double*)pc->zc, w, r, z, pc->partial + 2 * pc->PG,
              pc->partial + 3 * pc->PG, (const double*)(pc->partial + pc->PG), elem_grid(pc, 8),
              (int)(with_coarse && pc->m0 > 0), (int)(with_stars && pc->S > 0), dots ? pc->scal : nullptr,

@@ -168,8 +168,6 @@ struct spnet_pc_s {
   double* epart = nullptr;         // [n_elem*nc*ndof] Q1-weighted corner sums of r
   int32_t* ecoarse = nullptr;      // [n_elem*nc*ndof] coarse index at each corner (-1: none)
   int64_t* estar = nullptr;        // [n_elem*nc] base of the element's entries in w (-1: no star)
-  int32_t* ctask = nullptr;        // [2*n_ctask] combine tasks: (element, first dof), at most 32 dofs each
-  int n_ctask = 0;
   spnet::Scal* scal = nullptr;
   cudaGraphExec_t graph_exec = nullptr;  // a chunk of PCG iterations
   cudaStream_t side = nullptr;     // second stream of the graph (star solves)
