@@ -76,6 +76,22 @@ def parse():
     return ap.parse_args()
 
 
+def combine_over_ranks(n_local, seconds, world):
+    """Whole-job rate of independent replicas: the units all ranks processed over the
+    slowest rank's time (torch.distributed must be initialised when world > 1; NCCL
+    reduces on the GPU, gloo on the host)."""
+    if world <= 1:
+        return n_local / seconds, seconds
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tm = torch.tensor([float(seconds)], dtype=torch.float64, device=dev)
+    tn = torch.tensor([float(n_local)], dtype=torch.float64, device=dev)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tn, op=dist.ReduceOp.SUM)
+    return float(tn.item()) / float(tm.item()), float(tm.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -480,6 +496,9 @@ def run_gb300(args, rank, world, local):
     l1 = spnet.launch_count()
     clk = clocks.stop()
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
     # latency at 0.9 of the saturated throughput (Poisson arrivals)
     rate = 0.9 * sat["n"] / (sat["span_ms"] / 1e3)
     pois = serve(args.steps, args.inflight, prec, rate=rate)
@@ -574,14 +593,7 @@ def main():
             print(json.dumps({"mode": "multi_rhs", "workload": WORKLOADS[args.workload][1], "multi_rhs": r["mrhs"]}))
         return
     sat, pois, fp = r["sat"], r["pois"], r["fp"]
-    tot = sat["span_ms"] / 1e3
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
-    value = world * sat["n"] / tot
+    value, tot = combine_over_ranks(sat["n"], sat["span_ms"] / 1e3, world)
     times = r["times"]
     oi, pi, st, kb = r["last"]
     prof = r["prof"]
