@@ -650,6 +650,7 @@ def main():
                    "sum_star": int(pi.sum_star), "factor_nnz": int(pi.factor_nnz),
                    "max_star": int(pi.max_star), "total_levels": int(pi.total_levels),
                    "max_levels": int(pi.max_levels), "setup_ms_last": round(pi.setup_ms, 3),
+                   "star_warps_per_block": int(pi.star_warps_per_block),
                    "iterations": int(sat["iters"]), "relres": sat["relres"],
                    "l2": "inputs larger than L2: each request holds several hundred MB on the device",
                    "timing": ("CUDA events around each request, one at a time" if single else

@@ -77,7 +77,11 @@ typedef struct {
                         memory), each right-hand side with its own scalars and stop test;
                         the matrix, the star factors and the coarse tiles are read once
                         per block */
-  int reserved[11];
+  int star_map;      /* warps per block of the one-vector star solve: 0 picks it per size
+                        class (stars, largest star, entries per star) by timing the candidates
+                        once per process (default); 1..8 fixes it.  Every warp solves whole
+                        stars, so the choice changes no result */
+  int reserved[10];
 } spnet_options;
 
 typedef struct {
@@ -112,7 +116,8 @@ typedef struct {
   int64_t device_bytes; /* device memory held by the preconditioner */
   int64_t star_stream_bytes; /* bytes one star solve reads from its solve streams
                                 (headers, inverse permutations, entries) */
-  int64_t reserved[4];
+  int64_t star_warps_per_block; /* the star solve's mapping in use (see spnet_options.star_map) */
+  int64_t reserved[3];
 } spnet_pc_info;
 
 /* spnet_assemble -- assemble K on all n_nodes*ndof dofs from an edge list.

@@ -32,6 +32,8 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
     return fail(SPNET_ERR_BAD_INPUT, "setup_preconditioner: unknown star set");
   if (o.batch_rhs < 0 || o.batch_rhs > 32)
     return fail(SPNET_ERR_BAD_INPUT, "setup_preconditioner: batch_rhs must be in 0..32");
+  if (o.star_map < 0 || o.star_map > 8)
+    return fail(SPNET_ERR_BAD_INPUT, "setup_preconditioner: star_map must be in 0..8");
   spnet_pc_s* pc = new spnet_pc_s();
   pc->op = op;
   pc->mem.stream = op->stream;
@@ -40,6 +42,7 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
   pc->flexible = o.flexible < 0 ? (o.precision == SPNET_PREC_MIXED ? 1 : 0) : (o.flexible ? 1 : 0);
   pc->max_restarts = o.max_restarts < 0 ? 0 : o.max_restarts;
   pc->batch_rhs = o.batch_rhs < 1 ? 1 : o.batch_rhs;
+  pc->star_map = o.star_map;
   pc->d = op->dim;
   pc->nc = 1 << op->dim;
   pc->ndof = op->ndof;
@@ -113,6 +116,7 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
       (rc = pc->mem.get(&pc->epart, (size_t)pc->n_elem * pc->nc * pc->ndof)))
     return bail(rc);
   cudaMemsetAsync(pc->scal, 0, sizeof(Scal), s);
+  if ((rc = star_map_tune(pc))) return bail(rc);
   cudaEventRecord(e1, s);
   if (cudaEventSynchronize(e1) != cudaSuccess) return bail(fail(SPNET_ERR_CUDA, "setup_preconditioner: device error"));
   if (cudaGetLastError() != cudaSuccess) return bail(fail(SPNET_ERR_CUDA, "setup_preconditioner: launch error"));
@@ -247,6 +251,7 @@ int spnet_pc_get_info(spnet_pc_t pc, spnet_pc_info* info) {
   info->setup_ms = pc->setup_ms;
   info->device_bytes = pc->mem.bytes;
   info->star_stream_bytes = pc->stream_bytes;
+  info->star_warps_per_block = pc->solve_wpb;
   return SPNET_OK;
 }
 

@@ -112,6 +112,7 @@ struct spnet_pc_s {
   spnet::DevArena mem;
   int precision = SPNET_PREC_MIXED, star_set = SPNET_STARS_INTERIOR, flexible = 1, max_restarts = 2;
   int batch_rhs = 1;            // right-hand sides pcg_solve steps together
+  int star_map = 0;             // warps per block of the star solve: 0 tuned per size class
   int d = 0, ndof = 1, nc = 4;  // nc = 2^d corners
   int gamma[3] = {0, 0, 0};     // Dirichlet face bitmask per component
   int nH[3] = {1, 1, 1};
@@ -160,6 +161,9 @@ struct spnet_pc_s {
   size_t solve_smem = 0;           // its dynamic shared memory per block
   int32_t* sorder = nullptr;       // [solve_blocks*solve_wpb] star of each warp slot, -1: idle
   int32_t* star_desc = nullptr;    // [S] stars by solve cost, largest first
+  std::vector<double> star_cost;   // [S] host: estimated solve cost of each star
+  std::vector<int32_t> star_ord;   // [S] host: stars by cost, largest first
+  int solve_wpb_max = 0;           // most warps per block the shared-memory budget holds
   // work vectors (pc order)
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *b = nullptr;
   double* r2 = nullptr;            // second residual buffer (the iterations alternate)
@@ -284,6 +288,8 @@ int pc_factor_stars(spnet_pc_s* pc);
 int launch_star_batch(spnet_pc_s* pc, const double* R, int k, void* W, const int* done, cudaStream_t s);
 // the largest block width (a power of two <= 32) whose star solve fits a block's shared memory
 int star_batch_max_k(const spnet_pc_s* pc);
+// the star solve's mapping (warps per block): fixed by the options, or tuned per size class
+int star_map_tune(spnet_pc_s* pc);
 // coarse solve for k <= 32 right-hand sides at once: ZC [m0][k] from the corner sums EP [entries][k]
 size_t coarse_batch_part_bytes(const spnet_pc_s* pc, int k);
 int launch_coarse_batch(spnet_pc_s* pc, const double* EP, int k, double* ZC, void* part, const int* done,

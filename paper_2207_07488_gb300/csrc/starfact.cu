@@ -22,6 +22,9 @@
 #include <atomic>
 #include <cmath>
 #include <queue>
+#include <tuple>
+#include <mutex>
+#include <map>
 
 #include "spnet_internal.cuh"
 
@@ -1200,6 +1203,123 @@ int launch_star_batch(spnet_pc_s* pc, const double* R, int k, void* W, const int
   return star_batch_p<float>(pc, R, k, kp, (float*)W, done, s);
 }
 
+// The star solve's mapping for `wpb` warps per block.  The solve is bound by
+// the instruction issue of each SM, so every SM gets the same number k of
+// blocks (a grid of k * SMs blocks; the shared memory of a block is padded so
+// that no SM can hold more than k when they all fit in one wave) and the stars
+// are dealt to the blocks largest first, each to the block with the least work
+// so far.  Work of a star ~ entries / 32 + 2 levels.
+static int build_star_map(spnet_pc_s* pc, int wpb) {
+  cudaStream_t s = pc->op->stream;
+  const int S = pc->S;
+  const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
+  const int64_t wb = stream_warp_bytes(vb, pc->max_star);
+  const int nsm = num_sms();
+  int k = (int)((S + (int64_t)nsm * wpb - 1) / ((int64_t)nsm * wpb));
+  if (k < 1) k = 1;
+  size_t smem = (size_t)(wpb * wb);
+  auto occupancy = [&](size_t bytes, int* nb) -> cudaError_t {
+    return vb == 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_star_stream<double>, wpb * 32, bytes)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_star_stream<float>, wpb * 32, bytes);
+  };
+  int nb = 0;
+  SPNET_CUDA_TRY(occupancy(smem, &nb));
+  if (nb >= k) {
+    while (nb > k && smem + 1024 <= (size_t)STREAM_SMEM) {
+      smem += 1024;
+      SPNET_CUDA_TRY(occupancy(smem, &nb));
+    }
+    if (nb < k) smem -= 1024;  // never fewer than k blocks per SM
+  }
+  const int B = nsm * k;
+  std::vector<int32_t> slot((size_t)B * wpb, -1);
+  std::vector<int> fill(B, 0);
+  std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<std::pair<double, int>>> heap;
+  for (int b = 0; b < B; ++b) heap.push({0.0, b});
+  for (int i : pc->star_ord) {
+    const std::pair<double, int> top = heap.top();
+    heap.pop();
+    const int b = top.second;
+    slot[(size_t)b * wpb + fill[b]++] = i;
+    if (fill[b] < wpb) heap.push({top.first + pc->star_cost[i], b});
+  }
+  if (pc->sorder) {
+    SPNET_CUDA_TRY(cudaStreamSynchronize(s));  // no launch reads the old map any more
+    pc->mem.release(pc->sorder);
+    pc->sorder = nullptr;
+  }
+  SPNET_TRY(pc->mem.get(&pc->sorder, slot.size()));
+  SPNET_CUDA_TRY(cudaMemcpyAsync(pc->sorder, slot.data(), sizeof(int32_t) * slot.size(), cudaMemcpyHostToDevice, s));
+  SPNET_CUDA_TRY(cudaStreamSynchronize(s));  // the host slot table goes out of scope
+  pc->solve_wpb = wpb;
+  pc->solve_blocks = B;
+  pc->solve_smem = smem;
+  return SPNET_OK;
+}
+
+// Size classes of the star solve (half-octaves of the star count, the largest
+// star and the stream bytes per star) and the warps per block timed best for
+// each, once per process and device.
+static std::mutex map_mu;
+static std::map<std::tuple<int, int, int, int, int>, int> map_cache;
+
+static int half_octave(double x) { return x <= 1.0 ? 0 : (int)std::floor(2.0 * std::log2(x)); }
+
+int star_map_tune(spnet_pc_s* pc) {
+  if (pc->S == 0) return SPNET_OK;
+  const int wmax = pc->solve_wpb_max;
+  if (pc->star_map > 0) {
+    const int w = pc->star_map < wmax ? pc->star_map : wmax;
+    if (w != pc->solve_wpb) SPNET_TRY(build_star_map(pc, w));
+    return SPNET_OK;
+  }
+  int dev = 0;
+  SPNET_CUDA_TRY(cudaGetDevice(&dev));
+  const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
+  const auto key = std::make_tuple(dev, vb, half_octave(pc->S), half_octave(pc->max_star),
+                                   half_octave((double)pc->stream_bytes / pc->S));
+  std::lock_guard<std::mutex> lk(map_mu);  // one tuning per class, also under concurrent set-ups
+  auto it = map_cache.find(key);
+  if (it != map_cache.end()) {
+    const int w = it->second < wmax ? it->second : wmax;
+    if (w != pc->solve_wpb) SPNET_TRY(build_star_map(pc, w));
+    return SPNET_OK;
+  }
+  // candidates: the most warps per block the shared memory holds, half and a quarter of it
+  std::vector<int> cand;
+  for (int w = wmax; w >= 1 && (int)cand.size() < 3; w /= 2) cand.push_back(w);
+  cudaStream_t s = pc->op->stream;
+  SPNET_CUDA_TRY(cudaMemsetAsync(pc->vtmp, 0, sizeof(double) * pc->N, s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SPNET_CUDA_TRY(cudaEventCreate(&e0));
+  SPNET_CUDA_TRY(cudaEventCreate(&e1));
+  int best = wmax;
+  float best_ms = 0.0f;
+  int rc = SPNET_OK;
+  for (int w : cand) {
+    if ((rc = build_star_map(pc, w)) != SPNET_OK) break;
+    launch_star_solve(pc, pc->vtmp, nullptr, nullptr, nullptr, s);  // warm-up
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3; ++rep) launch_star_solve(pc, pc->vtmp, nullptr, nullptr, nullptr, s);
+    cudaEventRecord(e1, s);
+    float ms = 0.0f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = fail(SPNET_ERR_CUDA, "setup_preconditioner: timing the star solve failed");
+      break;
+    }
+    if (w == cand.front() || ms < best_ms) {
+      best = w;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SPNET_OK) return rc;
+  map_cache[key] = best;
+  if (best != pc->solve_wpb) SPNET_TRY(build_star_map(pc, best));
+  return SPNET_OK;
+}
+
 // headers, inverse permutations and entry streams of all stars
 static int pack_streams(spnet_pc_s* pc, DevArena& tmp, const std::vector<int32_t>& lev,
                         const std::vector<int32_t>& nz) {
@@ -1249,57 +1369,21 @@ static int pack_streams(spnet_pc_s* pc, DevArena& tmp, const std::vector<int32_t
     SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_stream<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, STREAM_SMEM));
     attr_set[dev][0] = true;
   }
-  // The solve is bound by the instruction issue of each SM, so every SM gets
-  // the same number k of blocks (a grid of k * SMs blocks; the shared memory of
-  // a block is padded so that no SM can hold more than k when they all fit in
-  // one wave) and the stars are dealt to the blocks largest first, each to the
-  // block with the least work so far.  Work of a star ~ entries / 32 + 2 levels.
-  const int nsm = num_sms();
-  int k = (int)((S + (int64_t)nsm * wpb - 1) / ((int64_t)nsm * wpb));
-  if (k < 1) k = 1;
-  size_t smem = (size_t)(wpb * wb);
-  auto occupancy = [&](size_t bytes, int* nb) -> cudaError_t {
-    return vb == 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_star_stream<double>, wpb * 32, bytes)
-                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_star_stream<float>, wpb * 32, bytes);
-  };
-  int nb = 0;
-  SPNET_CUDA_TRY(occupancy(smem, &nb));
-  if (nb >= k) {
-    while (nb > k && smem + 1024 <= (size_t)STREAM_SMEM) {
-      smem += 1024;
-      SPNET_CUDA_TRY(occupancy(smem, &nb));
-    }
-    if (nb < k) smem -= 1024;  // never fewer than k blocks per SM
-  }
-  const int B = nsm * k;
   std::vector<int32_t> sn(S);
   SPNET_CUDA_TRY(cudaMemcpyAsync(sn.data(), pc->star_n, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, s));
   SPNET_CUDA_TRY(cudaStreamSynchronize(s));
-  std::vector<double> cost(S);
-  std::vector<int32_t> ord(S);
+  pc->star_cost.assign(S, 0.0);
+  pc->star_ord.resize(S);
   for (int i = 0; i < S; ++i) {
-    cost[i] = 2.0 * ((double)sn[i] + nz[i]) / 32.0 + 2.0 * lev[i];
-    ord[i] = i;
+    pc->star_cost[i] = 2.0 * ((double)sn[i] + nz[i]) / 32.0 + 2.0 * lev[i];
+    pc->star_ord[i] = i;
   }
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-  std::vector<int32_t> slot((size_t)B * wpb, -1);
-  std::vector<int> fill(B, 0);
-  std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<std::pair<double, int>>> heap;
-  for (int b = 0; b < B; ++b) heap.push({0.0, b});
-  for (int i : ord) {
-    const std::pair<double, int> top = heap.top();
-    heap.pop();
-    const int b = top.second;
-    slot[(size_t)b * wpb + fill[b]++] = i;
-    if (fill[b] < wpb) heap.push({top.first + cost[i], b});
-  }
+  const std::vector<double>& cost = pc->star_cost;
+  std::stable_sort(pc->star_ord.begin(), pc->star_ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   SPNET_TRY(pc->mem.get(&pc->star_desc, S));  // stars by cost, largest first (multi-right-hand-side solves)
-  SPNET_CUDA_TRY(cudaMemcpyAsync(pc->star_desc, ord.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
-  SPNET_TRY(pc->mem.get(&pc->sorder, slot.size()));
-  SPNET_CUDA_TRY(cudaMemcpyAsync(pc->sorder, slot.data(), sizeof(int32_t) * slot.size(), cudaMemcpyHostToDevice, s));
-  pc->solve_wpb = wpb;
-  pc->solve_blocks = B;
-  pc->solve_smem = smem;
+  SPNET_CUDA_TRY(cudaMemcpyAsync(pc->star_desc, pc->star_ord.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
+  pc->solve_wpb_max = wpb;
+  SPNET_TRY(build_star_map(pc, wpb));
   SPNET_CUDA_TRY(cudaStreamSynchronize(s));
   return SPNET_OK;
 }

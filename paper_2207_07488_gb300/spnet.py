@@ -49,7 +49,8 @@ class SpnetError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("star_set", C.c_int), ("flexible", C.c_int),
-                ("max_restarts", C.c_int), ("batch_rhs", C.c_int), ("reserved", C.c_int * 11)]
+                ("max_restarts", C.c_int), ("batch_rhs", C.c_int), ("star_map", C.c_int),
+                ("reserved", C.c_int * 10)]
 
 
 class Request(C.Structure):
@@ -85,7 +86,7 @@ class PcInfo(C.Structure):
                 ("factor_nnz", C.c_int64), ("total_levels", C.c_int64), ("max_levels", C.c_int),
                 ("precision", C.c_int), ("star_set", C.c_int), ("flexible", C.c_int),
                 ("setup_ms", C.c_double), ("device_bytes", C.c_int64), ("star_stream_bytes", C.c_int64),
-                ("reserved", C.c_int64 * 4)]
+                ("star_warps_per_block", C.c_int64), ("reserved", C.c_int64 * 3)]
 
 
 _lib = None
@@ -305,13 +306,14 @@ class Preconditioner:
     """setup_preconditioner: the two-level additive Schwarz preconditioner."""
 
     def __init__(self, op: Operator, H, gamma_faces, precision=PREC_MIXED, star_set=STARS_INTERIOR,
-                 flexible=-1, max_restarts=2, batch_rhs=1):
+                 flexible=-1, max_restarts=2, batch_rhs=1, star_map=0):
         self._lib = op._lib
         self.op = op
         self.handle = C.c_void_p()
         o = Options()
         o.precision, o.star_set, o.flexible, o.max_restarts = precision, star_set, flexible, max_restarts
         o.batch_rhs = batch_rhs
+        o.star_map = star_map
         gf = (C.c_int * 3)(*(list(gamma_faces) + [0, 0, 0])[:3])
         _check(self._lib.setup_preconditioner(op.handle, float(H), gf, C.byref(o),
                                               C.byref(self.handle)))

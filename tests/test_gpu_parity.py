@@ -271,3 +271,22 @@ def test_errors_are_reported():
     with pytest.raises(spnet.SpnetError) as ei:
         spnet.Operator(2, 1, net.coords, rp, col, val, p.dirichlet_dofs[::-1].copy(), net.domain)
     assert ei.value.code == -1
+
+
+def test_star_solve_mapping_changes_no_result():
+    # each warp solves whole stars, so the warps per block of the star solve (fixed, or
+    # picked by timing per size class) changes timing only: the solutions are bitwise equal
+    p = problem("small3d")
+    sols, wpbs = [], []
+    for star_map in (0, 1, 2, 4, 8):
+        op = spnet.Operator.from_problem(p)
+        pc = spnet.Preconditioner(op, p.H, p.gamma_faces, precision=spnet.PREC_MIXED, star_map=star_map)
+        wpbs.append(pc.info.star_warps_per_block)
+        u, st = spnet.pcg_solve(op, pc, p.f, p.dirichlet_vals)
+        assert st[0].converged
+        sols.append(u)
+    assert 1 <= wpbs[0] <= 8 and wpbs[1] == 1 and wpbs[2] == 2
+    for u in sols[1:]:
+        np.testing.assert_array_equal(u, sols[0])
+    with pytest.raises(spnet.SpnetError):
+        spnet.Preconditioner(spnet.Operator.from_problem(p), p.H, p.gamma_faces, star_map=9)
