@@ -1265,19 +1265,27 @@ static std::map<std::tuple<int, int, int, int, int>, int> map_cache;
 
 static int half_octave(double x) { return x <= 1.0 ? 0 : (int)std::floor(2.0 * std::log2(x)); }
 
-int star_map_tune(spnet_pc_s* pc) {
-  if (pc->S == 0) return SPNET_OK;
-  const int wmax = pc->solve_wpb_max;
-  if (pc->star_map > 0) {
-    const int w = pc->star_map < wmax ? pc->star_map : wmax;
-    if (w != pc->solve_wpb) SPNET_TRY(build_star_map(pc, w));
-    return SPNET_OK;
-  }
+static std::tuple<int, int, int, int, int> map_key(const spnet_pc_s* pc) {
   int dev = 0;
-  SPNET_CUDA_TRY(cudaGetDevice(&dev));
+  cudaGetDevice(&dev);
   const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
-  const auto key = std::make_tuple(dev, vb, half_octave(pc->S), half_octave(pc->max_star),
-                                   half_octave((double)pc->stream_bytes / pc->S));
+  return std::make_tuple(dev, vb, half_octave(pc->S), half_octave(pc->max_star),
+                         half_octave((double)pc->stream_bytes / pc->S));
+}
+
+// the mapping to build first: the fixed one, the one cached for the size class, else the widest
+static int initial_wpb(const spnet_pc_s* pc, int wmax) {
+  if (pc->star_map > 0) return pc->star_map < wmax ? pc->star_map : wmax;
+  std::lock_guard<std::mutex> lk(map_mu);
+  auto it = map_cache.find(map_key(pc));
+  if (it == map_cache.end()) return wmax;
+  return it->second < wmax ? it->second : wmax;
+}
+
+int star_map_tune(spnet_pc_s* pc) {
+  if (pc->S == 0 || pc->star_map > 0) return SPNET_OK;  // fixed: built so by pack_streams
+  const int wmax = pc->solve_wpb_max;
+  const auto key = map_key(pc);
   std::lock_guard<std::mutex> lk(map_mu);  // one tuning per class, also under concurrent set-ups
   auto it = map_cache.find(key);
   if (it != map_cache.end()) {
@@ -1383,7 +1391,7 @@ static int pack_streams(spnet_pc_s* pc, DevArena& tmp, const std::vector<int32_t
   SPNET_TRY(pc->mem.get(&pc->star_desc, S));  // stars by cost, largest first (multi-right-hand-side solves)
   SPNET_CUDA_TRY(cudaMemcpyAsync(pc->star_desc, pc->star_ord.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
   pc->solve_wpb_max = wpb;
-  SPNET_TRY(build_star_map(pc, wpb));
+  SPNET_TRY(build_star_map(pc, initial_wpb(pc, wpb)));
   SPNET_CUDA_TRY(cudaStreamSynchronize(s));
   return SPNET_OK;
 }
