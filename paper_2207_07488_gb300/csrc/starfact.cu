@@ -1278,20 +1278,25 @@ static int initial_wpb(const spnet_pc_s* pc, int wmax) {
   if (pc->star_map > 0) return pc->star_map < wmax ? pc->star_map : wmax;
   std::lock_guard<std::mutex> lk(map_mu);
   auto it = map_cache.find(map_key(pc));
-  if (it == map_cache.end()) return wmax;
+  if (it == map_cache.end() || it->second < 1) return wmax;  // unknown, or being tuned
   return it->second < wmax ? it->second : wmax;
 }
 
 int star_map_tune(spnet_pc_s* pc) {
   if (pc->S == 0 || pc->star_map > 0) return SPNET_OK;  // fixed: built so by pack_streams
+  // fewer stars than four per SM: one wave holds them whatever the mapping
+  if (pc->S < 4 * num_sms()) return SPNET_OK;
   const int wmax = pc->solve_wpb_max;
   const auto key = map_key(pc);
-  std::lock_guard<std::mutex> lk(map_mu);  // one tuning per class, also under concurrent set-ups
-  auto it = map_cache.find(key);
-  if (it != map_cache.end()) {
-    const int w = it->second < wmax ? it->second : wmax;
-    if (w != pc->solve_wpb) SPNET_TRY(build_star_map(pc, w));
-    return SPNET_OK;
+  {
+    std::lock_guard<std::mutex> lk(map_mu);
+    auto it = map_cache.find(key);
+    if (it != map_cache.end()) {  // known (or being tuned by another set-up: keep the widest)
+      const int w = it->second < 1 ? pc->solve_wpb : it->second < wmax ? it->second : wmax;
+      if (w != pc->solve_wpb) SPNET_TRY(build_star_map(pc, w));
+      return SPNET_OK;
+    }
+    map_cache[key] = 0;  // this set-up tunes the class; the others do not wait for it
   }
   // candidates: the most warps per block the shared memory holds, half and a quarter of it
   std::vector<int> cand;
@@ -1322,8 +1327,12 @@ int star_map_tune(spnet_pc_s* pc) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(map_mu);
+    if (rc != SPNET_OK) map_cache.erase(key);
+    else map_cache[key] = best;
+  }
   if (rc != SPNET_OK) return rc;
-  map_cache[key] = best;
   if (best != pc->solve_wpb) SPNET_TRY(build_star_map(pc, best));
   return SPNET_OK;
 }
