@@ -1306,8 +1306,11 @@ int star_map_tune(spnet_pc_s* pc) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   SPNET_CUDA_TRY(cudaEventCreate(&e0));
   SPNET_CUDA_TRY(cudaEventCreate(&e1));
+  // In a PCG step the star solve runs beside the update and the coarse product, where many
+  // small blocks crowd those out: a narrower mapping is taken only when the solve is long
+  // (200 us or more, where it sets the step's length) and beats the widest by 5 % alone.
   int best = wmax;
-  float best_ms = 0.0f;
+  float best_ms = 0.0f, wide_ms = 0.0f;
   int rc = SPNET_OK;
   for (int w : cand) {
     if ((rc = build_star_map(pc, w)) != SPNET_OK) break;
@@ -1320,7 +1323,10 @@ int star_map_tune(spnet_pc_s* pc) {
       rc = fail(SPNET_ERR_CUDA, "setup_preconditioner: timing the star solve failed");
       break;
     }
-    if (w == cand.front() || ms < best_ms) {
+    if (w == cand.front()) {
+      wide_ms = best_ms = ms;
+      if (ms / 3.0f < 0.2f) break;  // a short solve: the widest mapping
+    } else if (ms < best_ms && ms < 0.95f * wide_ms) {
       best = w;
       best_ms = ms;
     }
