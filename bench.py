@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--inflight", type=int, default=4)
-    ap.add_argument("--mode", default="served", choices=["served", "single", "multi_rhs"],
+    ap.add_argument("--mode", default="served", choices=["served", "single", "multi_rhs", "c5"],
                     help="single: only the one-request-at-a-time measurement (for profiling runs)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multi-rhs", action="store_true")
     ap.add_argument("--no-structural", action="store_true")
+    ap.add_argument("--c5-fibers", type=int, default=200000,
+                    help="--mode c5: fibres of the large network (the configuration names 400000)")
+    ap.add_argument("--c5-nh", type=int, default=24, help="--mode c5: elements per axis (H = 1/nh)")
     ap.add_argument("--stream-requests", type=int, default=128,
                     help="requests of the serving-stream measurement (0: skip)")
     return ap.parse_args()
@@ -431,6 +434,45 @@ def run_gb300(args, rank, world, local):
                      "in host memory"),
         }
 
+    def large_multi_rhs(n_fibers, nh, k=32, n_one=4):
+        """32 load cases f ~ U(0,1) on one large 3D network (the config-2 generator with
+        n_fibers fibres, H = 1/nh): one batched pcg_solve (mixed, batch_rhs = 32) against
+        n_one of them one at a time, mixed and plain FP64; set-up timed separately."""
+        t0 = time.perf_counter()
+        net = nw.fiber_network_3d(n_fibers, 0.1, 0.004, nw.config_seed(5, 0))
+        p = nw.scalar_band_problem(net, 1.0 / nh, name=f"c5-{n_fibers}fib-H{nh}")
+        gen_s = time.perf_counter() - t0
+        rng = np.random.default_rng(55)
+        F = torch.from_numpy(rng.uniform(0.0, 1.0, size=(k, p.n_dof))).to(dev)
+        G = torch.from_numpy(np.ascontiguousarray(np.tile(p.dirichlet_vals, (k, 1)))).to(dev)
+        op = spnet.Operator.from_problem(p)
+        out = {}
+        for label, pr, width, n in (("batched", spnet.PREC_MIXED, k, k), ("one_at_a_time", spnet.PREC_MIXED, 1, n_one),
+                                    ("fp64_plain", spnet.PREC_FP64, 1, n_one)):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            pc = spnet.Preconditioner(op, p.H, p.gamma_faces, precision=pr, batch_rhs=width)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            _, st = spnet.pcg_solve(op, pc, F[:n], G[:n], rtol=1e-8)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            if not all(x.converged for x in st):
+                raise RuntimeError(f"large network: {label} did not converge")
+            info = pc.info
+            out[label] = {"value": round(n / (t3 - t2), 4), "unit": "solves/s", "rhs": n,
+                          "setup_s": round(t2 - t1, 3), "solve_s": round(t3 - t2, 3),
+                          "iterations": [int(min(x.iterations for x in st)), int(max(x.iterations for x in st))],
+                          "relres": max(x.relres for x in st)}
+            pc.close()
+        op.close()
+        return {"network": {"fibres": n_fibers, "nodes": int(net.n_nodes), "n_dof": int(p.n_dof),
+                            "stars": int(info.n_stars), "max_star": int(info.max_star), "m0": int(info.m0),
+                            "factor_nnz": int(info.factor_nnz), "H": f"1/{nh}", "generation_s": round(gen_s, 1)},
+                **out,
+                "note": (f"{k} load cases f ~ U(0,1), Dirichlet as config 2; host clock around each call, "
+                         "device arrays; solves/s = right-hand sides / solve time (set-up excluded)")}
+
     def structural_c3b():
         """The structural workload (3 dofs per node) on the 40000-fibre network, H = 1/12: one
         request at a time, operator + set-up + PCG from host arrays, mixed and plain FP64."""
@@ -472,6 +514,8 @@ def run_gb300(args, rank, world, local):
 
     if args.mode == "multi_rhs":  # the k-right-hand-side measurement only (profiling runs of the batched kernels)
         return dict(mrhs=multi_rhs())
+    if args.mode == "c5":  # a large network with 32 right-hand sides
+        return dict(c5=large_multi_rhs(args.c5_fibers, args.c5_nh))
     if args.mode == "single":  # one request at a time only (the command profiling runs use)
         timed(0, args.warmup)
         times, last = timed(args.steps, 0)
@@ -588,6 +632,10 @@ def main():
         print(json.dumps(line))
         return
     r = run_gb300(args, rank, world, local)
+    if args.mode == "c5":
+        if rank == 0:
+            print(json.dumps({"mode": "c5", "large_network_32_rhs": r["c5"]}))
+        return
     if args.mode == "multi_rhs":
         if rank == 0:
             print(json.dumps({"mode": "multi_rhs", "workload": WORKLOADS[args.workload][1], "multi_rhs": r["mrhs"]}))
