@@ -650,10 +650,16 @@ struct StarHdr {
 };
 static_assert(sizeof(StarHdr) == 80, "StarHdr layout");
 
-// shared memory of one warp: ring, y, inverse permutation, header
-__host__ __device__ inline int64_t stream_warp_bytes(int vb, int ymax) {
-  return (int64_t)RING_W * rec_bytes(vb) + align_up((int64_t)vb * ymax, 16) + align_up(2ll * ymax, 16) +
-         (int64_t)sizeof(StarHdr);
+// Stars beyond LARGE_STAR dofs are solved by a variant that holds fewer bytes per
+// warp in shared memory (an 8-window ring; the inverse permutation re-read from L2
+// when the results are written), so that more warps stay resident.
+constexpr int LARGE_STAR = 1024;
+constexpr int RING_LARGE = 8;
+
+// shared memory of one warp: ring, y, inverse permutation (not for large stars), header
+__host__ __device__ inline int64_t stream_warp_bytes(int vb, int ymax, bool large = false) {
+  return (int64_t)(large ? RING_LARGE : RING_W) * rec_bytes(vb) + align_up((int64_t)vb * ymax, 16) +
+         (large ? 0 : align_up(2ll * ymax, 16)) + (int64_t)sizeof(StarHdr);
 }
 
 // windows of a level with E entries
@@ -794,7 +800,7 @@ __device__ __forceinline__ T scan_step(T v, int o, int dl) {
 // slot (block, warp) -> star: sorder[blockIdx.x * wpb + warp], -1 for an idle slot.
 // With q set (a PCG step) the right-hand side is the new residual r - alpha q
 // (alpha from the SpMV), formed exactly as the update forms it; otherwise r.
-template <class T>
+template <class T, bool LARGE>
 __global__ void __launch_bounds__(256) k_star_stream(int wpb, int ymax, const int32_t* __restrict__ sorder,
                                                      const StarHdr* __restrict__ hdr, const char* __restrict__ recs,
                                                      const uint16_t* __restrict__ iperm, const double* __restrict__ r,
@@ -810,11 +816,12 @@ __global__ void __launch_bounds__(256) k_star_stream(int wpb, int ymax, const in
   if (s < 0) return;  // no block-wide barrier follows
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int RB = REC_COEF + WIN * (int)sizeof(T);
-  constexpr unsigned RING_BYTES = (unsigned)(RING_W * RB);
-  char* ring = (char*)smem4 + (int64_t)wid * stream_warp_bytes((int)sizeof(T), ymax);
+  constexpr int RW = LARGE ? RING_LARGE : RING_W;  // windows in flight
+  constexpr unsigned RING_BYTES = (unsigned)(RW * RB);
+  char* ring = (char*)smem4 + (int64_t)wid * stream_warp_bytes((int)sizeof(T), ymax, LARGE);
   T* y = (T*)(ring + RING_BYTES);
   uint16_t* ip = (uint16_t*)((char*)y + align_up((int64_t)sizeof(T) * ymax, 16));
-  StarHdr* h = (StarHdr*)((char*)ip + align_up(2ll * ymax, 16));
+  StarHdr* h = (StarHdr*)((char*)ip + (LARGE ? 0 : align_up(2ll * ymax, 16)));
   if (lane < (int)(sizeof(StarHdr) / 4)) ((int32_t*)h)[lane] = __ldg(((const int32_t*)(hdr + s)) + lane);
   __syncwarp();
   const int64_t wb = h->wbase;
@@ -825,7 +832,7 @@ __global__ void __launch_bounds__(256) k_star_stream(int wpb, int ymax, const in
   const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring);
   unsigned dst = ring_s + lane * 16;
   int F = 0;
-  for (; F < nw && F < RING_W; ++F) {
+  for (; F < nw && F < RW; ++F) {
     if (copier) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     src += RB;
@@ -861,7 +868,7 @@ __global__ void __launch_bounds__(256) k_star_stream(int wpb, int ymax, const in
       const int t = t0 + u * 32 + lane;
       if (t < n) {
         y[pv[u]] = (T)rv[u];
-        ip[t] = (uint16_t)pv[u];
+        if (!LARGE) ip[t] = (uint16_t)pv[u];
       }
     }
   }
@@ -870,7 +877,7 @@ __global__ void __launch_bounds__(256) k_star_stream(int wpb, int ymax, const in
   const char* const ring_end = ring + RING_BYTES;
   T carry = T(0);
   for (int k = 0; k < nw; ++k) {
-    if (F == k + RING_W) asm volatile("cp.async.wait_group %0;\n" ::"n"(RING_W - 1) : "memory");
+    if (F == k + RW) asm volatile("cp.async.wait_group %0;\n" ::"n"(RW - 1) : "memory");
     else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncwarp();
     const uint2 d = *(const uint2*)rec;
@@ -902,7 +909,7 @@ __global__ void __launch_bounds__(256) k_star_stream(int wpb, int ymax, const in
       ++F;
     }
   }
-  for (int t = lane; t < n; t += 32) w[wb + t] = y[ip[t]];
+  for (int t = lane; t < n; t += 32) w[wb + t] = y[LARGE ? __ldg(&iperm[wb + t]) : ip[t]];
 }
 
 void launch_star_solve(spnet_pc_s* pc, const double* r, const double* q, const Scal* sc, const int* done,
@@ -912,14 +919,17 @@ void launch_star_solve(spnet_pc_s* pc, const double* r, const double* q, const S
   ProfScope ps(KID_STARS, s);
   const int wpb = pc->solve_wpb;
   const unsigned grid = (unsigned)pc->solve_blocks;
-  if (pc->precision == SPNET_PREC_FP64)
-    k_star_stream<double><<<grid, wpb * 32, pc->solve_smem, s>>>(
-        wpb, pc->max_star, pc->sorder, (const StarHdr*)pc->shdr, pc->srec, pc->iperm_star, r, q, sc,
-        (double*)pc->w, done);
-  else
-    k_star_stream<float><<<grid, wpb * 32, pc->solve_smem, s>>>(
-        wpb, pc->max_star, pc->sorder, (const StarHdr*)pc->shdr, pc->srec, pc->iperm_star, r, q, sc,
-        (float*)pc->w, done);
+  const bool large = pc->max_star > LARGE_STAR;
+  const StarHdr* hdr = (const StarHdr*)pc->shdr;
+  if (pc->precision == SPNET_PREC_FP64) {
+    auto kern = large ? k_star_stream<double, true> : k_star_stream<double, false>;
+    kern<<<grid, wpb * 32, pc->solve_smem, s>>>(wpb, pc->max_star, pc->sorder, hdr, pc->srec, pc->iperm_star, r, q,
+                                                sc, (double*)pc->w, done);
+  } else {
+    auto kern = large ? k_star_stream<float, true> : k_star_stream<float, false>;
+    kern<<<grid, wpb * 32, pc->solve_smem, s>>>(wpb, pc->max_star, pc->sorder, hdr, pc->srec, pc->iperm_star, r, q,
+                                                sc, (float*)pc->w, done);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1213,14 +1223,18 @@ static int build_star_map(spnet_pc_s* pc, int wpb) {
   cudaStream_t s = pc->op->stream;
   const int S = pc->S;
   const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
-  const int64_t wb = stream_warp_bytes(vb, pc->max_star);
+  const bool large = pc->max_star > LARGE_STAR;
+  const int64_t wb = stream_warp_bytes(vb, pc->max_star, large);
   const int nsm = num_sms();
   int k = (int)((S + (int64_t)nsm * wpb - 1) / ((int64_t)nsm * wpb));
   if (k < 1) k = 1;
   size_t smem = (size_t)(wpb * wb);
   auto occupancy = [&](size_t bytes, int* nb) -> cudaError_t {
-    return vb == 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_star_stream<double>, wpb * 32, bytes)
-                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_star_stream<float>, wpb * 32, bytes);
+    if (vb == 8)
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          nb, large ? k_star_stream<double, true> : k_star_stream<double, false>, wpb * 32, bytes);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        nb, large ? k_star_stream<float, true> : k_star_stream<float, false>, wpb * 32, bytes);
   };
   int nb = 0;
   SPNET_CUDA_TRY(occupancy(smem, &nb));
@@ -1376,7 +1390,7 @@ static int pack_streams(spnet_pc_s* pc, DevArena& tmp, const std::vector<int32_t
                                                      pc->iperm_star, pc->srec);
   SPNET_CUDA_TRY(cudaGetLastError());
   // warps per block: as many as the shared-memory budget holds, at most eight
-  const int64_t wb = stream_warp_bytes(vb, pc->max_star);
+  const int64_t wb = stream_warp_bytes(vb, pc->max_star, pc->max_star > LARGE_STAR);
   int wpb = (int)(STREAM_SMEM / wb);
   wpb = wpb > 8 ? 8 : wpb;
   if (wpb < 1) return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: a star too large for the solve's shared memory");
@@ -1385,11 +1399,13 @@ static int pack_streams(spnet_pc_s* pc, DevArena& tmp, const std::vector<int32_t
   SPNET_CUDA_TRY(cudaGetDevice(&dev));
   dev &= 63;
   if (vb == 8 && !attr_set[dev][1]) {
-    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_stream<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, STREAM_SMEM));
+    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_stream<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, STREAM_SMEM));
+    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_stream<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, STREAM_SMEM));
     attr_set[dev][1] = true;
   }
   if (vb == 4 && !attr_set[dev][0]) {
-    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_stream<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, STREAM_SMEM));
+    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_stream<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, STREAM_SMEM));
+    SPNET_CUDA_TRY(cudaFuncSetAttribute(k_star_stream<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, STREAM_SMEM));
     attr_set[dev][0] = true;
   }
   std::vector<int32_t> sn(S);
