@@ -570,7 +570,9 @@ void launch_coarse_apply(spnet_pc_s* pc, const double* rc, double* zc, const int
 // R_0 R with blocks [coarse dof][k].  One block per stored tile stages the
 // tile (rows padded), the restricted right-hand sides of its row block and of
 // its column block in shared memory, and forms Z_IJ R_J (part [I][J]) and, off
-// the diagonal, Z_IJ^T R_I (part [J][I]).  A thread owns UR rows (interleaved
+// the diagonal, Z_IJ^T R_I (part [J][I]).  The restricted right-hand sides R_0 R
+// are formed once per step by k_restrict_batch (each value summed over the corner
+// sums of its mesh node in a fixed order) and read by the tiles as rows.  A thread owns UR rows (interleaved
 // across the lanes: no bank conflicts on the padded tile) times JR
 // right-hand sides and sums each over the tile's 128 columns in order, so a
 // result does not depend on k.  A second kernel sums the parts of each row in
@@ -588,10 +590,31 @@ struct BatchTile {
   static constexpr int ACTIVE = TPG * (KP / JR);                   // threads with work (<= 256)
 };
 
+// RC[ci][j] = (R_0 R)[ci][j] from the element corner sums EP [entries][k]
+template <class T>
+__global__ void __launch_bounds__(256) k_restrict_batch(int64_t m0, int k, const double* __restrict__ EP,
+                                                        const int32_t* __restrict__ rtab, T* __restrict__ RC,
+                                                        const int* done) {
+  pdl_wait();
+  pdl_trigger();
+  if (done && *done) return;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= m0 * k) return;
+  const int64_t ci = q / k;
+  const int j = (int)(q % k);
+  double sum = 0.0;
+#pragma unroll
+  for (int cp = 0; cp < 8; ++cp) {
+    const int off = rtab[8 * ci + cp];
+    if (off >= 0) sum += EP[(int64_t)off * k + j];
+  }
+  RC[q] = (T)sum;
+}
+
 template <class T, int KP>
 __global__ void __launch_bounds__(256) k_coarse_batch(const T* __restrict__ tiles, int nt, int64_t m0, int k,
-                                                      const double* __restrict__ EP, const int32_t* __restrict__ rtab,
-                                                      T* __restrict__ part, const int* done) {
+                                                      const T* __restrict__ RC, T* __restrict__ part,
+                                                      const int* done) {
   using BT = BatchTile<KP>;
   extern __shared__ __align__(16) char sm_cb[];
   T (*Zs)[CT + 1] = reinterpret_cast<T (*)[CT + 1]>(sm_cb);
@@ -604,21 +627,11 @@ __global__ void __launch_bounds__(256) k_coarse_batch(const T* __restrict__ tile
   upper_tile(blockIdx.x, nt, &I, &J);
   const T* Zt = tiles + (int64_t)blockIdx.x * CT * CT;
   for (int q = threadIdx.x; q < CT * CT; q += blockDim.x) Zs[q / CT][q % CT] = Zt[q];
-  // restricted right-hand sides: sum over the corner sums around the coarse dof's mesh node
+  // the restricted right-hand sides of the tile's row and column blocks
   for (int q = threadIdx.x; q < 2 * CT * KP; q += blockDim.x) {
     const int side = q / (CT * KP), u = (q / KP) % CT, j = q % KP;
     const int64_t ci = (int64_t)(side == 0 ? I : J) * CT + u;
-    T v = T(0);
-    if (ci < m0 && j < k) {
-      double sum = 0.0;
-#pragma unroll
-      for (int cp = 0; cp < 8; ++cp) {
-        const int off = rtab[8 * ci + cp];
-        if (off >= 0) sum += EP[(int64_t)off * k + j];
-      }
-      v = (T)sum;
-    }
-    (side == 0 ? sI : sJ)[u * KP + j] = v;
+    (side == 0 ? sI : sJ)[u * KP + j] = (ci < m0 && j < k) ? RC[ci * k + j] : T(0);
   }
   __syncthreads();
   if ((int)threadIdx.x >= BT::ACTIVE) return;  // no barrier follows
@@ -698,11 +711,14 @@ __global__ void __launch_bounds__(256) k_coarse_batch_reduce(int nt, int64_t m0,
   zc[q] = sum;
 }
 
-// bytes of the parts of the k-right-hand-side coarse product
+// bytes of the parts of the k-right-hand-side coarse product, then the restricted block RC [m0][k]
+static size_t parts_only_bytes(const spnet_pc_s* pc, int kp, int vb) {
+  return ((size_t)vb * pc->ctiles_n * pc->ctiles_n * CT * kp + 255) / 256 * 256;
+}
 size_t coarse_batch_part_bytes(const spnet_pc_s* pc, int k) {
   const int kp = k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
   const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
-  return (size_t)vb * pc->ctiles_n * pc->ctiles_n * CT * kp;
+  return parts_only_bytes(pc, kp, vb) + (size_t)vb * pc->m0 * k;
 }
 
 template <class T, int KP>
@@ -719,8 +735,10 @@ static int coarse_batch_t(spnet_pc_s* pc, const double* EP, int k, double* ZC, v
   }
   const unsigned tiles = (unsigned)n_upper_tiles(pc->ctiles_n);
   const unsigned rblocks = (unsigned)((pc->m0 * k + 255) / 256);
-  launch_pdl(k_coarse_batch<T, KP>, tiles, 256, smem, s, (const T*)pc->ctiles, pc->ctiles_n, (int64_t)pc->m0, k, EP,
-             (const int32_t*)pc->rtab, (T*)part, done);
+  T* RC = (T*)((char*)part + parts_only_bytes(pc, KP, (int)sizeof(T)));
+  launch_pdl(k_restrict_batch<T>, rblocks, 256, 0, s, (int64_t)pc->m0, k, EP, (const int32_t*)pc->rtab, RC, done);
+  launch_pdl(k_coarse_batch<T, KP>, tiles, 256, smem, s, (const T*)pc->ctiles, pc->ctiles_n, (int64_t)pc->m0, k,
+             (const T*)RC, (T*)part, done);
   launch_pdl(k_coarse_batch_reduce<T>, rblocks, 256, 0, s, pc->ctiles_n, (int64_t)pc->m0, k, KP, (const T*)part, ZC,
              done);
   return SPNET_OK;
@@ -743,7 +761,8 @@ int launch_coarse_batch(spnet_pc_s* pc, const double* EP, int k, double* ZC, voi
   if (pc->m0 == 0) return SPNET_OK;
   if (k < 1 || k > 32) return fail(SPNET_ERR_BAD_INPUT, "coarse solve: 1..32 right-hand sides at once");
   note_launch();
-  note_launch();  // the product and its row reduction
+  note_launch();
+  note_launch();  // the restriction, the product and its row reduction
   ProfScope ps(KID_COARSE, s);
   if (pc->precision == SPNET_PREC_FP64) return coarse_batch_p<double>(pc, EP, k, ZC, part, done, s);
   return coarse_batch_p<float>(pc, EP, k, ZC, part, done, s);
