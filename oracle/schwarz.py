@@ -10,8 +10,21 @@ with
 
     B r = R_0^T A_0^{-1} R_0 r + sum_j E_j A_j^{-1} E_j^T r.
 
-A node belongs to U(y_j) iff its host element is one of the elements around
-y_j (each element is half-open, so the node lies in exactly one of them).
+Which nodes a star holds (the problem's ``patch``):
+
+* "element": U(y_j) is the union of the half-open elements whose closure
+  contains y_j (Section 2.3), so a node belongs to it iff its host element is
+  one of the elements around y_j.  This is the star of the workloads ("the
+  2^d-element patch around a mesh node"); with stars at interior mesh nodes
+  only it is the reading that still covers the nodes on the Neumann faces.
+* "support": only the nodes where phi_j is nonzero, i.e. those at max-norm
+  distance below H from y_j.  The proof of Lemma 4.1 places its local parts
+  (v - I v) phi_j in V_j, and these vanish wherever phi_j does, so this is the
+  smallest star the stable decomposition needs.  It differs from "element"
+  only at nodes on the outer boundary of the patch, which the paper's grid
+  network (Section 6.2) has in number; with it the grid's rates agree with
+  Table lap_conv.
+
 Every A_j and A_0 is factored densely by Cholesky; the local terms are added
 in ascending star order.
 """
@@ -35,12 +48,23 @@ def star_mesh_nodes(nH, star_set):
     return out
 
 
-def star_dofs(elem, k_multi, nH):
-    """Free dofs whose host element touches mesh node k (the patch U(y_k))."""
+def star_dofs(elem, k_multi, nH, W=None):
+    """Free dofs whose host element touches mesh node k (the patch U(y_k)).
+
+    With the Q1 values W (n, 2^d) given, only the dofs where phi_k is nonzero
+    are kept ("support" patches): phi_k at a dof is W at the corner of the
+    dof's host element that sits at y_k.
+    """
     inside = np.ones(elem.shape[0], dtype=bool)
     for i in range(len(nH)):
         inside &= (elem[:, i] == k_multi[i] - 1) | (elem[:, i] == k_multi[i])
-    return np.nonzero(inside)[0]
+    S = np.nonzero(inside)[0]
+    if W is not None and S.size:
+        corner = np.zeros(S.size, dtype=np.int64)
+        for i in range(len(nH)):
+            corner += (k_multi[i] - elem[S, i]) << i
+        S = S[W[S, corner] != 0.0]
+    return S
 
 
 class SchwarzPreconditioner:
@@ -61,8 +85,10 @@ class SchwarzPreconditioner:
         self.factors = []
         self.local = local
         elem = self.coarse.elem
+        self.patch = getattr(problem, "patch", "element")
+        Wsup = self.coarse.W if self.patch == "support" else None
         for k in star_mesh_nodes(self.nH, star_set):
-            S = star_dofs(elem, mesh_multi(k, self.nH), self.nH)
+            S = star_dofs(elem, mesh_multi(k, self.nH), self.nH, Wsup)
             if S.size == 0:
                 continue
             Aj = self.A[S][:, S]

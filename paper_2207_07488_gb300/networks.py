@@ -31,6 +31,7 @@ from scipy.spatial import cKDTree
 
 FIBER, CONTACT = 0, 1
 STAR_INTERIOR, STAR_ALL = "interior", "all"
+PATCH_ELEMENT, PATCH_SUPPORT = "element", "support"
 
 
 def face_bit(axis: int, side: int) -> int:
@@ -68,7 +69,12 @@ class Problem:
     "scalar" (edge weights ``net.cond``) or "truss3" (3x3 edge blocks built
     from ``net.stiff`` and ``net.dirs``).  ``gamma_faces[c]`` is the bitmask of
     box faces on which component c is Dirichlet (the coarse space drops the
-    mesh nodes lying on them).
+    mesh nodes lying on them).  ``star_set`` picks the mesh nodes that carry a
+    star (the interior ones or all) and ``patch`` the nodes a star holds:
+    "element" (every node whose half-open host element touches the star's mesh
+    node) or "support" (only the nodes where that mesh node's Q1 basis
+    function is nonzero, which leaves out nodes on the outer boundary of the
+    patch).
     """
 
     net: Network
@@ -82,6 +88,7 @@ class Problem:
     star_set: str = STAR_INTERIOR
     name: str = ""
     meta: dict = field(default_factory=dict)
+    patch: str = PATCH_ELEMENT
 
     @property
     def n_dof(self) -> int:
@@ -442,10 +449,12 @@ def truss_band_problem(net: Network, H: float, ux: float = 0.01, star_set=STAR_I
                    H, faces, star_set, name)
 
 
-def grid_heat_problem(k: int, H: float, star_set=STAR_ALL) -> Problem:
+def grid_heat_problem(k: int, H: float, star_set=STAR_ALL, patch=PATCH_SUPPORT) -> Problem:
     """Heat problem of Section 6.2 on the (2^k+1)^2 grid: Gamma = boundary, f = M1.
 
-    (M1)(x) = 1/2 sum_{y~x} |x - y| (eq. 2.1 applied to the constant 1).
+    (M1)(x) = 1/2 sum_{y~x} |x - y| (eq. 2.1 applied to the constant 1).  Stars
+    sit at every mesh node and hold the nodes where the node's basis function
+    is nonzero (the grid's nodes lie on the mesh lines, where this matters).
     """
     net = grid_network_2d(k)
     X = net.coords
@@ -456,7 +465,7 @@ def grid_heat_problem(k: int, H: float, star_set=STAR_ALL) -> Problem:
     np.add.at(f, net.edges[:, 1], 0.5 * lengths)
     allf = X_FACES | face_bit(1, 0) | face_bit(1, 1)
     return Problem(net, 1, "scalar", on_b.astype(np.int64), np.zeros(on_b.size), f, H, (allf,),
-                   star_set, f"grid{k}")
+                   star_set, f"grid{k}", patch=patch)
 
 
 # ----------------------------------------------------------------------------
