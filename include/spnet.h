@@ -62,6 +62,14 @@ extern "C" {
 #define SPNET_STARS_INTERIOR 0  /* stars at mesh nodes off the boundary of Omega */
 #define SPNET_STARS_ALL 1       /* stars at every mesh node y_1..y_m (Section 4.1) */
 
+/* Which free dofs the star of mesh node y_j holds (Sections 2.3, 4.1). */
+#define SPNET_PATCH_ELEMENT 0  /* every dof whose half-open host element touches y_j: the
+                                  union of the (up to 2^d) elements around y_j */
+#define SPNET_PATCH_SUPPORT 1  /* only the dofs where the Q1 basis function of y_j is nonzero
+                                  (max-norm distance below H): the space the local parts
+                                  (v - I v) phi_j of the proof of Lemma 4.1 live in.  Differs
+                                  from ELEMENT only at dofs on the outer boundary of the patch */
+
 typedef struct spnet_op_s* spnet_op_t;
 typedef struct spnet_pc_s* spnet_pc_t;
 
@@ -81,7 +89,8 @@ typedef struct {
                         class (stars, largest star, entries per star) by timing the candidates
                         once per process (default); 1..8 fixes it.  Every warp solves whole
                         stars, so the choice changes no result */
-  int reserved[10];
+  int patch;         /* SPNET_PATCH_* (default SPNET_PATCH_ELEMENT) */
+  int reserved[9];
 } spnet_options;
 
 typedef struct {
@@ -310,23 +319,26 @@ int spnet_pc_export(spnet_pc_t pc, int what, void* host_buf, size_t bytes);
 /* spnet_pc_restrict_static -- r_c = R_0 r, exactly as spnet_pc_restrict, but the
  * call allocates no memory at all.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory at the time of
- * the call -- code running inside CUDA stream capture (where cudaMalloc is not
- * permitted), hosts that reserve all device memory up front, or real-time
- * loops that must not enter the allocator.
+ * the call -- hosts whose device memory is all reserved up front by another
+ * allocator (a framework's caching pool that has taken the whole GPU), and
+ * latency-bound loops that must not enter cudaMalloc, which can synchronise
+ * the device and take an unbounded time.
  *
  * r (device, free order, n_free doubles) and rc (device, coarse order, m0
- * doubles) are the caller's.  The scratch -- the Q1-weighted sums of r at the
- * 2^d corners of every element, n_elem * 2^d * ndof doubles -- lives in one
- * fixed array of 2^18 doubles (2 MiB) inside the library, which every GPU that
- * loads the library holds until the process exits.  Meshes that need more
- * corner sums are rejected with SPNET_ERR_UNSUPPORTED.  The first call on a
- * device looks the array's device address up (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
- * share the one array: calls whose work overlaps on the GPU (other threads,
- * other streams, several preconditioners) race and must be serialised by the
- * caller.  Every entry of the array that a call reads is written earlier in
- * the same call, so nothing has to be cleared between calls.  Runs on the
- * operator's stream and returns when rc is complete. */
+ * doubles) are the caller's, on the preconditioner's device, which must be
+ * the current device (else SPNET_ERR_BAD_INPUT).  The scratch -- the
+ * Q1-weighted sums of r at the 2^d corners of every element, n_elem * 2^d *
+ * ndof doubles -- lives in one fixed array of 2^18 doubles (2 MiB) inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  Meshes that need more corner sums are rejected with
+ * SPNET_ERR_UNSUPPORTED.  The first call on a device looks the array's device
+ * address up (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents: calls whose work overlaps on the GPU (other
+ * threads, other streams, several preconditioners) race and must be
+ * serialised by the caller.  Every entry of the array that a call reads is
+ * written earlier in the same call, so nothing has to be cleared between
+ * calls.  Runs on the operator's stream and returns when rc is complete. */
 int spnet_pc_restrict_static(spnet_pc_t pc, const double* r, double* rc);
 
 /* Instrumentation (process-wide; not part of the paper's method).

@@ -34,6 +34,8 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
     return fail(SPNET_ERR_BAD_INPUT, "setup_preconditioner: batch_rhs must be in 0..32");
   if (o.star_map < 0 || o.star_map > 8)
     return fail(SPNET_ERR_BAD_INPUT, "setup_preconditioner: star_map must be in 0..8");
+  if (o.patch != SPNET_PATCH_ELEMENT && o.patch != SPNET_PATCH_SUPPORT)
+    return fail(SPNET_ERR_BAD_INPUT, "setup_preconditioner: unknown patch rule");
   spnet_pc_s* pc = new spnet_pc_s();
   pc->op = op;
   pc->mem.stream = op->stream;
@@ -43,6 +45,7 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
   pc->max_restarts = o.max_restarts < 0 ? 0 : o.max_restarts;
   pc->batch_rhs = o.batch_rhs < 1 ? 1 : o.batch_rhs;
   pc->star_map = o.star_map;
+  pc->patch = o.patch;
   pc->d = op->dim;
   pc->nc = 1 << op->dim;
   pc->ndof = op->ndof;

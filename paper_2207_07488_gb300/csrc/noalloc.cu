@@ -3,7 +3,10 @@
 // The restriction needs scratch for the Q1-weighted corner sums of r on every
 // element.  spnet_pc_restrict takes that scratch from the preconditioner's own
 // device memory; spnet_pc_restrict_static takes it from a fixed array that is
-// part of the library image, so the call itself never allocates.
+// part of the library image, so the call itself never allocates: it serves
+// callers whose device memory is all reserved up front by another allocator,
+// and loops that must not enter cudaMalloc (which can synchronise the device
+// and take an unbounded time).
 #include <mutex>
 
 #include "spnet_internal.cuh"
@@ -16,12 +19,19 @@ constexpr int64_t STATIC_CORNER_SUMS = int64_t(1) << 18;
 static __device__ __align__(256) double g_corner_sums[STATIC_CORNER_SUMS];
 
 // device address of the array, looked up once per device with that device current
+// (in host code the name g_corner_sums is a host-side stand-in, not a device address)
 static double* g_corner_sums_addr[64] = {};
 static std::mutex g_corner_sums_mu;
 
-static int corner_sums_address(double** out) {
-  int dev = 0;
-  SPNET_CUDA_TRY(cudaGetDevice(&dev));
+// `dev` is the preconditioner's device; it must be the current one, since the
+// symbol lookup and the launches act on the current device
+static int corner_sums_address(int dev, double** out) {
+  int cur = 0;
+  SPNET_CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != dev)
+    return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_restrict_static: the preconditioner's device (" +
+                                         std::to_string(dev) + ") is not the current device (" +
+                                         std::to_string(cur) + ")");
   if (dev < 0 || dev >= 64) return fail(SPNET_ERR_UNSUPPORTED, "spnet_pc_restrict_static: device id >= 64");
   std::lock_guard<std::mutex> lk(g_corner_sums_mu);
   if (!g_corner_sums_addr[dev]) {
@@ -105,7 +115,7 @@ extern "C" int spnet_pc_restrict_static(spnet_pc_t pc, const double* r, double* 
                     " corner sums, more than the static scratch of " + std::to_string(STATIC_CORNER_SUMS) +
                     " (n_elem * 2^d * ndof)");
   double* sums = nullptr;
-  SPNET_TRY(corner_sums_address(&sums));
+  SPNET_TRY(corner_sums_address(pc->op->device, &sums));
   if (pc->m0 == 0) return SPNET_OK;
   cudaStream_t s = pc->op->stream;
   const Mesh m = mesh_of_pc(pc);

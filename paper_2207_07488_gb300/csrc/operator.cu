@@ -306,7 +306,10 @@ int build_operator(int dim, int ndof, int64_t n_nodes, const double* coords, con
     return fail(SPNET_ERR_UNSUPPORTED, "build_network_operator: more than 2^31 dofs");
   for (int a = 0; a < dim; ++a)
     if (!(domain_hi[a] > 0.0)) return fail(SPNET_ERR_BAD_INPUT, "build_network_operator: domain side <= 0");
+  int dev = 0;
+  SPNET_CUDA_TRY(cudaGetDevice(&dev));
   spnet_op_s* op = new spnet_op_s();
+  op->device = dev;
   if (s == 0) {
     // the legacy default stream cannot be captured into CUDA graphs: work on a
     // private stream instead (every call synchronises it before returning)

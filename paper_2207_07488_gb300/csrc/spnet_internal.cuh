@@ -95,6 +95,7 @@ struct spnet_op_s {
   int64_t n_nodes = 0, n_dof = 0, n_free = 0, n_dir = 0;
   double domain[3] = {1, 1, 1};
   cudaStream_t stream = 0;
+  int device = 0;               // CUDA device current when the operator was built
   bool own_stream = false;      // created by the library (the caller passed stream 0)
   spnet::DevArena mem;
   double* coords = nullptr;     // [n_nodes*dim]
@@ -113,6 +114,7 @@ struct spnet_pc_s {
   int precision = SPNET_PREC_MIXED, star_set = SPNET_STARS_INTERIOR, flexible = 1, max_restarts = 2;
   int batch_rhs = 1;            // right-hand sides pcg_solve steps together
   int star_map = 0;             // warps per block of the star solve: 0 tuned per size class
+  int patch = SPNET_PATCH_ELEMENT;  // dofs a star holds (SPNET_PATCH_*)
   int d = 0, ndof = 1, nc = 4;  // nc = 2^d corners
   int gamma[3] = {0, 0, 0};     // Dirichlet face bitmask per component
   int nH[3] = {1, 1, 1};

@@ -96,6 +96,9 @@ struct StarArgs {
   int* flags;
   int* next;
   int vbytes;
+  int patch;          // SPNET_PATCH_*
+  const double* q1w;  // [nc][N] Q1 values (the support rule tests them against zero)
+  int64_t N;
 };
 
 struct Scratch {
@@ -187,6 +190,17 @@ __device__ inline int local_of_pc(const Mesh& m, const StarElems& se, const int3
   return se.off[cp] + (j - elem_ptr[e]);
 }
 
+// "support" patches: local dof t lies outside the open support of the star's basis
+// function (its Q1 value there is zero).  The star's mesh node sits at corner
+// nc - 1 - c' of the element in slot c'.
+__device__ inline bool off_support(const StarElems& se, const int32_t* elem_ptr, const double* q1w,
+                                   int64_t N, int t) {
+  int cp = 0;
+  while (cp + 1 < se.nc && se.off[cp + 1] <= t) ++cp;
+  const int i = elem_ptr[se.e[cp]] + (t - se.off[cp]);
+  return q1w[(int64_t)(se.nc - 1 - cp) * N + i] == 0.0;
+}
+
 __device__ inline int warp_min(int v) {
   for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
@@ -242,16 +256,20 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
     const StarElems se = star_elems(A.m, k, A.elem_ptr);
     int km[3];
     mesh_multi(A.m, k, km);
-    // adjacency of the star graph
+    // adjacency of the star graph (with support patches a dof off the support is an
+    // isolated node: its row of the local matrix is the identity, and its solve
+    // coefficient is zero, so the star adds nothing there)
     bool ovf = false;
     for (int t = lane; t < n; t += 32) {
       int i = pc_of_local(se, A.elem_ptr, t);
       int cnt = 0;
-      for (int64_t q = A.kptr[i]; q < A.kptr[i + 1]; ++q) {
+      const bool tex = A.patch == SPNET_PATCH_SUPPORT && off_support(se, A.elem_ptr, A.q1w, A.N, t);
+      for (int64_t q = tex ? A.kptr[i + 1] : A.kptr[i]; q < A.kptr[i + 1]; ++q) {
         int j = A.kcol[q];
         if (j == i) continue;
         int lt = local_of_pc(A.m, se, A.elem_ptr, A.elem_of, km[0], km[1], km[2], j);
         if (lt < 0) continue;
+        if (A.patch == SPNET_PATCH_SUPPORT && off_support(se, A.elem_ptr, A.q1w, A.N, lt)) continue;
         if (cnt < CAP) W.nbr[(int64_t)t * CAP + cnt++] = (uint16_t)lt;
         else ovf = true;
       }
@@ -699,15 +717,31 @@ __device__ inline int window_steps(unsigned ends, int cnt) {
   return steps;
 }
 
+// which elimination positions of a star lie off its basis function's support
+struct SupportTest {
+  int patch;
+  StarElems se;
+  const int32_t* elem_ptr;
+  const double* q1w;
+  int64_t N;
+  const uint16_t* perm;  // elimination position -> local index
+  __device__ bool off(int v) const {
+    return patch == SPNET_PATCH_SUPPORT && off_support(se, elem_ptr, q1w, N, perm[v]);
+  }
+};
+
 // the windows of one level: entries of the rows of the level in order, the
 // descriptor of every window (ends, steps, carry flag)
 template <class T>
 __device__ void pack_level(char* recs, int64_t wb, int lane, int v0, int v1, const uint32_t* ptr,
-                           const uint16_t* idx, const double* val, const double* invd, int vb) {
+                           const uint16_t* idx, const double* val, const double* invd, int vb,
+                           const SupportTest& sup) {
   const int RB = rec_bytes(vb);
   const int64_t E = (int64_t)(ptr[v1] - ptr[v0]) + (v1 - v0);
   for (int v = v0 + lane; v < v1; v += 32) {
-    const double dv = invd[v];
+    // a dof off the star's support (support patches) is an isolated row: a zero
+    // coefficient makes its value, and the star's contribution there, zero
+    const double dv = sup.off(v) ? 0.0 : invd[v];
     int64_t j = (int64_t)(ptr[v] - ptr[v0]) + (v - v0);
     for (uint32_t q = ptr[v]; q <= ptr[v + 1]; ++q, ++j) {
       const bool diag = q == ptr[v + 1];
@@ -737,7 +771,8 @@ template <class T>
 __global__ void k_stream_pack(int S, Mesh m, const char* __restrict__ pool, const int64_t* __restrict__ star_off,
                               const int32_t* __restrict__ star_mesh, const int32_t* __restrict__ elem_ptr,
                               const int64_t* __restrict__ star_ptr, const int64_t* __restrict__ roff,
-                              StarHdr* __restrict__ hdr, uint16_t* __restrict__ iperm, char* __restrict__ recs) {
+                              StarHdr* __restrict__ hdr, uint16_t* __restrict__ iperm, char* __restrict__ recs,
+                              int patch, const double* __restrict__ q1w, int64_t N) {
   const int lane = threadIdx.x & 31;
   const int vb = (int)sizeof(T);
   const int RB = rec_bytes(vb);
@@ -776,13 +811,20 @@ __global__ void k_stream_pack(int S, Mesh m, const char* __restrict__ pool, cons
     for (int64_t q = lane; q < n16; q += 32) z4[q] = make_int4(0, 0, 0, 0);
     __syncwarp();
     __threadfence_block();
+    SupportTest sup;
+    sup.patch = patch;
+    sup.se = star_elems(m, star_mesh[s], elem_ptr);
+    sup.elem_ptr = elem_ptr;
+    sup.q1w = q1w;
+    sup.N = N;
+    sup.perm = perm;
     int64_t w = r0;
     for (int l = 0; l < nlev; ++l) {  // forward levels
-      pack_level<T>(recs, w, lane, lvl[l], lvl[l + 1], rowptr, rowidx, rowv, invd, vb);
+      pack_level<T>(recs, w, lane, lvl[l], lvl[l + 1], rowptr, rowidx, rowv, invd, vb, sup);
       w += level_windows(level_entries(rowptr, lvl, l));
     }
     for (int l = nlev - 1; l >= 0; --l) {  // backward levels, last first
-      pack_level<T>(recs, w, lane, lvl[l], lvl[l + 1], colptr, colidx, colv, invd, vb);
+      pack_level<T>(recs, w, lane, lvl[l], lvl[l + 1], colptr, colidx, colv, invd, vb, sup);
       w += level_windows(level_entries(colptr, lvl, l));
     }
   }
@@ -1383,11 +1425,11 @@ static int pack_streams(spnet_pc_s* pc, DevArena& tmp, const std::vector<int32_t
   if (vb == 8)
     k_stream_pack<double><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_mesh,
                                                       pc->elem_ptr, pc->star_ptr, roff, (StarHdr*)pc->shdr,
-                                                      pc->iperm_star, pc->srec);
+                                                      pc->iperm_star, pc->srec, pc->patch, pc->q1w, pc->N);
   else
     k_stream_pack<float><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_mesh,
                                                      pc->elem_ptr, pc->star_ptr, roff, (StarHdr*)pc->shdr,
-                                                     pc->iperm_star, pc->srec);
+                                                     pc->iperm_star, pc->srec, pc->patch, pc->q1w, pc->N);
   SPNET_CUDA_TRY(cudaGetLastError());
   // warps per block: as many as the shared-memory budget holds, at most eight
   const int64_t wb = stream_warp_bytes(vb, pc->max_star, pc->max_star > LARGE_STAR);
@@ -1519,6 +1561,9 @@ int pc_factor_stars(spnet_pc_s* pc) {
     A.flags = flags;
     A.next = counters;
     A.vbytes = 8;  // the set-up blobs keep FP64 values; the solve sections are packed later
+    A.patch = pc->patch;
+    A.q1w = pc->q1w;
+    A.N = pc->N;
     note_launch();
     ProfScope ps(KID_STAR_SYMBOLIC, s);
     k_star_symbolic<<<(unsigned)(warps / 4), 128, hot_in_smem ? (size_t)(4 * hot) : 0, s>>>(A);

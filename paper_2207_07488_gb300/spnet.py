@@ -25,6 +25,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 MODEL_SCALAR, MODEL_TRUSS3 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 STARS_INTERIOR, STARS_ALL = 0, 1
+PATCH_ELEMENT, PATCH_SUPPORT = 0, 1
 EXPORT_ELEMENTS, EXPORT_Q1, EXPORT_COARSE_MAP, EXPORT_STAR_SIZES = 0, 1, 2, 3
 EXPORT_STAR_MESH, EXPORT_A0, EXPORT_STAR_LEVELS = 4, 5, 6
 
@@ -50,7 +51,7 @@ class SpnetError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("star_set", C.c_int), ("flexible", C.c_int),
                 ("max_restarts", C.c_int), ("batch_rhs", C.c_int), ("star_map", C.c_int),
-                ("reserved", C.c_int * 10)]
+                ("patch", C.c_int), ("reserved", C.c_int * 9)]
 
 
 class Request(C.Structure):
@@ -302,11 +303,30 @@ class Operator:
             pass
 
 
+def check_static_restrict_args(r, rc, n_free, m0):
+    """Arguments of spnet_pc_restrict_static, checked before any launch: both torch
+    CUDA tensors on the same device, float64, contiguous; r of n_free entries, rc
+    of at least m0 (the kernels read r[0..n_free) and write rc[0..m0))."""
+    for name, t in (("r", r), ("rc", rc)):
+        if not _is_torch(t) or not t.is_cuda:
+            raise ValueError(f"restrict_static: {name} must be a CUDA tensor")
+        if str(t.dtype) != "torch.float64":
+            raise ValueError(f"restrict_static: {name} must be float64, not {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"restrict_static: {name} must be contiguous")
+    if r.device != rc.device:
+        raise ValueError("restrict_static: r and rc must be on the same device")
+    if r.numel() != n_free:
+        raise ValueError(f"restrict_static: r has {r.numel()} entries, the operator {n_free} free dofs")
+    if rc.numel() < m0:
+        raise ValueError(f"restrict_static: rc has {rc.numel()} entries, fewer than m0 = {m0}")
+
+
 class Preconditioner:
     """setup_preconditioner: the two-level additive Schwarz preconditioner."""
 
     def __init__(self, op: Operator, H, gamma_faces, precision=PREC_MIXED, star_set=STARS_INTERIOR,
-                 flexible=-1, max_restarts=2, batch_rhs=1, star_map=0):
+                 flexible=-1, max_restarts=2, batch_rhs=1, star_map=0, patch=PATCH_ELEMENT):
         self._lib = op._lib
         self.op = op
         self.handle = C.c_void_p()
@@ -314,6 +334,8 @@ class Preconditioner:
         o.precision, o.star_set, o.flexible, o.max_restarts = precision, star_set, flexible, max_restarts
         o.batch_rhs = batch_rhs
         o.star_map = star_map
+        o.patch = patch if isinstance(patch, int) else (PATCH_SUPPORT if patch == "support"
+                                                         else PATCH_ELEMENT)
         gf = (C.c_int * 3)(*(list(gamma_faces) + [0, 0, 0])[:3])
         _check(self._lib.setup_preconditioner(op.handle, float(H), gf, C.byref(o),
                                               C.byref(self.handle)))
@@ -356,13 +378,16 @@ class Preconditioner:
         return self._vec_call(self._lib.spnet_pc_restrict, r, self.info.m0)
 
     def restrict_static(self, r, rc):
-        """r_c = R_0 r into the caller's device tensor rc, allocating nothing."""
-        rp, mem, keep = _arg(r, np.float64)
-        if mem != MEM_DEVICE or not _is_torch(rc) or not rc.is_cuda:
-            raise ValueError("restrict_static takes device tensors only")
+        """r_c = R_0 r into the caller's device tensor rc, allocating nothing.
+
+        r and rc must be contiguous float64 CUDA tensors on one device, r of length
+        n_free and rc of at least m0 entries; anything else raises ValueError before
+        the library is called."""
+        check_static_restrict_args(r, rc, self.op.info.n_free, self.info.m0)
         import torch
-        torch.cuda.current_stream(keep.device).synchronize()
-        _check(self._lib.spnet_pc_restrict_static(self.handle, rp, C.c_void_p(rc.data_ptr())))
+        torch.cuda.current_stream(r.device).synchronize()
+        _check(self._lib.spnet_pc_restrict_static(self.handle, C.c_void_p(r.data_ptr()),
+                                                  C.c_void_p(rc.data_ptr())))
         return rc
 
     def coarse(self, rc):
@@ -488,6 +513,8 @@ class Server:
         q.opts.precision = precision
         ss = problem.star_set if star_set is None else star_set
         q.opts.star_set = ss if isinstance(ss, int) else (STARS_ALL if ss == "all" else STARS_INTERIOR)
+        q.opts.patch = PATCH_SUPPORT if getattr(problem, "patch", "element") == "support" \
+            else PATCH_ELEMENT
         q.opts.flexible = flexible
         q.opts.max_restarts = max_restarts
         q.opts.batch_rhs = batch_rhs

@@ -3,6 +3,9 @@ import ctypes
 import os
 import re
 
+import numpy as np
+import pytest
+
 from paper_2207_07488_gb300 import build as B
 from paper_2207_07488_gb300 import spnet
 
@@ -54,3 +57,33 @@ def test_argument_types_match_the_header():
         params = params.strip()
         n = 0 if params in ("", "void") else params.count(",") + 1
         assert len(getattr(lib, name).argtypes) == n, name
+
+
+def test_static_restrict_argument_checks_on_host():
+    # the binding's checks of spnet_pc_restrict_static's tensors run before any launch;
+    # exercised here with stand-ins that report CUDA placement without a GPU
+    import torch
+
+    from paper_2207_07488_gb300.spnet import check_static_restrict_args
+
+    class T:
+        def __init__(self, n, dtype=torch.float64, contiguous=True, device="cuda:0"):
+            self.n, self.dtype, self._c, self.device = n, dtype, contiguous, device
+            self.is_cuda = device.startswith("cuda")
+
+        def is_contiguous(self):
+            return self._c
+
+        def numel(self):
+            return self.n
+
+    T.__module__ = "torch.stand_in"
+    check_static_restrict_args(T(10), T(4), 10, 4)
+    check_static_restrict_args(T(10), T(5), 10, 4)   # a longer rc is fine
+    bad = [(T(10, dtype=torch.float32), T(4)), (T(10), T(4, dtype=torch.float32)),
+           (T(10, contiguous=False), T(4)), (T(10), T(4, contiguous=False)),
+           (T(9), T(4)), (T(11), T(4)), (T(10), T(3)), (T(10, device="cpu"), T(4)),
+           (T(10), T(4, device="cuda:1")), (np.zeros(10), T(4))]
+    for a, b in bad:
+        with pytest.raises(ValueError):
+            check_static_restrict_args(a, b, 10, 4)

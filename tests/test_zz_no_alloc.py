@@ -1,11 +1,13 @@
 """The allocation-free restriction entry point against the ordinary one.
 
 spnet_pc_restrict_static serves callers that cannot allocate device memory
-during the call (for example code inside CUDA stream capture).  It must give
-the same r_c = R_0 r as spnet_pc_restrict, on two calls in a row (the shared
-static scratch keeps the previous call's contents, which must not leak into
-the next result).  Collected last so that a failure here leaves every other
-test already run.
+during the call: hosts whose device memory is all reserved up front by
+another allocator, and loops that must not enter cudaMalloc.  It must give
+the same r_c = R_0 r as spnet_pc_restrict and as the oracle's R_0 r, on two
+calls in a row (the shared static scratch keeps the previous call's
+contents, which must not leak into the next result), for 2D and 3D meshes
+and for 1 and 3 dofs per node.  Collected last so that a failure here leaves
+every other test already run.
 """
 import numpy as np
 import pytest
@@ -16,34 +18,42 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
+from oracle import operator as oop  # noqa: E402
+from oracle.coarse import CoarseSpace  # noqa: E402
 from paper_2207_07488_gb300 import networks as nw  # noqa: E402
 from paper_2207_07488_gb300 import spnet  # noqa: E402
 
 
-def _case(dim):
-    if dim == 2:
-        p = nw.config1()
-    else:
+def _problem(case):
+    if case == "2d":
+        return nw.config1()
+    if case == "3d":
         net = nw.fiber_network_3d(1500, 0.2, 0.01, seed=31)
-        p = nw.scalar_band_problem(net, 0.25)
+        return nw.scalar_band_problem(net, 0.25)
+    net = nw.fiber_network_3d(1200, 0.25, 0.02, seed=41, keep="clamped_x")
+    return nw.truss_band_problem(net, 0.25)
+
+
+@pytest.mark.parametrize("case", ["2d", "3d", "3d_3dof"])
+def test_static_restrict_matches_restrict_twice(case):
+    p = _problem(case)
     op = spnet.Operator.from_problem(p)
     pc = spnet.Preconditioner(op, p.H, p.gamma_faces, precision=spnet.PREC_MIXED)
-    return op, pc
-
-
-@pytest.mark.parametrize("dim", [2, 3])
-def test_static_restrict_matches_restrict_twice(dim):
-    op, pc = _case(dim)
-    rng = np.random.default_rng(11 + dim)
+    free, A, _ = oop.split(p)
+    R0 = CoarseSpace(p, free, A.tocsr()).R0
+    rng = np.random.default_rng(11 + len(case))
     n, m0 = op.info.n_free, pc.info.m0
+    assert n == free.size and m0 == R0.shape[0]
     rc_out = torch.full((m0,), float("nan"), dtype=torch.float64, device="cuda")
     for call in range(2):
         r = rng.standard_normal(n) * (1 + call)
         ref = pc.restrict(r)
         got = pc.restrict_static(torch.from_numpy(r).cuda(), rc_out).cpu().numpy()
-        # the same arithmetic in the same order: equal to the ordinary entry point
-        # within the tolerance of the restriction parity test
-        assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+        # every entry within 1e-13 of the sum of magnitudes it adds up: against the
+        # ordinary entry point and against the oracle's R_0 r
+        bound = 1e-13 * (abs(R0) @ np.abs(r)) + 1e-300
+        assert np.all(np.abs(got - ref) <= bound)
+        assert np.all(np.abs(got - R0 @ r) <= bound)
 
 
 def _grid_patch(k=300, h_div=10, lo=0.45):
@@ -76,3 +86,18 @@ def test_static_restrict_rejects_oversized_mesh():
     # the ordinary entry point still serves this mesh
     rr = np.random.default_rng(5).standard_normal(op.info.n_free)
     assert np.all(np.isfinite(pc.restrict(rr)))
+
+
+def test_static_restrict_rejects_bad_tensors():
+    # checked in the binding before the library is called (no launch)
+    p = _problem("2d")
+    op = spnet.Operator.from_problem(p)
+    pc = spnet.Preconditioner(op, p.H, p.gamma_faces, precision=spnet.PREC_MIXED)
+    n, m0 = op.info.n_free, pc.info.m0
+    r = torch.zeros(n, dtype=torch.float64, device="cuda")
+    rc = torch.zeros(m0, dtype=torch.float64, device="cuda")
+    bad = [(r.float(), rc), (r, rc.float()), (r[:-1], rc), (r, rc[:-1]), (r.cpu(), rc),
+           (torch.zeros(2 * n, dtype=torch.float64, device="cuda")[::2], rc)]
+    for a, b in bad:
+        with pytest.raises(ValueError):
+            pc.restrict_static(a, b)
