@@ -74,9 +74,26 @@ def parse():
     ap.add_argument("--c5-fibers", type=int, default=200000,
                     help="--mode c5: fibres of the large network (the configuration names 400000)")
     ap.add_argument("--c5-nh", type=int, default=24, help="--mode c5: elements per axis (H = 1/nh)")
-    ap.add_argument("--stream-requests", type=int, default=128,
+    ap.add_argument("--stream-requests", type=int, default=512,
                     help="requests of the serving-stream measurement (0: skip)")
+    ap.add_argument("--stream-load", type=float, default=1.2,
+                    help="Poisson arrival rate of the serving stream, as a multiple of its saturated rate")
     return ap.parse_args()
+
+
+def _stream_request(i):
+    return nw.request_problem(4000 + i)
+
+
+def stream_requests(n):
+    """The serving stream's requests (networks.request_problem(4000 + i)), generated on the
+    host cores by a spawn-started pool (no fork after CUDA is initialised)."""
+    import multiprocessing as mp
+    workers = max(1, min(16, os.cpu_count() or 1, n // 8))
+    if workers == 1:
+        return [_stream_request(i) for i in range(n)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_stream_request, range(n), chunksize=4)
 
 
 def combine_over_ranks(n_local, seconds, world):
@@ -213,30 +230,58 @@ def peaks():
 # algorithmic bytes of one launch of the iteration kernels
 # ---------------------------------------------------------------------------
 def kernel_bytes(op, pc, prec_bytes):
-    """Algorithmic bytes of one launch of each iteration kernel: every array the
-    kernel must touch, counted once per pass (the star gather counts each star's
-    copy of r)."""
+    """Bytes of one launch of each iteration kernel: (algorithmic, format overhead).
+
+    Algorithmic bytes follow the per-iteration count of the method: every array
+    the kernel's mathematical task must touch, once per pass, in the precision it
+    computes in (FP64 vectors, v-byte factors and coarse inverse, 4-byte indices,
+    `xb`-byte local coordinates), with no storage-format extras.  For the star
+    solve that is the gather of r and the write of the local results (an index
+    list, r and the result: 4 + 8 + 8 bytes per star entry) and the factor
+    coefficients of both triangular solves (2 v per entry of L, diagonal
+    included); its window descriptors, column indices, padding slots, star
+    headers and inverse permutations are format overhead.  For the coarse
+    solve it is the upper triangle of the symmetric A_0^{-1} (the dense-inverse
+    method), the tile padding being overhead; int64 row pointers count as int32.
+    """
     n = op.info.n_free
     nnz = op.info.nnz_ff
     i = pc.info
     ss = i.sum_star
+    env = i.factor_nnz + ss                 # entries of the local factors, diagonal included
     d = op.dim
     nc = 2 ** d
-    vb = prec_bytes                      # factor, coarse inverse and star result bytes
-    xb = 8 if prec_bytes == 8 else 4     # local coordinates read by update / combine
+    vb = prec_bytes                         # factor, coarse inverse and star result bytes
+    xb = 8 if prec_bytes == 8 else 4        # local coordinates read by update / combine
     nt = (i.m0 + 127) // 128
-    return {
-        # values + columns, row pointers (int64), z gathered, p and q read and written
-        "spmv": 12 * nnz + 8 * (n + 1) + 8 * n + 32 * n,
-        # headers, inverse permutations and window records; r over every star; w written
-        "stars": i.star_stream_bytes + 8 * ss + vb * ss,
-        # the packed upper tiles of A_0^{-1}; r_c formed from the corner sums
-        "coarse": vb * (nt * (nt + 1) // 2) * 128 * 128 + 8 * 8 * i.m0 + 8 * i.m0,
+    m0 = i.m0
+    tiles = vb * (nt * (nt + 1) // 2) * 128 * 128
+    alg = {
+        # values + columns, row pointers, z read, p and q read and written (q = A z + beta q,
+        # p = z + beta p)
+        "spmv": 12 * nnz + 4 * (n + 1) + 8 * n + 32 * n,
         # x, p, r, q read, x and r written, local coordinates, corner sums written
         "update": 48 * n + xb * d * n + 8 * nc * i.n_elem,
-        # local coordinates, star results, r and the old z read, z written
-        "combine": xb * d * n + vb * ss + 24 * n,
+        # the upper triangle of A_0^{-1}; r_c from the corner sums; z_c written
+        "coarse": vb * m0 * (m0 + 1) // 2 + 8 * nc * i.n_elem + 8 * m0,
+        # index list, r gathered and results written per star entry; factor coefficients
+        "stars": 20 * ss + 2 * vb * env,
+        # local coordinates, star results, z_c, r and the old z read, z written
+        "combine": xb * d * n + vb * ss + 8 * m0 + 24 * n,
     }
+    over = {
+        "spmv": 4 * (n + 1),
+        "update": 0,
+        "coarse": tiles - vb * m0 * (m0 + 1) // 2,
+        # the solve streams as stored (window records, headers, inverse permutations), r and
+        # the results, less the algorithmic bytes
+        "stars": int(i.star_stream_bytes + 8 * ss + vb * ss - alg["stars"]),
+        "combine": 0,
+    }
+    return alg, over
+
+
+SCHWARZ = ("stars", "coarse", "combine")  # kernels of the preconditioner apply (a4-a7)
 
 
 def run_gb300(args, rank, world, local):
@@ -298,7 +343,7 @@ def run_gb300(args, rank, world, local):
         info = (op, pc, st[0])
         return info, x
 
-    def timed(n_steps, warm, host=None):
+    def timed(n_steps, warm, host=None, xs=None):
         times, last = [], None
         for k in range(warm + n_steps):
             flush.zero_()
@@ -314,14 +359,17 @@ def run_gb300(args, rank, world, local):
                 raise RuntimeError(f"solve did not converge: relres={st.relres}")
             if k >= warm:
                 times.append(e0.elapsed_time(e1))
+                if xs is not None:
+                    xs[k % len(probs)] = x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
             if k == warm + n_steps - 1:
                 last = (op.info, pc.info, st, kernel_bytes(op, pc, 8 if prec == spnet.PREC_FP64 else 4))
             pc.close()
             op.close()
         return times, last
 
-    def serve(n, inflight, precision, rate=None):
-        """n requests through a server; all at once, or Poisson arrivals at `rate` per second."""
+    def serve(n, inflight, precision, rate=None, keep=0):
+        """n requests through a server; all at once, or Poisson arrivals at `rate` per second.
+        The solutions of the first `keep` requests are returned (request k solves probs[k % R])."""
         sv = spnet.Server(max_inflight=inflight)
         rng = np.random.default_rng(1234)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n)) if rate else np.zeros(n)
@@ -339,8 +387,20 @@ def run_gb300(args, rank, world, local):
                 raise RuntimeError(f"request failed: {res}")
         span_ms = max(r["device_end_ms"] for _, r in out) - min(r["device_start_ms"] for _, r in out)
         lat = np.array([r["latency_ms"] for _, r in out])
-        return dict(n=n, span_ms=span_ms, wall_s=t1 - t0, lat=lat,
+        return dict(n=n, span_ms=span_ms, wall_s=t1 - t0, lat=lat, xs=[x[0] for x, _ in out[:keep]],
                     iters=max(r["iterations"] for _, r in out), relres=max(r["relres"] for _, r in out))
+
+    def relerr(a, b):
+        a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    def golden_u0():
+        """The oracle's solution of replicate 0 (FP64, relres 1e-12), stored by the test suite."""
+        path = os.path.join(ROOT, "tests", "golden", "c2_oracle_solution.npz")
+        if args.workload != "c2" or rank != 0 or not os.path.exists(path):
+            return None
+        u = np.load(path)["u"]
+        return u if u.size == probs[0].net.n_nodes else None
 
     def multi_rhs(k=32, n_one=8):
         """k load cases on one network: a block of k right-hand sides stepped together
@@ -356,19 +416,24 @@ def run_gb300(args, rank, world, local):
             spnet.pcg_solve(op, pc, F[:n], G[:n])  # warm-up: graph capture, kernel attributes
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            _, st = spnet.pcg_solve(op, pc, F[:n], G[:n])
+            U, st = spnet.pcg_solve(op, pc, F[:n], G[:n])
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             if not all(s.converged for s in st):
                 raise RuntimeError("multi-right-hand-side solve did not converge")
             out[width] = dict(value=n / dt, iters=[int(min(s.iterations for s in st)),
                                                    int(max(s.iterations for s in st))],
-                              relres=max(s.relres for s in st))
+                              relres=max(s.relres for s in st), U=U)
             pc.close()
+        # plain FP64 solutions of the same load cases (the reference of the errors)
+        pc = spnet.Preconditioner(op, p.H, p.gamma_faces, precision=spnet.PREC_FP64, batch_rhs=k)
+        U64, _ = spnet.pcg_solve(op, pc, F, G)
+        pc.close()
         op.close()
+        err = max(relerr(out[k]["U"][j].cpu().numpy(), U64[j].cpu().numpy()) for j in range(k))
         return {"k": k, "value": round(out[k]["value"], 3), "unit": "solves/s",
                 "one_at_a_time": round(out[1]["value"], 3), "iterations": out[k]["iters"],
-                "relres": out[k]["relres"],
+                "relres": out[k]["relres"], "relerr_vs_fp64_max": err,
                 "note": (f"{k} load cases f ~ U(0,1) on the first network, one pcg_solve with batch_rhs={k} "
                          f"against {n_one} of them with batch_rhs=1; solve only (operator and set-up "
                          "excluded), device arrays, host clock around the call")}
@@ -378,7 +443,9 @@ def run_gb300(args, rank, world, local):
         500..20000 fibres, about 300 nodes per coarse element, 1..16 right-hand sides, each
         request's right-hand sides stepped together), all at once and as Poisson arrivals;
         plain FP64 PCG (one request and one right-hand side at a time) on the first n_fp."""
-        reqs = [nw.request_problem(4000 + i) for i in range(n_req)]
+        t_gen = time.perf_counter()
+        reqs = stream_requests(n_req)
+        t_gen = time.perf_counter() - t_gen
 
         def run(items, precision, batched, inflight_, rate=None, keep=0):
             sv = spnet.Server(max_inflight=inflight_)
@@ -406,12 +473,11 @@ def run_gb300(args, rank, world, local):
 
         run(reqs[:4], prec, True, inflight)  # warm-up
         sat = run(reqs, prec, True, inflight, keep=n_fp)
-        rate = 0.9 * sat["n"] / (sat["span_ms"] / 1e3)
+        rate = args.stream_load * sat["n"] / (sat["span_ms"] / 1e3)
         pois = run(reqs, prec, True, inflight, rate=rate)
         fp = run(reqs[:n_fp], spnet.PREC_FP64, False, 1, keep=n_fp)
         same = run(reqs[:n_fp], prec, True, inflight)
-        relerr = max(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-                     for a, b in zip(sat["xs"], fp["xs"]))
+        errs = [max(relerr(a[j], b[j]) for j in range(a.shape[0])) for a, b in zip(sat["xs"], fp["xs"])]
         nodes = [p.net.n_nodes for p, _ in reqs]
         return {
             "requests": sat["n"], "rhs": sat["rhs"],
@@ -419,7 +485,9 @@ def run_gb300(args, rank, world, local):
             "requests_per_s": round(sat["n"] / (sat["span_ms"] / 1e3), 3),
             "latency_ms": {"p50": round(float(np.percentile(pois["lat"], 50)), 3),
                            "p99": round(float(np.percentile(pois["lat"], 99)), 3),
-                           "arrivals": f"Poisson at {rate:.1f} requests/s (0.9 of the saturated rate)"},
+                           "arrivals": f"Poisson at {rate:.1f} requests/s ({args.stream_load} x the saturated "
+                                       f"rate), {pois['n']} requests",
+                           "solves_per_s": round(pois["rhs"] / pois["wall_s"], 3)},
             "fp64_plain": {"value": round(fp["rhs"] / (fp["span_ms"] / 1e3), 3), "unit": "solves/s (right-hand sides)",
                            "requests": fp["n"], "rhs": fp["rhs"],
                            "note": "the first requests, one at a time, one right-hand side at a time, FP64"},
@@ -427,7 +495,9 @@ def run_gb300(args, rank, world, local):
                                      "unit": "solves/s (right-hand sides)", "requests": same["n"],
                                      "note": "the served batched mixed path on the requests of fp64_plain"},
             "relres_max": max(sat["relres"], pois["relres"]),
-            "relerr_vs_fp64_max": relerr,
+            "relerr_vs_fp64_max": max(errs),
+            "relerr_vs_fp64_per_request": [float(f"{e:.3g}") for e in errs],
+            "generation_s": round(t_gen, 1),
             "nodes": {"min": int(min(nodes)), "median": int(np.median(nodes)), "max": int(max(nodes))},
             "inflight": inflight,
             "note": ("value: right-hand sides over the device span of the saturated pass (all submitted at "
@@ -537,7 +607,7 @@ def run_gb300(args, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     l0 = spnet.launch_count()
-    sat = serve(args.steps, args.inflight, prec)
+    sat = serve(args.steps, args.inflight, prec, keep=len(probs))
     l1 = spnet.launch_count()
     clk = clocks.stop()
     torch.cuda.synchronize()
@@ -550,10 +620,18 @@ def run_gb300(args, rank, world, local):
     # plain FP64 PCG, one request at a time, on the same path
     n_fp = max(2, min(4, args.steps))
     serve(1, 1, spnet.PREC_FP64)
-    fp = serve(n_fp, 1, spnet.PREC_FP64)
+    fp = serve(n_fp, 1, spnet.PREC_FP64, keep=len(probs))
     # the mixed path one request at a time, device-resident inputs, L2 flushed between requests
-    times, last = timed(min(args.steps, 5), 0)
+    single_xs = {}
+    times, last = timed(min(args.steps, 5), 0, xs=single_xs)
     torch.cuda.synchronize()
+    # errors of the mixed results against plain FP64 PCG on the same networks, and
+    # against the oracle's stored FP64 solution of replicate 0
+    u0 = golden_u0()
+    errs = {"served_vs_fp64": max(relerr(a, b) for a, b in zip(sat["xs"], fp["xs"])),
+            "single_stream_vs_fp64": max(relerr(single_xs[j], fp["xs"][j]) for j in single_xs),
+            "fp64_vs_oracle": relerr(fp["xs"][0], u0) if u0 is not None else None,
+            "served_vs_oracle": relerr(sat["xs"][0], u0) if u0 is not None else None}
     # a profiled pass over the same steps: every kernel launch timed with CUDA
     # events on its own stream (eager launches, so that each kernel has its events)
     spnet.profile_reset()
@@ -572,17 +650,43 @@ def run_gb300(args, rank, world, local):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(p.n_dof * 8)}
     mrhs = None if args.no_multi_rhs else multi_rhs()
     c3b = None if args.no_structural else structural_c3b()
-    c4 = stream_c4(args.stream_requests, args.inflight, min(8, args.stream_requests)) if args.stream_requests else None
+    c4 = stream_c4(args.stream_requests, args.inflight, min(16, args.stream_requests)) if args.stream_requests else None
     return dict(sat=sat, pois=pois, fp=fp, times=times, last=last, prof=prof, launches=l1 - l0,
                 clocks=clk, e2e=e2e, desc=desc, prof_steps=len(ptimes), prof_ms=sum(ptimes), mrhs=mrhs,
-                stream=c4, c3b=c3b)
+                stream=c4, c3b=c3b, errs=errs)
+
+
+def host_cpu():
+    """The host's CPU model and the threads the oracle's numpy/BLAS may use."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            if k.strip() in ("model name", "Model", "Hardware") and v.strip():
+                model = v.strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    env = {k: os.environ[k] for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+           if k in os.environ}
+    threads = os.cpu_count()
+    for v in env.values():
+        if v.isdigit():
+            threads = min(threads, int(v))
+    return {"cpu": model, "machine": os.uname().machine, "cores": os.cpu_count(), "blas_threads": threads,
+            "thread_env": env}
 
 
 def cpu_oracle_sample(problem, iters_full, sample_iters=3):
     """Bounded CPU sample: the oracle's set-up plus a few PCG iterations.
 
-    Returns (seconds for one full solve, extrapolated as set-up + iters_full x
-    the measured time per iteration, description).
+    Returns (sample seconds, the fraction of one full solve the sample is,
+    description).  The fraction is (set-up + s t_it) / (set-up + iters_full t_it)
+    with t_it the measured time per iteration: the rest of the solve repeats
+    iterations like the sampled ones.
     """
     from oracle.solve import OracleSolver
 
@@ -593,9 +697,9 @@ def cpu_oracle_sample(problem, iters_full, sample_iters=3):
     t2 = time.perf_counter()
     per_it = (t2 - t1) / sample_iters
     full = (t1 - t0) + iters_full * per_it
-    desc = (f"oracle set-up ({t1 - t0:.1f} s) + {sample_iters} PCG iterations ({per_it:.2f} s each), "
-            f"extrapolated to {iters_full} iterations")
-    return full, desc
+    desc = (f"oracle set-up ({t1 - t0:.1f} s) + {sample_iters} PCG iterations ({per_it:.2f} s each) = "
+            f"{(t2 - t0) / full:.3f} of a {iters_full}-iteration solve")
+    return t2 - t0, (t2 - t0) / full, desc
 
 
 def main():
@@ -613,20 +717,26 @@ def main():
             return
         prob = gen(0)
         iters = REF_ITERS.get(args.workload)
-        times, desc_s = [], ""
+        times, fracs, desc_s = [], [], ""
         for k in range(args.warmup + args.steps):
-            t, desc_s = cpu_oracle_sample(prob, iters, sample_iters=2)
+            t, fr, desc_s = cpu_oracle_sample(prob, iters, sample_iters=2)
             if k >= args.warmup:
                 times.append(t)
-        v = len(times) / sum(times)
+                fracs.append(fr)
+        v = sum(fracs) / sum(times)  # solves (fractions of a solve) per second
+        host = host_cpu()
         line = {
             "impl": "reference", "metric": "solves/s at rel-res 1e-8 (served; p50/p99 latency)", "value": v,
             "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "solve": "assembly+setup+pcg, rtol 1e-8", "impl": "cpu fp64 oracle"},
-            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "config": {"workload": desc, "solve": "assembly+setup+pcg, rtol 1e-8", "impl": "cpu fp64 oracle",
+                       "step": ("one bounded sample per step (set-up + 2 PCG iterations), "
+                                f"{sum(fracs) / len(fracs):.3f} of a solve on average; value = the "
+                                "solve fractions of the timed steps over their time")},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": host["blas_threads"], "kind": "oracle",
+                             "host": host,
                              "sample": f"per step: {desc_s} ({desc}, numpy/scipy FP64)"},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }
@@ -644,13 +754,21 @@ def main():
     sat, pois, fp = r["sat"], r["pois"], r["fp"]
     value, tot = combine_over_ranks(sat["n"], sat["span_ms"] / 1e3, world)
     times = r["times"]
-    oi, pi, st, kb = r["last"]
+    oi, pi, st, (kb, ko) = r["last"]
     prof = r["prof"]
     # dominant iteration kernel by device time inside the timed region
     cand = {k: v for k, v in prof.items() if k in kb and v[0] > 0}
     dom = max(cand, key=lambda k: cand[k][1]) if cand else None
     peak, src = peaks()
     roof = None
+    per_kernel = {}
+    for k in cand:
+        n_l, ms = prof[k]
+        avg_s = ms / n_l / 1e3
+        per_kernel[k] = {"algorithmic_bytes": int(kb[k]), "format_overhead_bytes": int(ko[k]),
+                         "avg_launch_us": round(avg_s * 1e6, 3),
+                         "achieved_gbs": round(kb[k] / avg_s / 1e9, 1),
+                         "frac": round(kb[k] / avg_s / 1e9 / peak, 4)}
     if dom:
         n_l, ms = prof[dom]
         avg_s = ms / n_l / 1e3
@@ -659,12 +777,28 @@ def main():
                 "measured_in": "profiled pass of the same steps (CUDA events per launch)",
                 "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": profiled_traffic(dom), "bytes_per_launch": int(kb[dom]),
+                "format_overhead_bytes_per_launch": int(ko[dom]),
                 "avg_launch_us": round(avg_s * 1e6, 3)}
+        if "spmv" in per_kernel:
+            roof["frac_spmv"] = per_kernel["spmv"]["frac"]
+        sch = [k for k in SCHWARZ if k in cand]
+        if sch:
+            b = sum(kb[k] for k in sch)
+            t = sum(prof[k][1] / prof[k][0] / 1e3 for k in sch)
+            roof["frac_schwarz_apply"] = round(b / t / 1e9 / peak, 4)
+            roof["schwarz_apply"] = {"kernels": sch, "algorithmic_bytes": int(b), "us": round(t * 1e6, 3),
+                                     "note": ("star solve + coarse product + combine (prolongation, star "
+                                              "sums), times added (the star solve overlaps the others)")}
+        roof["bytes_rule"] = ("algorithmic bytes per the per-iteration count of the method: index list, "
+                              "r and results per star entry (20 B) and 2 v B per factor entry for the star "
+                              "solve; storage-format bytes (window descriptors, columns, headers, padding, "
+                              "tile padding, int64 row pointers) listed apart as format overhead")
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        t, desc_s = cpu_oracle_sample(WORKLOADS[args.workload][0](0), int(st.iterations))
-        cpu = {"value": 1.0 / t, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{desc_s}; {desc}, numpy/scipy FP64"}
+        t, fr, desc_s = cpu_oracle_sample(WORKLOADS[args.workload][0](0), int(st.iterations))
+        host = host_cpu()
+        cpu = {"value": fr / t, "unit": "solves/s", "cores": host["blas_threads"], "kind": "oracle",
+               "host": host, "sample": f"{desc_s}; {desc}, numpy/scipy FP64"}
     if rank != 0:
         return
     share = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0] > 0}
@@ -692,7 +826,9 @@ def main():
         "structural_c3b": r.get("c3b"),
         "single_stream": {"value": round(len(times) / (sum(times) / 1e3), 3), "unit": "solves/s",
                           "ms_per_solve": round(sum(times) / len(times), 3),
+                          "relerr_vs_fp64_max": (r.get("errs") or {}).get("single_stream_vs_fp64"),
                           "note": "mixed, one request at a time, inputs on the device, L2 flushed between"},
+        "relerr": r.get("errs"),
         "config": {"workload": r["desc"], "precision": args.precision, "inflight": args.inflight,
                    "n_free": int(oi.n_free),
                    "nnz": int(oi.nnz_ff), "m0": int(pi.m0), "stars": int(pi.n_stars),
@@ -706,7 +842,7 @@ def main():
                               "device span of the served requests (CUDA events), all submitted at once"),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": int(r["launches"]),
-        "clocks": r["clocks"], "kernels": share,
+        "clocks": r["clocks"], "kernels": share, "kernel_roofline": per_kernel,
     }
     print(json.dumps(line))
 
