@@ -45,10 +45,13 @@ extern "C" {
 #define SPNET_ERR_NOT_SPD (-2)         /* a pivot <= 0 in a local or coarse factorisation */
 #define SPNET_ERR_NO_MEMORY (-3)       /* device allocation failed */
 #define SPNET_ERR_NO_CONVERGENCE (-4)  /* maxit reached; the iterate is still returned */
-#define SPNET_ERR_TIMEOUT (-5)         /* a bounded device wait expired */
+#define SPNET_ERR_TIMEOUT (-5)         /* a bounded device wait expired (reserved: no call of
+                                          this build waits on the device with a limit, so
+                                          none returns it) */
 #define SPNET_ERR_CUDA (-6)            /* a CUDA runtime error */
 #define SPNET_ERR_UNSUPPORTED (-7)     /* a size beyond the limits of this build */
 #define SPNET_ERR_BAD_H (-8)           /* l_i / H is not an integer >= 1 */
+#define SPNET_ERR_CANCELLED (-9)       /* a served request was cancelled before admission */
 
 #define SPNET_MEM_HOST 0
 #define SPNET_MEM_DEVICE 1
@@ -126,7 +129,9 @@ typedef struct {
   int64_t star_stream_bytes; /* bytes one star solve reads from its solve streams
                                 (headers, inverse permutations, entries) */
   int64_t star_warps_per_block; /* the star solve's mapping in use (see spnet_options.star_map) */
-  int64_t reserved[3];
+  int64_t coarse_dropped;       /* coarse functions left out of A_0^{-1} as linear combinations
+                                   of earlier ones (see setup_preconditioner) */
+  int64_t reserved[2];
 } spnet_pc_info;
 
 /* spnet_assemble -- assemble K on all n_nodes*ndof dofs from an edge list.
@@ -175,8 +180,15 @@ int build_network_operator(int dim, int ndof, int64_t n_nodes, const double* coo
  * that component is Dirichlet (bit 2*axis for x_axis = 0, bit 2*axis+1 for
  * x_axis = l_axis); mesh nodes on those faces carry no coarse dof.  Coarse
  * basis functions are truncated to free dofs; a function that vanishes at
- * every free dof of its component is dropped.  opts may be NULL (defaults).
- * Errors: BAD_H, NOT_SPD (a local or coarse pivot <= 0), UNSUPPORTED
+ * every free dof of its component is dropped.  When the truncated functions
+ * are linearly dependent (A_0 singular), the coarse solve works on a basis of
+ * their span V_H: in coarse-dof order, a function whose pivot in the
+ * elimination of A_0 is at most 1e-8 times its diagonal entry of A_0 lies in
+ * the span of the functions before it and is left out
+ * (spnet_pc_info.coarse_dropped); P_0 is unchanged.  In mixed precision A_0
+ * is inverted in FP32 unless a pivot falls to 1e-3 of its diagonal entry or
+ * below, in which case the inverse is formed in FP64 and rounded.  opts may be
+ * NULL (defaults).  Errors: BAD_H, NOT_SPD (a local pivot <= 0), UNSUPPORTED
  * (a star beyond 65535 dofs), NO_MEMORY.
  */
 int setup_preconditioner(spnet_op_t op, double H, const int* gamma_faces,
@@ -191,7 +203,9 @@ int setup_preconditioner(spnet_op_t op, double H, const int* gamma_faces,
  * recursive residual, then recomputes b - A x in FP64 and restarts from it
  * (at most max_restarts times) if it is above the tolerance.  stats [nrhs]
  * is host memory (may be NULL).  Returns NO_CONVERGENCE if any right-hand
- * side misses rtol within maxit steps (x is still written).
+ * side misses rtol within maxit steps (x is still written), BAD_INPUT if a
+ * right-hand side's lifted data b = f_I - K_ID g or its initial residual is
+ * not finite (a NaN or Inf at a free dof of f, in g, or in x0).
  */
 int pcg_solve(spnet_op_t op, spnet_pc_t pc, int nrhs, const double* f, const double* g,
               double* x, int use_x0, double rtol, int maxit, int mem, spnet_stats* stats);
@@ -248,14 +262,31 @@ typedef struct {
   char message[256];        /* the error message when status != SPNET_OK */
 } spnet_result;
 
-/* spnet_server_create -- start max_inflight (1..64) workers on the current device. */
+/* spnet_server_create -- start max_inflight (1..64) workers on the current device.  The
+ * memory budget of the running requests is the device's free memory now, less
+ * reserve_bytes (NO_MEMORY if that is not positive). */
 int spnet_server_create(int max_inflight, int64_t reserve_bytes, spnet_server_t* out);
-/* spnet_server_submit -- queue a request (host arrays, borrowed until spnet_server_wait
- * returns for it); *ticket identifies it.  Errors: BAD_INPUT (malformed request). */
+/* spnet_server_submit -- queue a request (host arrays, borrowed until spnet_server_wait or
+ * spnet_server_poll has returned its result); *ticket identifies it.  Errors: BAD_INPUT
+ * (malformed request), NO_MEMORY (its estimated peak device memory, spnet_server_estimate,
+ * exceeds the server's budget: it could never be admitted; nothing is queued). */
 int spnet_server_submit(spnet_server_t server, const spnet_request* request, int64_t* ticket);
 /* spnet_server_wait -- block until the request is done; its result (the solutions are in
  * request->x).  A request that failed reports its error in result->status/message. */
 int spnet_server_wait(spnet_server_t server, int64_t ticket, spnet_result* result);
+/* spnet_server_poll -- the non-blocking form of spnet_server_wait: *done = 1 and the result
+ * (the ticket is then retired) if the request has finished, else *done = 0. */
+int spnet_server_poll(spnet_server_t server, int64_t ticket, spnet_result* result, int* done);
+/* spnet_server_cancel -- withdraw a request that is still queued: *cancelled = 1 and its
+ * result (wait/poll) reports SPNET_ERR_CANCELLED; a request already admitted runs to its
+ * end (*cancelled = 0).  Errors: BAD_INPUT (unknown ticket). */
+int spnet_server_cancel(spnet_server_t server, int64_t ticket, int* cancelled);
+/* spnet_server_estimate -- the peak device bytes admission charges for a request (the
+ * operator and its copies of K, star factors and solve windows, the dense A_0 and its
+ * inverse, the PCG vectors and blocks).  Host only. */
+int spnet_server_estimate(const spnet_request* request, int64_t* bytes);
+/* spnet_server_budget -- the device bytes the server's running requests may hold. */
+int spnet_server_budget(spnet_server_t server, int64_t* bytes);
 /* spnet_server_destroy -- finish every queued request, stop the workers, free the server. */
 int spnet_server_destroy(spnet_server_t server);
 

@@ -27,6 +27,19 @@ Which nodes a star holds (the problem's ``patch``):
 
 Every A_j and A_0 is factored densely by Cholesky; the local terms are added
 in ascending star order.
+
+A rank-deficient coarse basis.  V_0 = V_H is the span of the basis functions
+truncated to the free dofs, and these can be linearly dependent (a function
+whose support holds few free nodes may be a combination of its neighbours
+there); A_0 = R_0 A R_0^T is then singular, but the projection P_0 onto the
+span is still defined.  The oracle keeps a basis of the span: Cholesky of A_0
+in the coarse-dof order, where a function whose pivot (its part A-orthogonal
+to the functions kept before it) is at most COARSE_DROP = 1e-8 times its
+diagonal entry lies in their span and is left out.  Exactly dependent
+functions leave pivots at rounding level (3e-11 and below on the sparse
+networks here), independent ones 1e-6 and above; 1e-8 sits between, on a
+logarithmic scale.  With K the kept functions,
+P_0 = R_K^T A_KK^{-1} R_K A, which equals R_0^T A_0^+ R_0 A.
 """
 from __future__ import annotations
 
@@ -35,6 +48,38 @@ import scipy.linalg as sla
 import scipy.sparse.linalg as spla
 
 from .coarse import CoarseSpace, mesh_multi, mesh_shape
+
+
+COARSE_DROP = 1e-8  # relative pivot at or below which a coarse function is in the span of earlier ones
+
+
+def coarse_basis(A0, tol=COARSE_DROP):
+    """Kept coarse dofs and the Cholesky factor of A_0 on them.
+
+    Cholesky in the coarse-dof order; dof k is left out when its pivot
+    d_k = A0[k,k] - sum over kept j < k of L[k,j]^2 is at most tol * A0[k,k].
+    When no pivot is that small this is LAPACK's Cholesky of A_0 (the same
+    pivots); otherwise the elimination is written out with the drops.
+    """
+    m = A0.shape[0]
+    diag = np.diag(A0).copy()
+    try:
+        L = np.linalg.cholesky(A0)
+        if np.all(np.diag(L) ** 2 > tol * diag):
+            return np.arange(m), (L, True)
+    except np.linalg.LinAlgError:
+        pass
+    S = A0.copy()                      # the Schur complement of the kept dofs so far
+    keep = np.zeros(m, dtype=bool)
+    for k in range(m):
+        d = S[k, k]
+        if not d > tol * diag[k]:
+            continue
+        keep[k] = True
+        col = S[k + 1:, k] / d
+        S[k + 1:, k + 1:] -= np.outer(col, S[k, k + 1:])
+    K = np.nonzero(keep)[0]
+    return K, (np.linalg.cholesky(A0[np.ix_(K, K)]), True)
 
 
 def star_mesh_nodes(nH, star_set):
@@ -99,14 +144,25 @@ class SchwarzPreconditioner:
             self.star_mesh.append(k)
             self.stars.append(S)
             self.factors.append(fac)
-        self.c0 = sla.cho_factor(self.coarse.A0, lower=True) if self.coarse.m0 else None
+        self.c0 = None
+        self.coarse_kept = np.zeros(0, dtype=np.int64)
+        if self.coarse.m0:
+            self.coarse_kept, self.c0 = coarse_basis(self.coarse.A0)
 
     # pieces of B, exposed so that each step can be checked on its own
+    def coarse_solve(self, rc):
+        """z_c with z_K = A_KK^{-1} r_K on the kept coarse dofs, zero on the others."""
+        zc = np.zeros_like(rc)
+        if self.c0 is not None:
+            K = self.coarse_kept
+            zc[K] = sla.cho_solve(self.c0, rc[K])
+        return zc
+
     def coarse_term(self, r):
-        """R_0^T A_0^{-1} R_0 r."""
+        """R_0^T A_0^{-1} R_0 r (A_0^{-1} on the kept basis of V_H)."""
         if self.c0 is None:
             return np.zeros_like(r)
-        return self.coarse.prolong(sla.cho_solve(self.c0, self.coarse.restrict(r)))
+        return self.coarse.prolong(self.coarse_solve(self.coarse.restrict(r)))
 
     def local_solve(self, j, rj):
         if self.local == "dense":

@@ -559,6 +559,11 @@ int pcg_batch_run(spnet_op_s* op, spnet_pc_s* pc, int k, const double* df, const
     Scal sc{};
     SPNET_CUDA_TRY(cudaMemcpyAsync(&sc, pc->scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
     SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!std::isfinite(sc.bb) || !std::isfinite(sc.rr)) {  // (the guard releases the events)
+      return fail(SPNET_ERR_BAD_INPUT, std::isfinite(sc.bb)
+                                           ? "pcg_solve: non-finite initial guess"
+                                           : "pcg_solve: non-finite right-hand side or Dirichlet data");
+    }
     h.bb[j] = sc.bb;
     h.rr[j] = sc.rr;
     h.done[j] = (sc.bb == 0.0 || sqrt(sc.rr) <= rtol * sqrt(sc.bb) || maxit <= 0) ? 1 : 0;

@@ -255,6 +255,7 @@ int spnet_pc_get_info(spnet_pc_t pc, spnet_pc_info* info) {
   info->device_bytes = pc->mem.bytes;
   info->star_stream_bytes = pc->stream_bytes;
   info->star_warps_per_block = pc->solve_wpb;
+  info->coarse_dropped = pc->coarse_dropped;
   return SPNET_OK;
 }
 

@@ -5,7 +5,21 @@
 //   A_ij -> A_ij - A_iK P A_Kj,  A_iK -> A_iK P,  A_Kj -> P A_Kj,  A_KK -> -P
 // with P = A_KK^{-1}; after sweeping every block the matrix holds -A^{-1}.
 // For an SPD matrix the pivot blocks are Schur complements, hence SPD, so no
-// pivoting is needed.  Each application is then one dense symmetric
+// pivoting is needed.
+// A_0 is singular when the basis functions truncated to the free dofs are
+// linearly dependent; P_0, the projection onto their span V_H, is still
+// defined.  A scalar pivot d_k that is at most DROP64 = 1e-8 times the
+// original diagonal entry A0_kk marks a function in the span of the ones swept
+// before it (exact dependence leaves d_k at rounding level, ~1e-11 or less,
+// while independent functions of the workloads keep 1e-6 or more): it is not
+// swept, and its row and column of P are zeroed, so it never enters the other
+// blocks.  A sweep over a set of pivots gives the inverse of the swept block
+// whatever the order, so the result is A_KK^{-1} on the kept functions K and
+// zero elsewhere: the same P_0.  FP32 sweeps cannot tell rounding from a small
+// pivot once one small pivot is kept, so the mixed-precision set-up sweeps in
+// FP32 only while every pivot stays above TRIG32 = 1e-3 of its diagonal entry
+// (ordinary meshes: 0.4 and more); otherwise the inverse is formed in FP64,
+// with the drops, and rounded to FP32.  Each application is then one dense symmetric
 // matrix-vector product that every SM can share, instead of two dependent
 // triangular solves.
 // The sweeps and the product run in FP64 or, for the mixed-precision
@@ -61,10 +75,17 @@ __device__ inline T zat(const T* tiles, int nt, int64_t i, int64_t j) {
 // D_pp -> -1 / D_pp; after kb pivots the block holds -D^{-1}.  Row and column
 // p pass through shared memory, double-buffered (one barrier per pivot); every
 // thread forms 1 / D_pp itself.  Returns true where a pivot was not positive.
+constexpr double DROP64 = 1e-8;  // FP64 sweeps: relative pivot at or below which a function is dropped
+constexpr double TRIG32 = 1e-3;  // FP32 sweeps: relative pivot at or below which FP64 takes over
+
+// As above, with dropping: dg holds the original diagonal entries of the block's
+// rows; a pivot at or below tol times its entry is not swept.  Returns the bitmask
+// of the dropped pivots (uniform over the threads).
 template <class T>
-__device__ bool invert_block_regs(T (&d)[4][4], int kb, T (*rowp)[NB], T (*colp)[NB]) {
+__device__ uint64_t invert_block_regs(T (&d)[4][4], int kb, T (*rowp)[NB], T (*colp)[NB], const double* dg,
+                                      double tol) {
   const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
-  bool bad = false;
+  uint64_t dropped = 0;
   for (int q = 0; q < NB / 4; ++q) {
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -80,10 +101,10 @@ __device__ bool invert_block_regs(T (&d)[4][4], int kb, T (*rowp)[NB], T (*colp)
         for (int b = 0; b < 4; ++b) colp[buf][4 * tr + b] = d[b][a];
       }
       __syncthreads();
-      T piv = colp[buf][p];
-      if (!(piv > (T)0)) {
-        bad = true;
-        piv = (T)1;
+      const T piv = colp[buf][p];
+      if (!((double)piv > tol * dg[p])) {  // in the span of the pivots kept so far
+        dropped |= 1ull << p;
+        continue;
       }
       const T ip = (T)1 / piv;
       T cv[4], rv[4];
@@ -104,19 +125,21 @@ __device__ bool invert_block_regs(T (&d)[4][4], int kb, T (*rowp)[NB], T (*colp)
         }
     }
   }
-  return bad;
+  return dropped;
 }
 
-// P = (the inverted block) = -(d after the sweeps), zero outside kb x kb
+// P = (the inverted block) = -(d after the sweeps), zero outside kb x kb and in the
+// rows and columns of dropped pivots
 template <class T>
-__device__ void store_pivot(const T (&d)[4][4], int kb, T* P) {
+__device__ void store_pivot(const T (&d)[4][4], int kb, uint64_t dropped, T* P) {
   const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int i = 4 * tr + a, j = 4 * tc + b;
-      P[i * NB + j] = (i < kb && j < kb) ? -d[a][b] : (T)0;
+      const bool off = ((dropped >> i) & 1) || ((dropped >> j) & 1);
+      P[i * NB + j] = (i < kb && j < kb && !off) ? -d[a][b] : (T)0;
     }
 }
 
@@ -134,7 +157,8 @@ __global__ void k_tiles_from_A0(const double* __restrict__ A0, int64_t m0, int n
 
 // the first pivot block (its inverse P); later ones are inverted by the sweep
 template <class T>
-__global__ void __launch_bounds__(256) k_pivot_inverse(const T* tiles, int nt, int k0, int kb, T* P, int* flags) {
+__global__ void __launch_bounds__(256) k_pivot_inverse(const T* tiles, int nt, int k0, int kb, T* P,
+                                                       const double* diag0, double tol, int* ndrop) {
   __shared__ T rowp[2][NB], colp[2][NB];
   const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
   T d[4][4];
@@ -145,9 +169,9 @@ __global__ void __launch_bounds__(256) k_pivot_inverse(const T* tiles, int nt, i
       const int i = 4 * tr + a, j = 4 * tc + b;
       d[a][b] = (i < kb && j < kb) ? zat(tiles, nt, k0 + i, k0 + j) : (T)0;
     }
-  const bool bad = invert_block_regs(d, kb, rowp, colp);
-  if (bad) atomicOr(flags, FLAG_COARSE_SPD);
-  store_pivot(d, kb, P);
+  const uint64_t dropped = invert_block_regs(d, kb, rowp, colp, diag0 + k0, tol);
+  if (threadIdx.x == 0 && dropped) atomicAdd(ndrop, __popcll(dropped));
+  store_pivot(d, kb, dropped, P);
 }
 
 // Tm = P R with R the pivot rows Z[k0 + t][:] (rows of length ldr).  The first
@@ -241,7 +265,7 @@ template <class T>
 __global__ void __launch_bounds__(256) k_sweep(T* __restrict__ tiles, int nt, int n64, int64_t m0, int64_t ldr,
                                                int k0, const T* __restrict__ P, const T* __restrict__ R,
                                                const T* __restrict__ Tm, T* __restrict__ Pn, T* __restrict__ Rn,
-                                               int* flags) {
+                                               const double* __restrict__ diag0, double tol, int* ndrop) {
   extern __shared__ __align__(16) char sm_sweep[];  // R and Tm slices, NB x NB each
   T (*sR)[NB] = reinterpret_cast<T (*)[NB]>(sm_sweep);
   T (*sT)[NB] = reinterpret_cast<T (*)[NB]>(sm_sweep + sizeof(T) * NB * NB);
@@ -329,10 +353,15 @@ __global__ void __launch_bounds__(256) k_sweep(T* __restrict__ tiles, int nt, in
   if (has_next && blockIdx.x == 0) {  // the next pivot block, already updated: invert it
     __shared__ T rowp[2][NB], colp[2][NB];
     const int kbn = (int)((m0 - k0 - NB) < NB ? (m0 - k0 - NB) : NB);
-    const bool bad = invert_block_regs(d, kbn, rowp, colp);
-    if (bad) atomicOr(flags, FLAG_COARSE_SPD);
-    store_pivot(d, kbn, Pn);
+    const uint64_t dropped = invert_block_regs(d, kbn, rowp, colp, diag0 + k0 + NB, tol);
+    if (threadIdx.x == 0 && dropped) atomicAdd(ndrop, __popcll(dropped));
+    store_pivot(d, kbn, dropped, Pn);
   }
+}
+
+__global__ void k_diag_of(const double* __restrict__ A0, int64_t m0, double* __restrict__ dg) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m0; i += (int64_t)gridDim.x * blockDim.x)
+    dg[i] = A0[i * m0 + i];
 }
 
 template <class T>
@@ -341,8 +370,10 @@ __global__ void k_negate(T* z, int64_t n) {
     z[q] = -z[q];
 }
 
+// Sweep the upper tiles of A_0 (T arithmetic) into the upper tiles of A_0^{-1}
+// (on the kept functions); *ndrop receives the count of pivots at or below tol.
 template <class T>
-static int invert_impl(spnet_pc_s* pc, const double* A0) {
+static int sweep_inverse(spnet_pc_s* pc, const double* A0, T* tiles, double tol, int* ndrop_out) {
   cudaStream_t s = pc->op->stream;
   const int64_t m0 = pc->m0;
   DevArena tmp;
@@ -355,21 +386,24 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
   const int n64 = (int)((m0 + NB - 1) / NB);
   const int64_t ldr = (int64_t)n64 * NB;
   const int64_t nti = n_upper_tiles(nt);
-  T* tiles = nullptr;
-  SPNET_TRY(pc->mem.get(&tiles, nti * CT * CT));
-  pc->ctiles = tiles;
-  pc->ctiles_n = nt;
   T *P = nullptr, *R = nullptr, *Tm = nullptr;
   SPNET_TRY(tmp.get(&P, 2 * NB * NB));
   SPNET_TRY(tmp.get(&R, 2 * NB * ldr));  // pivot rows of this step and of the next
   SPNET_TRY(tmp.get(&Tm, NB * ldr));
   SPNET_CUDA_TRY(cudaMemsetAsync(R, 0, sizeof(T) * 2 * NB * ldr, s));
   SPNET_CUDA_TRY(cudaMemsetAsync(Tm, 0, sizeof(T) * NB * ldr, s));
+  double* diag0 = nullptr;  // original diagonal of A_0 (the drop test's scale), padded to ldr
+  int* ndrop = nullptr;
+  SPNET_TRY(tmp.get(&diag0, ldr));
+  SPNET_TRY(tmp.get(&ndrop, 1));
+  SPNET_CUDA_TRY(cudaMemsetAsync(diag0, 0, sizeof(double) * ldr, s));
+  SPNET_CUDA_TRY(cudaMemsetAsync(ndrop, 0, sizeof(int), s));
+  note_launch();
+  k_diag_of<<<(unsigned)((m0 + 255) / 256), 256, 0, s>>>(A0, m0, diag0);
   note_launch();
   k_tiles_from_A0<T><<<(unsigned)nti, 256, 0, s>>>(A0, m0, nt, tiles);
-  SPNET_CUDA_TRY(cudaMemsetAsync(pc->op->dflags, 0, sizeof(int), s));
   note_launch();
-  k_pivot_inverse<T><<<1, 256, 0, s>>>(tiles, nt, 0, (int)(m0 < NB ? m0 : NB), P, pc->op->dflags);
+  k_pivot_inverse<T><<<1, 256, 0, s>>>(tiles, nt, 0, (int)(m0 < NB ? m0 : NB), P, diag0, tol, ndrop);
   const unsigned subtiles = (unsigned)n_upper_tiles(n64);
   const size_t sweep_smem = 2 * sizeof(T) * NB * NB;
   if (sweep_smem > 48 * 1024) {
@@ -392,12 +426,57 @@ static int invert_impl(spnet_pc_s* pc, const double* A0) {
     k_panel<T><<<(unsigned)(ldr / 16), 256, 0, s>>>(tiles, nt, m0, ldr, k0, kb, Pc, Rc, Tm, step == 0 ? 1 : 0);
     note_launch();
     ProfScope ps(KID_SWEEP, s);
-    k_sweep<T><<<subtiles, 256, sweep_smem, s>>>(tiles, nt, n64, m0, ldr, k0, Pc, Rc, Tm, Pn, Rn, pc->op->dflags);
+    k_sweep<T><<<subtiles, 256, sweep_smem, s>>>(tiles, nt, n64, m0, ldr, k0, Pc, Rc, Tm, Pn, Rn, diag0, tol, ndrop);
   }
   note_launch();
   k_negate<T><<<4 * num_sms(), 256, 0, s>>>(tiles, nti * CT * CT);
   SPNET_CUDA_TRY(cudaGetLastError());
-  return check_flags(pc->op->dflags, s, "setup_preconditioner (coarse matrix)");
+  SPNET_CUDA_TRY(cudaMemcpyAsync(ndrop_out, ndrop, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+  return SPNET_OK;
+}
+
+__global__ void k_round_tiles(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    b[q] = (float)a[q];
+}
+
+template <class T>
+static int invert_impl(spnet_pc_s* pc, const double* A0) {
+  cudaStream_t s = pc->op->stream;
+  const int64_t m0 = pc->m0;
+  const int nt = (int)((m0 + CT - 1) / CT);
+  const int64_t nti = n_upper_tiles(nt);
+  T* tiles = nullptr;
+  SPNET_TRY(pc->mem.get(&tiles, nti * CT * CT));
+  pc->ctiles = tiles;
+  pc->ctiles_n = nt;
+  int nd = 0;
+  if constexpr (sizeof(T) == 8) {
+    SPNET_TRY(sweep_inverse<T>(pc, A0, tiles, DROP64, &nd));
+    pc->coarse_dropped = nd;
+    return SPNET_OK;
+  } else {
+    SPNET_TRY(sweep_inverse<T>(pc, A0, tiles, TRIG32, &nd));
+    pc->coarse_dropped = 0;
+    if (nd == 0) return SPNET_OK;
+    // a pivot at or below TRIG32: an ill-conditioned or singular A_0, inverted in FP64
+    DevArena tmp;
+    tmp.stream = s;
+    struct Guard {
+      DevArena& a;
+      ~Guard() { a.free_all(); }
+    } guard{tmp};
+    double* t64 = nullptr;
+    SPNET_TRY(tmp.get(&t64, nti * CT * CT));
+    SPNET_TRY(sweep_inverse<double>(pc, A0, t64, DROP64, &nd));
+    pc->coarse_dropped = nd;
+    note_launch();
+    k_round_tiles<<<4 * num_sms(), 256, 0, s>>>(t64, tiles, nti * CT * CT);
+    SPNET_CUDA_TRY(cudaGetLastError());
+    SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+    return SPNET_OK;
+  }
 }
 
 int pc_coarse_invert(spnet_pc_s* pc, double* A0) {

@@ -719,6 +719,13 @@ int pcg_run(spnet_op_s* op, spnet_pc_s* pc, int nrhs, const double* f, const dou
       k_residual<<<G, 256, 0, s>>>(N, pc->b, pc->q, pc->r, pc->partial, &pc->scal->rr, cnt3);
       SPNET_CUDA_TRY(cudaMemcpyAsync(&h, pc->scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
       SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+      if (!std::isfinite(h.bb) || !std::isfinite(h.rr)) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(SPNET_ERR_BAD_INPUT, std::isfinite(h.bb)
+                                             ? "pcg_solve: non-finite initial guess"
+                                             : "pcg_solve: non-finite right-hand side or Dirichlet data");
+      }
       const double tol = rtol * sqrt(h.bb);
       if (h.bb == 0.0) break;
       if (sqrt(h.rr) > tol && h.iter < maxit) {

@@ -7,7 +7,8 @@
 // solutions back.  Requests wait in a FIFO queue and are admitted when a worker
 // is free and the device memory the request is estimated to need fits the
 // budget (the free memory when the server was created, less a reserve, less
-// the estimates of the requests running).  The work of admitted requests
+// the estimates of the requests running); a request whose estimate alone
+// exceeds the budget is refused at submission.  The work of admitted requests
 // overlaps on the GPU (different streams).  Nothing a request computes depends
 // on what else runs: every kernel reduces in a fixed order, so a result is the
 // same alone and in the mix.
@@ -160,7 +161,6 @@ static void worker_main(spnet_server_s* sv) {
   const bool ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaEventCreate(&ev0) == cudaSuccess && cudaEventCreate(&ev1) == cudaSuccess;
   for (;;) {
-    int64_t ticket = 0;
     Job* job = nullptr;
     {
       std::unique_lock<std::mutex> lk(sv->mu);
@@ -168,9 +168,9 @@ static void worker_main(spnet_server_s* sv) {
         if (sv->stop && sv->queue.empty()) break;
         if (!sv->queue.empty()) {
           Job& head = sv->jobs[sv->queue.front()];
-          // FIFO admission: the head waits until its estimate fits (or nothing else runs)
-          if (sv->committed + head.est <= sv->budget || sv->running == 0) {
-            ticket = sv->queue.front();
+          // FIFO admission: the head waits until its estimate fits (it fits once nothing
+          // else runs: submission refuses estimates beyond the budget)
+          if (sv->committed + head.est <= sv->budget) {
             sv->queue.pop_front();
             job = &head;
             sv->committed += job->est;
@@ -200,7 +200,6 @@ static void worker_main(spnet_server_s* sv) {
     }
     sv->cv_done.notify_all();
     sv->cv_queue.notify_all();
-    (void)ticket;
   }
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
@@ -248,14 +247,19 @@ extern "C" int spnet_server_submit(spnet_server_t sv, const spnet_request* req, 
       !q.f || !q.g || !q.x || (q.model == SPNET_MODEL_TRUSS3 && !q.dirs) || (q.n_dirichlet > 0 && !q.dirichlet_dofs) ||
       !(q.H > 0) || !(q.rtol > 0) || q.maxit < 1)
     return fail(SPNET_ERR_BAD_INPUT, "spnet_server_submit: malformed request");
+  const int64_t est = request_estimate(&q);
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->stop) return fail(SPNET_ERR_BAD_INPUT, "spnet_server_submit: the server is shutting down");
+  if (est > sv->budget)
+    return fail(SPNET_ERR_NO_MEMORY, "spnet_server_submit: the request is estimated to need " +
+                                         std::to_string(est) + " device bytes, more than the server's budget of " +
+                                         std::to_string(sv->budget));
   const int64_t t = sv->next_ticket++;
   Job& job = sv->jobs[t];
   job.req = q;
   job.res = spnet_result{};
   job.submit = Clock::now();
-  job.est = request_estimate(&q);
+  job.est = est;
   sv->queue.push_back(t);
   *ticket = t;
   sv->cv_queue.notify_all();
@@ -271,6 +275,60 @@ extern "C" int spnet_server_wait(spnet_server_t sv, int64_t ticket, spnet_result
   sv->cv_done.wait(lk, [&] { return it->second.done; });
   *out = it->second.res;
   sv->jobs.erase(it);
+  return SPNET_OK;
+}
+
+extern "C" int spnet_server_poll(spnet_server_t sv, int64_t ticket, spnet_result* out, int* done) {
+  cudaGetLastError();
+  if (!sv || !out || !done) return fail(SPNET_ERR_BAD_INPUT, "spnet_server_poll: null argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->jobs.find(ticket);
+  if (it == sv->jobs.end()) return fail(SPNET_ERR_BAD_INPUT, "spnet_server_poll: unknown ticket");
+  *done = it->second.done ? 1 : 0;
+  if (*done) {
+    *out = it->second.res;
+    sv->jobs.erase(it);
+  }
+  return SPNET_OK;
+}
+
+extern "C" int spnet_server_cancel(spnet_server_t sv, int64_t ticket, int* cancelled) {
+  cudaGetLastError();
+  if (!sv || !cancelled) return fail(SPNET_ERR_BAD_INPUT, "spnet_server_cancel: null argument");
+  *cancelled = 0;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->jobs.find(ticket);
+    if (it == sv->jobs.end()) return fail(SPNET_ERR_BAD_INPUT, "spnet_server_cancel: unknown ticket");
+    for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q) {
+      if (*q != ticket) continue;
+      sv->queue.erase(q);
+      Job& job = it->second;
+      job.res.status = SPNET_ERR_CANCELLED;
+      std::strncpy(job.res.message, "cancelled before admission", sizeof(job.res.message) - 1);
+      job.res.queue_ms = job.res.latency_ms = ms_between(job.submit, Clock::now());
+      job.done = true;
+      *cancelled = 1;
+      break;
+    }
+  }
+  if (*cancelled) {
+    sv->cv_done.notify_all();
+    sv->cv_queue.notify_all();  // the next request may now be the head
+  }
+  return SPNET_OK;
+}
+
+extern "C" int spnet_server_estimate(const spnet_request* req, int64_t* bytes) {
+  if (!req || !bytes) return fail(SPNET_ERR_BAD_INPUT, "spnet_server_estimate: null argument");
+  *bytes = request_estimate(req);
+  return SPNET_OK;
+}
+
+extern "C" int spnet_server_budget(spnet_server_t sv, int64_t* bytes) {
+  if (!sv || !bytes) return fail(SPNET_ERR_BAD_INPUT, "spnet_server_budget: null argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  *bytes = sv->budget;
   return SPNET_OK;
 }
 

@@ -133,6 +133,7 @@ struct spnet_pc_s {
   spnet::Csr K;                // A in pc order
   // coarse space
   int m0 = 0;
+  int coarse_dropped = 0;      // coarse functions left out as dependent on the others
   int32_t* cidx = nullptr;     // [n_mesh*ndof]
   void* ctiles = nullptr;      // A_0^{-1} (float or double by precision): its upper 128 x 128 tiles, packed
   void* cpart = nullptr;       // [nt*nt*CT] per row block and tile column: partial products

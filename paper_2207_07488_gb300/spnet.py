@@ -21,6 +21,7 @@ ERRORS = {
 }
 ERR_BAD_INPUT, ERR_NOT_SPD, ERR_NO_MEMORY, ERR_NO_CONVERGENCE = -1, -2, -3, -4
 ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED, ERR_BAD_H = -5, -6, -7, -8
+ERR_CANCELLED = -9
 MEM_HOST, MEM_DEVICE = 0, 1
 MODEL_SCALAR, MODEL_TRUSS3 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
@@ -36,7 +37,8 @@ EXPORTED = [
     "spnet_pc_prolong", "spnet_pc_stars", "spnet_pc_export", "spnet_launch_count",
     "spnet_profile_enable", "spnet_profile_read", "spnet_profile_reset", "spnet_pc_restrict_static",
     "spnet_server_create", "spnet_server_submit", "spnet_server_wait", "spnet_server_destroy",
-    "spnet_pc_apply_batch",
+    "spnet_pc_apply_batch", "spnet_server_poll", "spnet_server_cancel", "spnet_server_estimate",
+    "spnet_server_budget",
 ]
 KERNELS = ["spmv", "update", "restrict", "stars", "coarse", "combine", "direction",
            "star_symbolic", "star_numeric", "sweep", "galerkin"]
@@ -87,7 +89,8 @@ class PcInfo(C.Structure):
                 ("factor_nnz", C.c_int64), ("total_levels", C.c_int64), ("max_levels", C.c_int),
                 ("precision", C.c_int), ("star_set", C.c_int), ("flexible", C.c_int),
                 ("setup_ms", C.c_double), ("device_bytes", C.c_int64), ("star_stream_bytes", C.c_int64),
-                ("star_warps_per_block", C.c_int64), ("reserved", C.c_int64 * 3)]
+                ("star_warps_per_block", C.c_int64), ("coarse_dropped", C.c_int64),
+                ("reserved", C.c_int64 * 2)]
 
 
 _lib = None
@@ -132,6 +135,10 @@ def load(build_if_missing: bool = True):
     lib.spnet_server_create.argtypes = [i32, i64, C.POINTER(P)]
     lib.spnet_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(i64)]
     lib.spnet_server_wait.argtypes = [P, i64, C.POINTER(Result)]
+    lib.spnet_server_poll.argtypes = [P, i64, C.POINTER(Result), C.POINTER(C.c_int)]
+    lib.spnet_server_cancel.argtypes = [P, i64, C.POINTER(C.c_int)]
+    lib.spnet_server_estimate.argtypes = [C.POINTER(Request), C.POINTER(i64)]
+    lib.spnet_server_budget.argtypes = [P, C.POINTER(i64)]
     lib.spnet_server_destroy.argtypes = [P]
     for name in EXPORTED:
         getattr(lib, name).restype = C.c_int
@@ -476,64 +483,43 @@ class Server:
                star_set=None, flexible=-1, max_restarts=2, batch_rhs=1):
         """Queue one request for `problem` (a networks.Problem); f: (n_dof,) or (nrhs, n_dof),
         default problem.f; g likewise over the Dirichlet dofs, default problem.dirichlet_vals."""
-        net = problem.net
-        f = problem.f if f is None else f
-        f = np.ascontiguousarray(np.atleast_2d(np.asarray(f, np.float64)))
-        nrhs = f.shape[0]
-        g = problem.dirichlet_vals if g is None else g
-        g = np.ascontiguousarray(np.broadcast_to(np.atleast_2d(np.asarray(g, np.float64)),
-                                                 (nrhs, len(problem.dirichlet_dofs))))
-        x = np.zeros((nrhs, problem.n_dof), np.float64)
-        edges = np.ascontiguousarray(net.edges, np.int64)
-        scalar = problem.model == "scalar"
-        coef = np.ascontiguousarray(net.cond if scalar else net.stiff, np.float64)
-        dirs = None if scalar else np.ascontiguousarray(net.dirs, np.float64)
-        coords = np.ascontiguousarray(net.coords, np.float64)
-        dd = np.ascontiguousarray(problem.dirichlet_dofs, np.int64)
-        q = Request()
-        q.model = MODEL_SCALAR if scalar else MODEL_TRUSS3
-        q.dim = net.dim
-        q.n_nodes = net.n_nodes
-        q.n_edges = net.n_edges
-        q.edges = edges.ctypes.data
-        q.coef = coef.ctypes.data
-        q.dirs = dirs.ctypes.data if dirs is not None else None
-        q.coords = coords.ctypes.data
-        for a in range(3):
-            q.domain_hi[a] = float(net.domain[a]) if a < net.dim else 1.0
-        q.n_dirichlet = len(dd)
-        q.dirichlet_dofs = dd.ctypes.data if len(dd) else None
-        q.nrhs = nrhs
-        q.f = f.ctypes.data
-        q.g = g.ctypes.data if g.size else x.ctypes.data
-        q.x = x.ctypes.data
-        q.H = float(problem.H)
-        for a, v in enumerate((list(problem.gamma_faces) + [0, 0, 0])[:3]):
-            q.gamma_faces[a] = int(v)
-        q.opts.precision = precision
-        ss = problem.star_set if star_set is None else star_set
-        q.opts.star_set = ss if isinstance(ss, int) else (STARS_ALL if ss == "all" else STARS_INTERIOR)
-        q.opts.patch = PATCH_SUPPORT if getattr(problem, "patch", "element") == "support" \
-            else PATCH_ELEMENT
-        q.opts.flexible = flexible
-        q.opts.max_restarts = max_restarts
-        q.opts.batch_rhs = batch_rhs
-        q.rtol = float(rtol)
-        q.maxit = int(maxit)
+        live = make_request(problem, f, g, precision, rtol, maxit, star_set, flexible, max_restarts,
+                            batch_rhs)
         ticket = C.c_int64(0)
-        _check(self._lib.spnet_server_submit(self.handle, C.byref(q), C.byref(ticket)))
-        self._live[ticket.value] = (q, edges, coef, dirs, coords, dd, f, g, x)
+        _check(self._lib.spnet_server_submit(self.handle, C.byref(live[0]), C.byref(ticket)))
+        self._live[ticket.value] = live
         return ticket.value
 
-    def wait(self, ticket):
-        """Block until the request is done: (x of shape (nrhs, n_dof), result dict)."""
-        res = Result()
-        _check(self._lib.spnet_server_wait(self.handle, C.c_int64(ticket), C.byref(res)))
+    def _result(self, ticket, res):
         live = self._live.pop(ticket)
         out = {k: getattr(res, k) for k in ("status", "iterations", "relres", "queue_ms", "latency_ms",
                                               "device_start_ms", "device_end_ms")}
         out["message"] = res.message.decode(errors="replace")
         return live[-1], out
+
+    def wait(self, ticket):
+        """Block until the request is done: (x of shape (nrhs, n_dof), result dict)."""
+        res = Result()
+        _check(self._lib.spnet_server_wait(self.handle, C.c_int64(ticket), C.byref(res)))
+        return self._result(ticket, res)
+
+    def poll(self, ticket):
+        """(x, result dict) if the request has finished, else None (non-blocking)."""
+        res = Result()
+        done = C.c_int(0)
+        _check(self._lib.spnet_server_poll(self.handle, C.c_int64(ticket), C.byref(res), C.byref(done)))
+        return self._result(ticket, res) if done.value else None
+
+    def cancel(self, ticket):
+        """Withdraw a queued request; True if it had not been admitted yet."""
+        c = C.c_int(0)
+        _check(self._lib.spnet_server_cancel(self.handle, C.c_int64(ticket), C.byref(c)))
+        return bool(c.value)
+
+    def budget(self):
+        b = C.c_int64(0)
+        _check(self._lib.spnet_server_budget(self.handle, C.byref(b)))
+        return int(b.value)
 
     def close(self):
         if self.handle:
@@ -545,3 +531,62 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def request_estimate(problem, f=None, **kw):
+    """Device bytes the server's admission charges for a request (spnet_server_estimate)."""
+    live = make_request(problem, f, None, **kw)
+    b = C.c_int64(0)
+    _check(load().spnet_server_estimate(C.byref(live[0]), C.byref(b)))
+    return int(b.value)
+
+
+def make_request(problem, f=None, g=None, precision=PREC_MIXED, rtol=1e-8, maxit=2000, star_set=None,
+                 flexible=-1, max_restarts=2, batch_rhs=1):
+    """A spnet_request for `problem` and the arrays it points to (keep them alive with it):
+    (request, edges, coef, dirs, coords, dirichlet dofs, f, g, x)."""
+    net = problem.net
+    f = problem.f if f is None else f
+    f = np.ascontiguousarray(np.atleast_2d(np.asarray(f, np.float64)))
+    nrhs = f.shape[0]
+    g = problem.dirichlet_vals if g is None else g
+    g = np.ascontiguousarray(np.broadcast_to(np.atleast_2d(np.asarray(g, np.float64)),
+                                             (nrhs, len(problem.dirichlet_dofs))))
+    x = np.zeros((nrhs, problem.n_dof), np.float64)
+    edges = np.ascontiguousarray(net.edges, np.int64)
+    scalar = problem.model == "scalar"
+    coef = np.ascontiguousarray(net.cond if scalar else net.stiff, np.float64)
+    dirs = None if scalar else np.ascontiguousarray(net.dirs, np.float64)
+    coords = np.ascontiguousarray(net.coords, np.float64)
+    dd = np.ascontiguousarray(problem.dirichlet_dofs, np.int64)
+    q = Request()
+    q.model = MODEL_SCALAR if scalar else MODEL_TRUSS3
+    q.dim = net.dim
+    q.n_nodes = net.n_nodes
+    q.n_edges = net.n_edges
+    q.edges = edges.ctypes.data
+    q.coef = coef.ctypes.data
+    q.dirs = dirs.ctypes.data if dirs is not None else None
+    q.coords = coords.ctypes.data
+    for a in range(3):
+        q.domain_hi[a] = float(net.domain[a]) if a < net.dim else 1.0
+    q.n_dirichlet = len(dd)
+    q.dirichlet_dofs = dd.ctypes.data if len(dd) else None
+    q.nrhs = nrhs
+    q.f = f.ctypes.data
+    q.g = g.ctypes.data if g.size else x.ctypes.data
+    q.x = x.ctypes.data
+    q.H = float(problem.H)
+    for a, v in enumerate((list(problem.gamma_faces) + [0, 0, 0])[:3]):
+        q.gamma_faces[a] = int(v)
+    q.opts.precision = precision
+    ss = problem.star_set if star_set is None else star_set
+    q.opts.star_set = ss if isinstance(ss, int) else (STARS_ALL if ss == "all" else STARS_INTERIOR)
+    q.opts.patch = PATCH_SUPPORT if getattr(problem, "patch", "element") == "support" \
+        else PATCH_ELEMENT
+    q.opts.flexible = flexible
+    q.opts.max_restarts = max_restarts
+    q.opts.batch_rhs = batch_rhs
+    q.rtol = float(rtol)
+    q.maxit = int(maxit)
+    return (q, edges, coef, dirs, coords, dd, f, g, x)

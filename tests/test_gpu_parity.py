@@ -173,7 +173,7 @@ def test_restrict_coarse_prolong(name, prec):
     rc = pc.restrict(r)
     check_entries(rc, R0 @ r, 1e-13 * (abs(R0) @ np.abs(r)) + 1e-300, "restrict")
     zc = pc.coarse(rc)
-    ref = np.linalg.solve(o.B.coarse.A0, rc)
+    ref = o.B.coarse_solve(rc)
     # A_0^{-1} applied in FP64 or FP32 (cond(A_0) is at most a few hundred here): every
     # entry within the precision's error of the largest entry
     tol = 1e-10 if prec == "fp64" else 2e-4
@@ -321,3 +321,51 @@ def test_star_solve_mapping_changes_no_result():
         np.testing.assert_array_equal(u, sols[0])
     with pytest.raises(spnet.SpnetError):
         spnet.Preconditioner(spnet.Operator.from_problem(p), p.H, p.gamma_faces, star_map=9)
+
+
+def test_dependent_coarse_functions():
+    # a sparse 3D draw whose truncated coarse functions are linearly dependent (three of
+    # them lie in the span of earlier ones): A_0 is singular, P_0 the projection onto the
+    # span (Section 4.1).  The library drops the same three in FP64, its P_0 reproduces
+    # V_H, its coarse term matches the oracle's entry by entry, and both precisions solve.
+    net = nw.fiber_network_3d(1500, 0.2, 0.01, seed=3)
+    p = nw.scalar_band_problem(net, 0.25, name="small3d-dependent")
+    o = OracleSolver(p, local="dense")
+    n_dep = o.B.coarse.m0 - o.B.coarse_kept.size
+    assert n_dep == 3
+    R0 = o.B.coarse.R0
+    rng = np.random.default_rng(8)
+    for prec in ("fp64", "mixed"):
+        op = spnet.Operator.from_problem(p)
+        pc = spnet.Preconditioner(op, p.H, p.gamma_faces, precision=PREC[prec])
+        if prec == "fp64":
+            assert pc.info.coarse_dropped == n_dep
+            v = R0.T @ rng.standard_normal(R0.shape[0])
+            Pv = pc.prolong(pc.coarse(pc.restrict(o.A @ v)))
+            assert np.abs(Pv - v).max() <= 1e-9 * np.abs(v).max()
+            r = rng.standard_normal(o.A.shape[0])
+            ref = o.B.coarse_term(r)
+            got = pc.prolong(pc.coarse(pc.restrict(r)))
+            check_entries(got, ref, 1e-9 * np.abs(ref).max(), "coarse term")
+        else:
+            assert pc.info.coarse_dropped >= n_dep
+        u, st = spnet.pcg_solve(op, pc, p.f, p.dirichlet_vals, rtol=1e-8)
+        assert st[0].converged and st[0].relres <= 1e-8
+        ref = o.solve(rtol=1e-8, flexible=(prec == "mixed"))
+        assert rel(u, ref.u) <= 1e-6
+
+
+def test_structural_workload_as_written():
+    # the 20000-fibre structural network spans nothing: the clamped component is kept, f = 0
+    # and its Dirichlet data are zero, so u = 0; its coarse functions are dependent
+    p = nw.config3()
+    op = spnet.Operator.from_problem(p)
+    for prec in (spnet.PREC_FP64, spnet.PREC_MIXED):
+        pc = spnet.Preconditioner(op, p.H, p.gamma_faces, precision=prec)
+        assert pc.info.coarse_dropped > 0
+        u, st = spnet.pcg_solve(op, pc, p.f, p.dirichlet_vals, rtol=1e-8)
+        assert st[0].converged and np.all(u == 0.0)
+        # a load on the free dofs is solved too
+        f = np.random.default_rng(1).uniform(0.0, 1.0, p.n_dof)
+        u, st = spnet.pcg_solve(op, pc, f, p.dirichlet_vals, rtol=1e-8)
+        assert st[0].converged and st[0].relres <= 1e-8
