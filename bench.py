@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--inflight", type=int, default=4)
-    ap.add_argument("--mode", default="served", choices=["served", "single", "multi_rhs", "c5"],
+    ap.add_argument("--mode", default="served", choices=["served", "single", "multi_rhs", "c5", "lap_conv"],
                     help="single: only the one-request-at-a-time measurement (for profiling runs)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
@@ -583,6 +583,8 @@ def run_gb300(args, rank, world, local):
                 "note": ("40000-fibre 3D network, 3 dofs per node, clamped at x < 0.01, u_x = 0.01 at x > 0.99, "
                          "H = 1/12; one request at a time from host arrays (operator, set-up, PCG), host clock")}
 
+    if args.mode == "lap_conv":  # the paper's heat experiments (Section 6.2, Table lap_conv)
+        return dict(lap_conv=lap_conv_table())
     if args.mode == "multi_rhs":  # the k-right-hand-side measurement only (profiling runs of the batched kernels)
         return dict(mrhs=multi_rhs())
     if args.mode == "c5":  # a large network with 32 right-hand sides
@@ -680,6 +682,48 @@ def host_cpu():
             "thread_env": env}
 
 
+# Table lap_conv (Section 6.2): (mean, largest) PCG rate at H^-1 = 4, 8, 16, 32
+LAP_CONV_PAPER = {"grid": [(0.18, 0.31), (0.25, 0.33), (0.27, 0.32), (0.28, 0.31)],
+                  "fibre": [(0.29, 0.48), (0.33, 0.43), (0.39, 0.49), (0.42, 0.47)],
+                  "fibre_weighted": [(0.34, 0.44), (0.40, 0.52), (0.45, 0.51), (0.47, 0.54)]}
+
+
+def lap_conv_table(seed=6000):
+    """The three heat problems of Section 6.2 through the library: the (2^9+1)^2 grid,
+    the uniform fibre network of Section 6.1 (fibres of length 0.05, total length 1000)
+    with gamma = 1 and with gamma ~ U[0.1, 1]; Gamma = the boundary, f = M1, stars at
+    every mesh node; mean and largest rate until the K-norm error has fallen by 1e-8."""
+    from paper_2207_07488_gb300.experiments import pcg_rates
+    t0 = time.perf_counter()
+    net = nw.fiber_heat_network(seed)
+    gamma = nw.heat_weights(net, seed + 1)
+    gen_s = time.perf_counter() - t0
+    out = {"networks": {"grid": {"nodes": (2 ** 9 + 1) ** 2},
+                        "fibre": {"nodes": int(net.n_nodes), "edges": int(net.n_edges), "seed": seed,
+                                  "generation_s": round(gen_s, 1)}}}
+    for name in ("grid", "fibre", "fibre_weighted"):
+        rows = []
+        for k, Hinv in enumerate((4, 8, 16, 32)):
+            if name == "grid":
+                p = nw.grid_heat_problem(9, 1.0 / Hinv)
+            else:
+                p = nw.fiber_heat_problem(net, 1.0 / Hinv, gamma=gamma if name == "fibre_weighted" else None)
+            t1 = time.perf_counter()
+            try:
+                r = pcg_rates(p)
+            except Exception as e:  # stars beyond the library's 65535 dofs (H^-1 = 4 here)
+                rows.append({"H_inv": Hinv, "paper": LAP_CONV_PAPER[name][k], "not_run": str(e)[:160]})
+                continue
+            rows.append({"H_inv": Hinv, "tau_mean": round(r["mean"], 3), "tau_max": round(r["max"], 3),
+                         "paper": LAP_CONV_PAPER[name][k], "steps": r["steps"], "stars": r["stars"],
+                         "m0": r["m0"], "s": round(time.perf_counter() - t1, 2)})
+        out[name] = rows
+    out["note"] = ("rates tau_l = |e_l|_K / |e_{l-1}|_K for l >= 2 until |e_l|_K <= 1e-8 |e_0|_K; FP64 "
+                   "textbook PCG through the library (iterate l = the solve with maxit = l), reference "
+                   "solution at relres 1e-13; paper values from Table lap_conv")
+    return out
+
+
 def cpu_oracle_sample(problem, iters_full, sample_iters=3):
     """Bounded CPU sample: the oracle's set-up plus a few PCG iterations.
 
@@ -743,6 +787,10 @@ def main():
         print(json.dumps(line))
         return
     r = run_gb300(args, rank, world, local)
+    if args.mode == "lap_conv":
+        if rank == 0:
+            print(json.dumps({"mode": "lap_conv", "table": r["lap_conv"]}))
+        return
     if args.mode == "c5":
         if rank == 0:
             print(json.dumps({"mode": "c5", "large_network_32_rhs": r["c5"]}))

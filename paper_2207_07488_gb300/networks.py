@@ -468,6 +468,40 @@ def grid_heat_problem(k: int, H: float, star_set=STAR_ALL, patch=PATCH_SUPPORT) 
                    star_set, f"grid{k}", patch=patch)
 
 
+def fiber_heat_network(seed: int, total_length: float = 1000.0, r: float = 0.05) -> Network:
+    """The uniform 2D fibre network of Section 6.1: fibres of length r with midpoints
+    uniform in [-r/2, 1 + r/2]^2 and uniform angles, drawn until their clipped length
+    (the total edge length |1|_M^2) reaches total_length; a node at every crossing,
+    nodes closer than r * 1e-4 along a fibre merged, and only the components that
+    reach the boundary of the square kept (the rest cannot carry the Dirichlet data)."""
+    return fiber_network_2d(0, r, seed, midpoint_pad=0.5 * r, keep="boundary", total_length=total_length)
+
+
+def fiber_heat_problem(net: Network, H: float, gamma=None, name="") -> Problem:
+    """The heat problem of Section 6.2 on a network: Gamma = the boundary of the unit
+    square (u = 0 there), f = M1 (eq. 2.1: half the length of the edges at a node),
+    conductance gamma_xy / |x - y| (Example 3.2) with gamma = 1 or the given per-edge
+    weights; stars at every mesh node holding the nodes where the node's basis
+    function is nonzero."""
+    from dataclasses import replace
+    if gamma is not None:
+        net = replace(net, cond=net.cond * np.asarray(gamma, np.float64))
+    X = net.coords
+    on_b = np.nonzero(np.any((X <= 0.0) | (X >= 1.0), axis=1))[0]
+    lengths = np.linalg.norm(X[net.edges[:, 1]] - X[net.edges[:, 0]], axis=1)
+    f = np.zeros(net.n_nodes)
+    np.add.at(f, net.edges[:, 0], 0.5 * lengths)
+    np.add.at(f, net.edges[:, 1], 0.5 * lengths)
+    allf = X_FACES | face_bit(1, 0) | face_bit(1, 1)
+    return Problem(net, 1, "scalar", on_b.astype(np.int64), np.zeros(on_b.size), f, H, (allf,),
+                   STAR_ALL, name, patch=PATCH_SUPPORT)
+
+
+def heat_weights(net: Network, seed: int, lo: float = 0.1, hi: float = 1.0) -> np.ndarray:
+    """Per-edge weights gamma_xy ~ U[lo, hi] (the weighted fibre network of Section 6.2)."""
+    return np.random.default_rng(seed).uniform(lo, hi, size=net.n_edges)
+
+
 # ----------------------------------------------------------------------------
 # the workloads
 # ----------------------------------------------------------------------------
