@@ -93,7 +93,12 @@ typedef struct {
                         once per process (default); 1..8 fixes it.  Every warp solves whole
                         stars, so the choice changes no result */
   int patch;         /* SPNET_PATCH_* (default SPNET_PATCH_ELEMENT) */
-  int reserved[9];
+  int no_panels;     /* 1: solve the dense block that ends a large star's elimination level by
+                        level also in blocks of right-hand sides; 0 (default): in mixed
+                        precision with batch_rhs >= 2, blocks of 32 nodes or more are solved
+                        by 16-row panels with tensor-core products (TF32 inputs split in high
+                        and low parts, FP32 accumulation) */
+  int reserved[8];
 } spnet_options;
 
 typedef struct {
@@ -131,7 +136,9 @@ typedef struct {
   int64_t star_warps_per_block; /* the star solve's mapping in use (see spnet_options.star_map) */
   int64_t coarse_dropped;       /* coarse functions left out of A_0^{-1} as linear combinations
                                    of earlier ones (see setup_preconditioner) */
-  int64_t reserved[2];
+  int64_t panel_stars;          /* stars whose dense block the k-right-hand-side solve runs by
+                                   panels on tensor cores (see spnet_options.no_panels) */
+  int64_t reserved[1];
 } spnet_pc_info;
 
 /* spnet_assemble -- assemble K on all n_nodes*ndof dofs from an edge list.
@@ -336,6 +343,8 @@ int spnet_pc_apply_batch(spnet_pc_t pc, int k, const double* r, double* z, int w
  *       SPNET_EXPORT_STAR_MESH  int32 [n_stars]    mesh node of each star
  *       SPNET_EXPORT_A0         double [m0*m0]     the Galerkin matrix A_0 (row-major)
  *       SPNET_EXPORT_STAR_LEVELS int32 [n_stars]   level count of each star's local solve
+ *       SPNET_EXPORT_STAR_CORE  int32 [n_stars]    nodes of the dense block that ends each star's
+ *                                                  elimination (0: none)
  * bytes must be at least the size listed.
  */
 #define SPNET_EXPORT_ELEMENTS 0
@@ -345,6 +354,7 @@ int spnet_pc_apply_batch(spnet_pc_t pc, int k, const double* r, double* z, int w
 #define SPNET_EXPORT_STAR_MESH 4
 #define SPNET_EXPORT_A0 5
 #define SPNET_EXPORT_STAR_LEVELS 6
+#define SPNET_EXPORT_STAR_CORE 7
 int spnet_pc_export(spnet_pc_t pc, int what, void* host_buf, size_t bytes);
 
 /* spnet_pc_restrict_static -- r_c = R_0 r, exactly as spnet_pc_restrict, but the

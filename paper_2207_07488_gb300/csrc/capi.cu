@@ -46,6 +46,7 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
   pc->batch_rhs = o.batch_rhs < 1 ? 1 : o.batch_rhs;
   pc->star_map = o.star_map;
   pc->patch = o.patch;
+  pc->panels = o.no_panels ? 0 : 1;
   pc->d = op->dim;
   pc->nc = 1 << op->dim;
   pc->ndof = op->ndof;
@@ -256,6 +257,7 @@ int spnet_pc_get_info(spnet_pc_t pc, spnet_pc_info* info) {
   info->star_stream_bytes = pc->stream_bytes;
   info->star_warps_per_block = pc->solve_wpb;
   info->coarse_dropped = pc->coarse_dropped;
+  info->panel_stars = pc->panel_stars;
   return SPNET_OK;
 }
 
@@ -410,6 +412,7 @@ int spnet_pc_export(spnet_pc_t pc, int what, void* host_buf, size_t bytes) {
     case SPNET_EXPORT_Q1: need = sizeof(double) * pc->N * pc->nc; break;
     case SPNET_EXPORT_COARSE_MAP: need = sizeof(int32_t) * (size_t)pc->n_mesh * pc->ndof; break;
     case SPNET_EXPORT_STAR_SIZES: case SPNET_EXPORT_STAR_MESH: case SPNET_EXPORT_STAR_LEVELS:
+    case SPNET_EXPORT_STAR_CORE:
       need = sizeof(int32_t) * pc->S; break;
     case SPNET_EXPORT_A0:
       if (!pc->A0 && pc->m0 > 0) return fail(SPNET_ERR_UNSUPPORTED, "spnet_pc_export: A_0 is kept only for m0 <= 2048");

@@ -607,6 +607,9 @@ int export_item(spnet_pc_s* pc, int what, void* host_buf) {
     case SPNET_EXPORT_STAR_LEVELS:
       if (pc->S) SPNET_CUDA_TRY(cudaMemcpyAsync(host_buf, pc->star_lev, sizeof(int32_t) * pc->S, cudaMemcpyDeviceToHost, s));
       break;
+    case SPNET_EXPORT_STAR_CORE:
+      if (pc->S) SPNET_CUDA_TRY(cudaMemcpyAsync(host_buf, pc->star_core, sizeof(int32_t) * pc->S, cudaMemcpyDeviceToHost, s));
+      break;
     case SPNET_EXPORT_A0:
       if (pc->m0) SPNET_CUDA_TRY(cudaMemcpyAsync(host_buf, pc->A0, sizeof(double) * (size_t)pc->m0 * pc->m0,
                                                  cudaMemcpyDeviceToHost, s));

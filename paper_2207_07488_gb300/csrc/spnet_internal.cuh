@@ -153,6 +153,14 @@ struct spnet_pc_s {
   int32_t* star_n = nullptr;       // [S]
   int32_t* star_lev = nullptr;     // [S]
   int32_t* star_nnz = nullptr;     // [S]
+  int32_t* star_core = nullptr;    // [S] nodes of the dense block that ends each star's elimination
+  // k-right-hand-side solves (FP32) of stars whose dense block is solved by panels on tensor cores
+  int panels = 1;                  // build them (spnet_options.panels)
+  int panel_stars = 0;             // stars solved that way
+  void* bhdr = nullptr;            // [S] headers of the k-right-hand-side solve (null: none)
+  char* brec = nullptr;            // their window records
+  float* coreL = nullptr;          // the dense blocks' tiles in MMA fragment order
+  int64_t panel_bytes = 0;         // bytes of brec and coreL
   // solve windows: per-star header (80 B), inverse permutation, window records
   void* shdr = nullptr;            // [S] headers
   uint16_t* iperm_star = nullptr;  // [sum_s] local index -> elimination position, at star_ptr

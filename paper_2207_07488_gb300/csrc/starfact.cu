@@ -93,6 +93,7 @@ struct StarArgs {
   int64_t* star_off;
   int32_t* star_lev;
   int32_t* star_nnz;
+  int32_t* star_core;
   int* flags;
   int* next;
   int vbytes;
@@ -404,6 +405,7 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
       nlev++;
       if (full) dense = true;
     }
+    int core_c = 0;  // nodes of the dense block
     if (dense && npos < n) {
       // the rest, in ascending node order, one node per level, columns dense
       const int core0 = npos;
@@ -431,6 +433,7 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
       }
       nlev += c;
       ncol += c * (c - 1) / 2;
+      core_c = c;
       if (lane == 0) W.colstart[n] = ncol;
       __syncwarp();
     }
@@ -474,6 +477,7 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
       A.star_off[s] = (int64_t)off;
       A.star_lev[s] = nlev;
       A.star_nnz[s] = ncol;
+      A.star_core[s] = core_c;
     }
     int32_t* gidx = (int32_t*)(blob + L.gidx);
     uint16_t* perm = (uint16_t*)(blob + L.perm);
@@ -730,6 +734,23 @@ struct SupportTest {
   }
 };
 
+// the descriptor of every window of a level of E entries (ends set already): scan
+// steps and the carry flag
+__device__ inline void finish_level(char* recs, int64_t wb, int lane, int64_t E, int RB) {
+  __syncwarp();
+  __threadfence_block();
+  const int nwl = level_windows(E);
+  for (int k = lane; k < nwl; k += 32) {
+    char* rec = recs + (wb + k) * RB;
+    const int cnt = (int)((E - (int64_t)k * WIN) < WIN ? (E - (int64_t)k * WIN) : WIN);
+    const unsigned ends = *(volatile unsigned*)rec;
+    const int steps = window_steps(ends, cnt);
+    const unsigned carry = (cnt == WIN && !((ends >> 31) & 1u)) ? 1u : 0u;
+    ((unsigned*)rec)[1] = (unsigned)steps | (carry << 8);
+  }
+  __syncwarp();
+}
+
 // the windows of one level: entries of the rows of the level in order, the
 // descriptor of every window (ends, steps, carry flag)
 template <class T>
@@ -752,18 +773,7 @@ __device__ void pack_level(char* recs, int64_t wb, int lane, int v0, int v1, con
       if (diag) atomicOr((unsigned*)rec, 1u << sl);
     }
   }
-  __syncwarp();
-  __threadfence_block();
-  const int nwl = level_windows(E);
-  for (int k = lane; k < nwl; k += 32) {
-    char* rec = recs + (wb + k) * RB;
-    const int cnt = (int)((E - (int64_t)k * WIN) < WIN ? (E - (int64_t)k * WIN) : WIN);
-    const unsigned ends = *(volatile unsigned*)rec;
-    const int steps = window_steps(ends, cnt);
-    const unsigned carry = (cnt == WIN && !((ends >> 31) & 1u)) ? 1u : 0u;
-    ((unsigned*)rec)[1] = (unsigned)steps | (carry << 8);
-  }
-  __syncwarp();
+  finish_level(recs, wb, lane, E, RB);
 }
 
 // warp per star: set-up blob (FP64 factor) -> header, inverse permutation, window records
@@ -975,6 +985,199 @@ void launch_star_solve(spnet_pc_s* pc, const double* r, const double* q, const S
 }
 
 // ---------------------------------------------------------------------------
+// Dense blocks with many right-hand sides, on tensor cores.
+// The elimination of a large star ends in a dense block of c nodes, one node
+// per level; such blocks hold most of the factor of large stars (over 80 % on
+// the 200000-fibre 3D network and on the largest 2D serving requests) and,
+// solved level by level, are a chain of 2c dependent steps.  In the k-right-
+// hand-side solve (FP32) a star whose block has at least CORE_TC nodes runs
+//   the forward sparse levels,
+//   one level that removes the terms outside the block from the block's rows
+//     (y_c = r_c - L_cn y_n),
+//   L_cc y_c = y_c and L_cc^T z_c = y_c by panels of 16 rows,
+//   the backward sparse levels.
+// A forward panel step multiplies the panel by the inverse of its 16 x 16
+// diagonal tile and subtracts L_rp y_p from every later panel r; a backward
+// step uses the transposed tiles and updates the earlier panels.  Every
+// product is a warp-level tensor-core MMA (m16n8k8 with TF32 inputs, each
+// input split into a high and a low TF32 part and three products accumulated
+// in FP32, which keeps FP32 accuracy).  The chain shrinks to 2 ceil(c/16)
+// panel steps.
+// A star's block area in coreL (floats), 16 x 16 blocks of 256 floats in MMA
+// A-fragment order ([k half][lane][4]: lane l, value e holds row l/4 + 8 (e&1),
+// column 8 khalf + l%4 + 4 (e>>1)), np = ceil(c / 16) panels:
+//   DI(p), DIT(p)    inverse of diagonal tile p and its transpose
+//   F(r, q), FT(r, q)  tile (r, q) of L_cc (r > q) and its transpose
+// Rows and columns past c are zero.
+// ---------------------------------------------------------------------------
+constexpr int CORE_TC = 32;  // smallest dense block solved by panels
+
+struct BatchHdr {
+  int64_t eoff;   // first window record (in brec for a star solved with its block by panels, else srec)
+  int64_t coff;   // first float of the star's block area in coreL (-1: none)
+  int32_t nfwd;   // records before the block's solve
+  int32_t ne;     // records in all
+  int32_t core0;  // elimination position of the block's first node
+  int32_t c;      // nodes of the block (0: no panel solve)
+};
+static_assert(sizeof(BatchHdr) == 32, "BatchHdr layout");
+
+__host__ __device__ inline int core_panels(int c) { return (c + 15) / 16; }
+__host__ __device__ inline int64_t core_floats(int c) {
+  const int64_t np = core_panels(c);
+  return 256 * np * (np + 1);
+}
+__host__ __device__ inline int64_t blk_DI(int p) { return 256ll * p; }
+__host__ __device__ inline int64_t blk_DIT(int np, int p) { return 256ll * (np + p); }
+__host__ __device__ inline int64_t blk_F(int np, int r, int q) { return 256ll * (2ll * np + (int64_t)r * (r - 1) / 2 + q); }
+__host__ __device__ inline int64_t blk_FT(int np, int r, int q) {
+  return 256ll * (2ll * np + (int64_t)np * (np - 1) / 2 + (int64_t)r * (r - 1) / 2 + q);
+}
+
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// B fragments of rows rb .. rb+15 of the block's part of y (columns 0..7; columns past
+// JW and rows past c read as zero), split into high and low TF32 parts: [k half][b0, b1]
+struct PanelB {
+  uint32_t h[2][2], l[2][2];
+};
+template <int JW>
+__device__ __forceinline__ PanelB load_panel_b(const float* y, int core0, int rb, int c) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  PanelB B;
+#pragma unroll
+  for (int kh = 0; kh < 2; ++kh)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int r = rb + kh * 8 + t + 4 * e;
+      const float v = (g < JW && r < c) ? y[(core0 + r) * JW + g] : 0.f;
+      B.h[kh][e] = tf32_of(v);
+      B.l[kh][e] = tf32_of(v - __uint_as_float(B.h[kh][e]));
+    }
+  return B;
+}
+
+// the A fragment of one k half, split into high and low TF32 parts
+__device__ __forceinline__ void split_a(const float4 a, uint32_t (&ah)[4], uint32_t (&al)[4]) {
+  const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    ah[e] = tf32_of(av[e]);
+    al[e] = tf32_of(av[e] - __uint_as_float(ah[e]));
+  }
+}
+
+// d[i] = block i (16 x 16, fragments at blk[i]) x the panel B, for NB blocks at once: their
+// fragments are loaded together and their products interleaved (independent chains)
+template <int NB>
+__device__ __forceinline__ void blocks_mma(float (&d)[NB][4], const float* const (&blk)[NB], const PanelB& B) {
+  const int lane = threadIdx.x & 31;
+  float4 a[NB][2];
+#pragma unroll
+  for (int i = 0; i < NB; ++i)
+#pragma unroll
+    for (int kh = 0; kh < 2; ++kh) a[i][kh] = __ldg(reinterpret_cast<const float4*>(blk[i]) + kh * 32 + lane);
+#pragma unroll
+  for (int i = 0; i < NB; ++i)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) d[i][e] = 0.f;
+#pragma unroll
+  for (int kh = 0; kh < 2; ++kh) {
+    uint32_t ah[NB][4], al[NB][4];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) split_a(a[i][kh], ah[i], al[i]);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) mma_tf32(d[i], al[i], B.h[kh][0], B.h[kh][1]);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) mma_tf32(d[i], ah[i], B.l[kh][0], B.l[kh][1]);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) mma_tf32(d[i], ah[i], B.h[kh][0], B.h[kh][1]);
+  }
+}
+
+// rows rb + l/4 (+ 8), columns 2 (l%4) (+ 1) of the block's part of y: set (sub = false)
+// or subtract (sub = true) the accumulator d
+template <int JW>
+__device__ __forceinline__ void blk_store(const float (&d)[4], float* y, int core0, int rb, int c, bool sub) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int row = rb + g + ((e >> 1) << 3), col = 2 * t + (e & 1);
+    if (col < JW && row < c) {
+      float* p = &y[(core0 + row) * JW + col];
+      *p = sub ? *p - d[e] : d[e];
+    }
+  }
+}
+
+// subtract (block of panel r) x B from panel r, for the panels r of [r0, r1) (step dr), four
+// at a time; blk(r) gives the block's fragments
+template <int JW, class BlkOf>
+__device__ __forceinline__ void panel_updates(const PanelB& B, float* y, int core0, int c, int r0, int r1,
+                                              BlkOf blk) {
+  int r = r0;
+  for (; r + 4 <= r1; r += 4) {
+    const float* const bl[4] = {blk(r), blk(r + 1), blk(r + 2), blk(r + 3)};
+    float u[4][4];
+    blocks_mma<4>(u, bl, B);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) blk_store<JW>(u[i], y, core0, 16 * (r + i), c, true);
+  }
+  for (; r < r1; ++r) {
+    const float* const bl[1] = {blk(r)};
+    float u[1][4];
+    blocks_mma<1>(u, bl, B);
+    blk_store<JW>(u[0], y, core0, 16 * r, c, true);
+  }
+}
+
+// L_cc y_c = y_c, then L_cc^T z_c = y_c, in place on the block's part of y (one warp)
+template <int JW>
+__device__ void core_panel_solve(const float* __restrict__ L, float* y, int core0, int c) {
+  const int np = core_panels(c);
+  for (int p = 0; p < np; ++p) {
+    {
+      const PanelB B = load_panel_b<JW>(y, core0, 16 * p, c);
+      const float* const bl[1] = {L + blk_DI(p)};
+      float d[1][4];
+      blocks_mma<1>(d, bl, B);
+      __syncwarp();
+      blk_store<JW>(d[0], y, core0, 16 * p, c, false);
+      __syncwarp();
+    }
+    const PanelB B = load_panel_b<JW>(y, core0, 16 * p, c);
+    panel_updates<JW>(B, y, core0, c, p + 1, np, [&](int r) { return L + blk_F(np, r, p); });
+    __syncwarp();
+  }
+  for (int p = np - 1; p >= 0; --p) {
+    {
+      const PanelB B = load_panel_b<JW>(y, core0, 16 * p, c);
+      const float* const bl[1] = {L + blk_DIT(np, p)};
+      float d[1][4];
+      blocks_mma<1>(d, bl, B);
+      __syncwarp();
+      blk_store<JW>(d[0], y, core0, 16 * p, c, false);
+      __syncwarp();
+    }
+    const PanelB B = load_panel_b<JW>(y, core0, 16 * p, c);
+    panel_updates<JW>(B, y, core0, c, 0, p, [&](int r) { return L + blk_FT(np, p, r); });
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Star solves for k right-hand sides at once (k <= 32).  Each star is solved
 // by kp / JW warps (kp: k rounded up to a power of two; JW = min(kp, 4)), one
 // warp per block, each owning JW right-hand sides.  A warp streams the same
@@ -1070,7 +1273,8 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int groups, int ymax, 
                                                    const StarHdr* __restrict__ hdr, const char* __restrict__ recs,
                                                    const uint16_t* __restrict__ iperm,
                                                    const double* __restrict__ R, T* __restrict__ W,
-                                                   const int* done) {
+                                                   const int* done, const BatchHdr* __restrict__ bhdr,
+                                                   const char* __restrict__ brec, const float* __restrict__ coreL) {
   constexpr int QN = 32 / JW;    // slot groups of a window
   constexpr int SPL = WIN / QN;  // slots per lane (= JW)
   constexpr unsigned FULL = 0xffffffffu;
@@ -1092,9 +1296,24 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int groups, int ymax, 
   if (lane < (int)(sizeof(StarHdr) / 4)) ((int32_t*)h)[lane] = __ldg(((const int32_t*)(hdr + s)) + lane);
   __syncwarp();
   const int64_t wb = h->wbase;
-  const int n = h->n, nw = h->ne;
+  const int n = h->n;
+  int nw = h->ne, nfwd = h->ne, core0 = 0, cc = 0;
+  int64_t eoff = h->eoff, coff = 0;
+  const char* rbase = recs;
+  if (bhdr) {  // a dense block solved by panels: its own record stream
+    const BatchHdr bh = bhdr[s];
+    if (bh.c > 0) {
+      eoff = bh.eoff;
+      nw = bh.ne;
+      nfwd = bh.nfwd;
+      core0 = bh.core0;
+      cc = bh.c;
+      coff = bh.coff;
+      rbase = brec;
+    }
+  }
   const bool copier = lane * 16 < RB;
-  const char* src = recs + h->eoff * RB + lane * 16;
+  const char* src = rbase + eoff * RB + lane * 16;
   const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring);
   unsigned dst = ring_s + lane * 16;
   int F = 0;
@@ -1144,6 +1363,9 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int groups, int ymax, 
   const int s0 = q * SPL;
   T carry = T(0);  // the open segment's sum from the previous window (column j)
   for (int w = 0; w < nw; ++w) {
+    if constexpr (sizeof(T) == 4) {
+      if (cc > 0 && w == nfwd) core_panel_solve<JW>(coreL + coff, (float*)y, core0, cc);
+    }
     if (F == w + BRING) asm volatile("cp.async.wait_group %0;\n" ::"n"(BRING - 1) : "memory");
     else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncwarp();
@@ -1204,6 +1426,10 @@ __global__ void __launch_bounds__(32) k_star_batch(int k, int groups, int ymax, 
       ++F;
     }
   }
+  if constexpr (sizeof(T) == 4) {
+    if (cc > 0 && nfwd == nw) core_panel_solve<JW>(coreL + coff, (float*)y, core0, cc);
+  }
+  __syncwarp();
   if (act)
     for (int t = q; t < n; t += QN) W[(wb + t) * k + jj] = y[ip[t] * JW + j];
 }
@@ -1230,12 +1456,17 @@ static int star_batch_t(spnet_pc_s* pc, const double* R, int k, int kp, T* W, co
     attr_set[dev] = true;
   }
   const int groups = kp / JW;
+  const bool panels = sizeof(T) == 4 && pc->bhdr != nullptr;
   launch_pdl(k_star_batch<T, JW>, (unsigned)(pc->S * groups), 32, smem, s, k, groups, pc->max_star,
              (const int32_t*)pc->star_desc, (const StarHdr*)pc->shdr, (const char*)pc->srec,
-             (const uint16_t*)pc->iperm_star, R, W, done);
+             (const uint16_t*)pc->iperm_star, R, W, done, panels ? (const BatchHdr*)pc->bhdr : nullptr,
+             panels ? (const char*)pc->brec : nullptr, panels ? (const float*)pc->coreL : nullptr);
   return SPNET_OK;
 }
 
+// Right-hand sides per warp: batch_jw.  (Eight per warp, a whole MMA width, halves the
+// warps that replay a star's sparse records but doubles the shared memory of each: on
+// the 200000-fibre network with 32 right-hand sides 74 against 52 ms per solve.)
 template <class T>
 static int star_batch_p(spnet_pc_s* pc, const double* R, int k, int kp, T* W, const int* done, cudaStream_t s) {
   switch (batch_jw(kp)) {
@@ -1399,6 +1630,252 @@ int star_map_tune(spnet_pc_s* pc) {
   return SPNET_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Set-up of the panel solves (see "Dense blocks with many right-hand sides")
+// ---------------------------------------------------------------------------
+// entries of the pre-update level: the block's rows, their entries outside the
+// block (the first entries of each row) and a unit diagonal
+__device__ inline int64_t pre_entries(const uint32_t* rowptr, int core0, int n) {
+  const int64_t c = n - core0;
+  return (int64_t)(rowptr[n] - rowptr[core0]) - c * (c - 1) / 2 + c;
+}
+
+// records of the k-right-hand-side stream and floats of the block area, per star
+__global__ void k_panel_sizes(int S, const char* pool, const int64_t* star_off, const int32_t* star_core,
+                              int64_t* nrec, int64_t* nflt) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
+    const int c = star_core[s];
+    if (c < CORE_TC) {
+      nrec[s] = 0;
+      nflt[s] = 0;
+      continue;
+    }
+    const char* blob = pool + star_off[s];
+    const int32_t* h = (const int32_t*)blob;
+    const int n = h[0], nlev = h[1], nnz = h[2];
+    const BlobLayout B = blob_layout(n, nlev, nnz, 8);
+    const uint32_t* rowptr = (const uint32_t*)(blob + B.rowptr);
+    const uint32_t* colptr = (const uint32_t*)(blob + B.colptr);
+    const uint16_t* lvl = (const uint16_t*)(blob + B.lvl);
+    int64_t nw = level_windows(pre_entries(rowptr, n - c, n));
+    for (int l = 0; l < nlev - c; ++l)
+      nw += level_windows(level_entries(rowptr, lvl, l)) + level_windows(level_entries(colptr, lvl, l));
+    nrec[s] = nw;
+    nflt[s] = core_floats(c);
+  }
+}
+
+// the pre-update level: row v of the block gets y_v - sum over its columns u outside the
+// block of L_vu y_u (a unit diagonal, coefficients -L_vu)
+template <class T>
+__device__ void pack_pre_level(char* recs, int64_t wb, int lane, int core0, int n, const uint32_t* rowptr,
+                               const uint16_t* rowidx, const double* rowv, int vb) {
+  const int RB = rec_bytes(vb);
+  for (int v = core0 + lane; v < n; v += 32) {
+    const int64_t i = v - core0;
+    const uint32_t q1 = rowptr[v + 1] - (uint32_t)i;  // the block's own columns are the last i entries
+    int64_t j = (int64_t)(rowptr[v] - rowptr[core0]) - i * (i - 1) / 2 + i;
+    for (uint32_t q = rowptr[v]; q <= q1; ++q, ++j) {
+      const bool diag = q == q1;
+      char* rec = recs + (wb + j / WIN) * RB;
+      const int sl = (int)(j % WIN);
+      ((uint16_t*)(rec + REC_HDR))[sl] = diag ? (uint16_t)v : rowidx[q];
+      ((T*)(rec + REC_COEF))[sl] = (T)(diag ? 1.0 : -rowv[q]);
+      if (diag) atomicOr((unsigned*)rec, 1u << sl);
+    }
+  }
+  finish_level(recs, wb, lane, pre_entries(rowptr, core0, n), RB);
+}
+
+// warp per star: the k-right-hand-side header, and for a star with a panel-solved block its
+// records (forward sparse levels, pre-update level, backward sparse levels)
+template <class T>
+__global__ void k_panel_pack(int S, Mesh m, const char* __restrict__ pool, const int64_t* __restrict__ star_off,
+                             const int32_t* __restrict__ star_core, const int32_t* __restrict__ star_mesh,
+                             const int32_t* __restrict__ elem_ptr, const StarHdr* __restrict__ hdr,
+                             const int64_t* __restrict__ boff, const int64_t* __restrict__ coff,
+                             BatchHdr* __restrict__ bhdr, char* __restrict__ recs, int patch,
+                             const double* __restrict__ q1w, int64_t N) {
+  const int lane = threadIdx.x & 31;
+  const int vb = (int)sizeof(T);
+  const int RB = rec_bytes(vb);
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nwarps) {
+    const int c = star_core[s];
+    if (c < CORE_TC) {
+      if (lane == 0) {
+        BatchHdr b;
+        b.eoff = hdr[s].eoff;
+        b.coff = -1;
+        b.nfwd = hdr[s].ne;
+        b.ne = hdr[s].ne;
+        b.core0 = hdr[s].n;
+        b.c = 0;
+        bhdr[s] = b;
+      }
+      continue;
+    }
+    const char* blob = pool + star_off[s];
+    const int32_t* hb = (const int32_t*)blob;
+    const int n = hb[0], nlev = hb[1], nnz = hb[2];
+    const BlobLayout B = blob_layout(n, nlev, nnz, 8);
+    const uint32_t* rowptr = (const uint32_t*)(blob + B.rowptr);
+    const uint32_t* colptr = (const uint32_t*)(blob + B.colptr);
+    const uint16_t* lvl = (const uint16_t*)(blob + B.lvl);
+    const uint16_t* rowidx = (const uint16_t*)(blob + B.rowidx);
+    const uint16_t* colidx = (const uint16_t*)(blob + B.colidx);
+    const double* rowv = (const double*)(blob + B.v64);
+    const double* colv = rowv + nnz;
+    const double* invd = colv + nnz;
+    const int core0 = n - c, lnc = nlev - c;
+    const int64_t r0 = boff[s], r1 = boff[s + 1];
+    int4* z4 = (int4*)(recs + r0 * RB);
+    const int64_t n16 = (r1 - r0) * RB / 16;
+    for (int64_t q = lane; q < n16; q += 32) z4[q] = make_int4(0, 0, 0, 0);
+    __syncwarp();
+    __threadfence_block();
+    SupportTest sup;  // as in the one-vector stream
+    sup.patch = patch;
+    sup.se = star_elems(m, star_mesh[s], elem_ptr);
+    sup.elem_ptr = elem_ptr;
+    sup.q1w = q1w;
+    sup.N = N;
+    sup.perm = (const uint16_t*)(blob + B.perm);
+    int64_t w = r0;
+    for (int l = 0; l < lnc; ++l) {
+      pack_level<T>(recs, w, lane, lvl[l], lvl[l + 1], rowptr, rowidx, rowv, invd, vb, sup);
+      w += level_windows(level_entries(rowptr, lvl, l));
+    }
+    pack_pre_level<T>(recs, w, lane, core0, n, rowptr, rowidx, rowv, vb);
+    w += level_windows(pre_entries(rowptr, core0, n));
+    const int nfwd = (int)(w - r0);
+    for (int l = lnc - 1; l >= 0; --l) {
+      pack_level<T>(recs, w, lane, lvl[l], lvl[l + 1], colptr, colidx, colv, invd, vb, sup);
+      w += level_windows(level_entries(colptr, lvl, l));
+    }
+    if (lane == 0) {
+      BatchHdr b;
+      b.eoff = r0;
+      b.coff = coff[s];
+      b.nfwd = nfwd;
+      b.ne = (int32_t)(r1 - r0);
+      b.core0 = core0;
+      b.c = c;
+      bhdr[s] = b;
+    }
+  }
+}
+
+// entry (a, b), a > b, of the block L_cc (local indices): row core0 + a lists the block's
+// columns 0..a-1 as its last a entries
+__device__ __forceinline__ double core_L(const uint32_t* rowptr, const double* rowv, int core0, int a, int b) {
+  return rowv[rowptr[core0 + a + 1] - a + b];
+}
+
+// (inverse of the diagonal tile of panel p)[i][j], local i, j in 0..15 (zero past c):
+// forward substitution on column j of the tile, in FP64
+__device__ double diag_tile_inverse(const uint32_t* rowptr, const double* rowv, const double* invd, int core0,
+                                    int c, int p, int i, int j) {
+  const int r0 = 16 * p;
+  if (i < j || r0 + i >= c || r0 + j >= c) return 0.0;
+  double x[16];
+  x[j] = invd[core0 + r0 + j];
+  for (int m = j + 1; m <= i; ++m) {
+    double acc = 0.0;
+    for (int q = j; q < m; ++q) acc += core_L(rowptr, rowv, core0, r0 + m, r0 + q) * x[q];
+    x[m] = -acc * invd[core0 + r0 + m];
+  }
+  return x[i];
+}
+
+// block per star with a panel-solved block: its block area in coreL (FP32)
+__global__ void __launch_bounds__(256) k_core_pack(int S, const char* __restrict__ pool,
+                                                   const int64_t* __restrict__ star_off,
+                                                   const int32_t* __restrict__ star_core,
+                                                   const int64_t* __restrict__ coff, float* __restrict__ coreL) {
+  for (int s = blockIdx.x; s < S; s += gridDim.x) {
+    const int c = star_core[s];
+    if (c < CORE_TC) continue;
+    const char* blob = pool + star_off[s];
+    const int32_t* hb = (const int32_t*)blob;
+    const int n = hb[0], nlev = hb[1], nnz = hb[2];
+    const BlobLayout B = blob_layout(n, nlev, nnz, 8);
+    const uint32_t* rowptr = (const uint32_t*)(blob + B.rowptr);
+    const double* rowv = (const double*)(blob + B.v64);
+    const double* invd = rowv + 2ll * nnz;
+    const int core0 = n - c, np = core_panels(c);
+    float* out = coreL + coff[s];
+    const int64_t total = core_floats(c);
+    for (int64_t f = threadIdx.x; f < total; f += blockDim.x) {
+      const int64_t blk = f >> 8;
+      const int in = (int)(f & 255);
+      const int kh = in >> 7, ln = (in >> 2) & 31, e = in & 3;
+      const int li = (ln >> 2) + ((e & 1) << 3);       // row inside the 16 x 16 block
+      const int lj = kh * 8 + (ln & 3) + ((e >> 1) << 2);  // column inside it
+      double v = 0.0;
+      if (blk < np) {  // DI(p)
+        v = diag_tile_inverse(rowptr, rowv, invd, core0, c, (int)blk, li, lj);
+      } else if (blk < 2 * np) {  // DIT(p)
+        v = diag_tile_inverse(rowptr, rowv, invd, core0, c, (int)(blk - np), lj, li);
+      } else {
+        int64_t t = blk - 2 * np;
+        const int64_t half = (int64_t)np * (np - 1) / 2;
+        const bool tr = t >= half;
+        if (tr) t -= half;
+        int r = 1;
+        while ((int64_t)r * (r + 1) / 2 <= t) ++r;  // t = r (r - 1) / 2 + q
+        const int q = (int)(t - (int64_t)r * (r - 1) / 2);
+        // F(r, q)[li][lj] = L_cc[16 r + li][16 q + lj]; FT(r, q)[li][lj] = L_cc[16 r + lj][16 q + li]
+        const int a = tr ? 16 * r + lj : 16 * r + li;
+        const int b = tr ? 16 * q + li : 16 * q + lj;
+        if (a < c && b < c) v = core_L(rowptr, rowv, core0, a, b);
+      }
+      out[f] = (float)v;
+    }
+  }
+}
+
+// the k-right-hand-side stream and block areas (FP32 solves with batch_rhs >= 2)
+static int pack_panels(spnet_pc_s* pc, DevArena& tmp) {
+  cudaStream_t s = pc->op->stream;
+  const int S = pc->S;
+  std::vector<int32_t> core(S);
+  SPNET_CUDA_TRY(cudaMemcpyAsync(core.data(), pc->star_core, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, s));
+  SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+  int dense = 0;
+  for (int v : core) dense += v >= CORE_TC;
+  pc->panel_stars = dense;
+  if (dense == 0) return SPNET_OK;
+  int64_t *nrec = nullptr, *nflt = nullptr, *boff = nullptr, *coff = nullptr;
+  SPNET_TRY(tmp.get(&nrec, S + 1));
+  SPNET_TRY(tmp.get(&nflt, S + 1));
+  SPNET_TRY(tmp.get(&boff, S + 1));
+  SPNET_TRY(tmp.get(&coff, S + 1));
+  note_launch();
+  k_panel_sizes<<<(S + 255) / 256, 256, 0, s>>>(S, pc->pool, pc->star_off, pc->star_core, nrec, nflt);
+  SPNET_TRY(scan_exclusive64(nrec, boff, S, s, tmp));
+  SPNET_TRY(scan_exclusive64(nflt, coff, S, s, tmp));
+  int64_t tr = 0, tf = 0;
+  SPNET_CUDA_TRY(cudaMemcpyAsync(&tr, boff + S, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SPNET_CUDA_TRY(cudaMemcpyAsync(&tf, coff + S, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+  const int RB = rec_bytes(4);
+  SPNET_TRY(pc->mem.alloc(&pc->bhdr, (size_t)S * sizeof(BatchHdr)));
+  SPNET_TRY(pc->mem.get(&pc->brec, (tr > 0 ? tr : 1) * RB));
+  SPNET_TRY(pc->mem.get(&pc->coreL, tf > 0 ? tf : 1));
+  pc->panel_bytes = tr * RB + tf * 4;
+  note_launch();
+  k_panel_pack<float><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_core,
+                                                  pc->star_mesh, pc->elem_ptr, (const StarHdr*)pc->shdr, boff, coff,
+                                                  (BatchHdr*)pc->bhdr, pc->brec, pc->patch, pc->q1w, pc->N);
+  note_launch();
+  const int grid = S < 8 * num_sms() ? S : 8 * num_sms();
+  k_core_pack<<<grid, 256, 0, s>>>(S, pc->pool, pc->star_off, pc->star_core, coff, pc->coreL);
+  SPNET_CUDA_TRY(cudaGetLastError());
+  SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+  return SPNET_OK;
+}
+
 // headers, inverse permutations and entry streams of all stars
 static int pack_streams(spnet_pc_s* pc, DevArena& tmp, const std::vector<int32_t>& lev,
                         const std::vector<int32_t>& nz) {
@@ -1526,6 +2003,7 @@ int pc_factor_stars(spnet_pc_s* pc) {
   SPNET_TRY(pc->mem.get(&pc->star_off, pc->S));
   SPNET_TRY(pc->mem.get(&pc->star_lev, pc->S));
   SPNET_TRY(pc->mem.get(&pc->star_nnz, pc->S));
+  SPNET_TRY(pc->mem.get(&pc->star_core, pc->S));
   // pool estimate: per dof 28 bytes + ~4 factor entries of 32 bytes, per star 64
   int64_t cap = pc->sum_s * (28 + 4 * 32) + (int64_t)pc->S * 64 + (1 << 20);
   int* flags = pc->op->dflags;
@@ -1558,6 +2036,7 @@ int pc_factor_stars(spnet_pc_s* pc) {
     A.star_off = pc->star_off;
     A.star_lev = pc->star_lev;
     A.star_nnz = pc->star_nnz;
+    A.star_core = pc->star_core;
     A.flags = flags;
     A.next = counters;
     A.vbytes = 8;  // the set-up blobs keep FP64 values; the solve sections are packed later
@@ -1614,8 +2093,10 @@ int pc_factor_stars(spnet_pc_s* pc) {
     pc->total_levels += lev[i];
     pc->max_levels = lev[i] > pc->max_levels ? lev[i] : pc->max_levels;
   }
-  // the solve streams; the set-up blobs are released
+  // the solve streams (and the panel solves of dense blocks for FP32 blocks of right-hand
+  // sides); the set-up blobs are released
   SPNET_TRY(pack_streams(pc, tmp, lev, nz));
+  if (pc->precision == SPNET_PREC_MIXED && pc->batch_rhs >= 2 && pc->panels) SPNET_TRY(pack_panels(pc, tmp));
   pc->mem.release(pc->pool);
   pc->pool = nullptr;
   return SPNET_OK;

@@ -28,7 +28,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 STARS_INTERIOR, STARS_ALL = 0, 1
 PATCH_ELEMENT, PATCH_SUPPORT = 0, 1
 EXPORT_ELEMENTS, EXPORT_Q1, EXPORT_COARSE_MAP, EXPORT_STAR_SIZES = 0, 1, 2, 3
-EXPORT_STAR_MESH, EXPORT_A0, EXPORT_STAR_LEVELS = 4, 5, 6
+EXPORT_STAR_MESH, EXPORT_A0, EXPORT_STAR_LEVELS, EXPORT_STAR_CORE = 4, 5, 6, 7
 
 EXPORTED = [
     "spnet_assemble", "build_network_operator", "setup_preconditioner", "pcg_solve",
@@ -53,7 +53,7 @@ class SpnetError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("star_set", C.c_int), ("flexible", C.c_int),
                 ("max_restarts", C.c_int), ("batch_rhs", C.c_int), ("star_map", C.c_int),
-                ("patch", C.c_int), ("reserved", C.c_int * 9)]
+                ("patch", C.c_int), ("no_panels", C.c_int), ("reserved", C.c_int * 8)]
 
 
 class Request(C.Structure):
@@ -90,7 +90,7 @@ class PcInfo(C.Structure):
                 ("precision", C.c_int), ("star_set", C.c_int), ("flexible", C.c_int),
                 ("setup_ms", C.c_double), ("device_bytes", C.c_int64), ("star_stream_bytes", C.c_int64),
                 ("star_warps_per_block", C.c_int64), ("coarse_dropped", C.c_int64),
-                ("reserved", C.c_int64 * 2)]
+                ("panel_stars", C.c_int64), ("reserved", C.c_int64 * 1)]
 
 
 _lib = None
@@ -333,7 +333,7 @@ class Preconditioner:
     """setup_preconditioner: the two-level additive Schwarz preconditioner."""
 
     def __init__(self, op: Operator, H, gamma_faces, precision=PREC_MIXED, star_set=STARS_INTERIOR,
-                 flexible=-1, max_restarts=2, batch_rhs=1, star_map=0, patch=PATCH_ELEMENT):
+                 flexible=-1, max_restarts=2, batch_rhs=1, star_map=0, patch=PATCH_ELEMENT, panels=True):
         self._lib = op._lib
         self.op = op
         self.handle = C.c_void_p()
@@ -341,6 +341,7 @@ class Preconditioner:
         o.precision, o.star_set, o.flexible, o.max_restarts = precision, star_set, flexible, max_restarts
         o.batch_rhs = batch_rhs
         o.star_map = star_map
+        o.no_panels = 0 if panels else 1
         o.patch = patch if isinstance(patch, int) else (PATCH_SUPPORT if patch == "support"
                                                          else PATCH_ELEMENT)
         gf = (C.c_int * 3)(*(list(gamma_faces) + [0, 0, 0])[:3])
@@ -413,6 +414,7 @@ class Preconditioner:
             EXPORT_STAR_SIZES: (np.int32, (i.n_stars,)),
             EXPORT_STAR_MESH: (np.int32, (i.n_stars,)),
             EXPORT_STAR_LEVELS: (np.int32, (i.n_stars,)),
+            EXPORT_STAR_CORE: (np.int32, (i.n_stars,)),
             EXPORT_A0: (np.float64, (i.m0, i.m0)),
         }[what]
         out = np.zeros(spec[1], dtype=spec[0])
