@@ -98,3 +98,33 @@ def test_a_column_does_not_depend_on_its_neighbours():
     Zc = pc.apply_batch(R[[7, 8, 0]], which=2)  # 3 columns: the same padded width 4
     np.testing.assert_array_equal(Za[0], Zb[1])
     np.testing.assert_array_equal(Za[0], Zc[2])
+
+
+@functools.lru_cache(maxsize=None)
+def downscaled_large():
+    # the 400000-fibre workload's geometry scaled by 4 into the unit cube (fibres of length
+    # 0.4, contacts below 0.016, 400000 / 4^3 = 6250 fibres, H = 4/32): a quarter-size cube of
+    # that network, 139k nodes, 343 stars of ~2400 dofs whose eliminations end in dense blocks
+    net = nw.fiber_network_3d(6250, 0.4, 0.016, nw.config_seed(5, 1))
+    p = nw.scalar_band_problem(net, 1.0 / 8, name="3d-6250fib-L0.4-H8")
+    return p, OracleSolver(p, local="sparse")
+
+
+def test_downscaled_large_network_32_rhs():
+    p, o = downscaled_large()
+    op = spnet.Operator.from_problem(p)
+    pc = spnet.Preconditioner(op, p.H, p.gamma_faces, precision=spnet.PREC_MIXED, batch_rhs=32)
+    assert pc.info.panel_stars > 0
+    R = np.random.default_rng(80).standard_normal((32, o.A.shape[0]))
+    Zs = pc.apply_batch(R, which=2)
+    Z = pc.apply_batch(R)
+    for j in (0, 31):
+        check_star_term(o, R[j], Zs[j], "mixed")
+        assert rel(Z[j], o.B.apply(R[j])) <= 2e-4
+    rng = np.random.default_rng(81)
+    F = rng.uniform(0.0, 1.0, size=(32, p.n_dof))
+    G = np.tile(p.dirichlet_vals, (32, 1))
+    U, st = spnet.pcg_solve(op, pc, F, G, rtol=1e-8)
+    assert all(s.converged and s.relres <= 1e-8 for s in st)
+    ref = o.solve(f=F[5], g=G[5], rtol=1e-8, flexible=True)
+    assert rel(U[5], ref.u) <= 1e-6
