@@ -138,7 +138,9 @@ typedef struct {
                                    of earlier ones (see setup_preconditioner) */
   int64_t panel_stars;          /* stars whose dense block the k-right-hand-side solve runs by
                                    panels on tensor cores (see spnet_options.no_panels) */
-  int64_t reserved[1];
+  int64_t tuned;                /* the tuner's other choices: SpMV lanes per row
+                                   + 256 * right-hand sides per warp of the batched star solve
+                                   (0: chosen by the block width) */
 } spnet_pc_info;
 
 /* spnet_assemble -- assemble K on all n_nodes*ndof dofs from an edge list.
@@ -296,6 +298,25 @@ int spnet_server_estimate(const spnet_request* request, int64_t* bytes);
 int spnet_server_budget(spnet_server_t server, int64_t* bytes);
 /* spnet_server_destroy -- finish every queued request, stop the workers, free the server. */
 int spnet_server_destroy(spnet_server_t server);
+
+/* The tuner.  setup_preconditioner times, once per device and size class, the warps per
+ * block of the one-vector star solve (unless spnet_options.star_map fixes it), the lanes
+ * per row of the SpMV (operators of 65536 free dofs or more) and the right-hand sides per
+ * warp of the batched star solve (batch_rhs >= 4), on the preconditioner's own data, and
+ * keeps the choices in a process-wide cache.  The last two change the order of sums, so
+ * every set-up of a class uses the one measured value (a set-up meeting a class being
+ * measured waits for it).  The cache can be saved and loaded, so that another process takes
+ * the same choices without measuring: a text file of lines
+ * "device<TAB>kind<TAB>c0,c1,c2,c3<TAB>value" (device: name, SM count, compute capability).
+ * spnet_tune_cache_load  add the lines of a file to the cache.  Errors: BAD_INPUT (unreadable
+ *                        file or malformed line; nothing is added then).
+ * spnet_tune_cache_save  write the cache's measured entries (all devices) to a file.
+ * spnet_tune_cache_clear forget every measured entry and the counts.
+ * spnet_tune_counts      choices measured, and choices taken from the cache, since the clear. */
+int spnet_tune_cache_load(const char* path);
+int spnet_tune_cache_save(const char* path);
+int spnet_tune_cache_clear(void);
+int spnet_tune_counts(int64_t* measured, int64_t* reused);
 
 /* spnet_last_error -- copy the calling thread's last error message (NUL-terminated). */
 int spnet_last_error(char* buf, size_t len);

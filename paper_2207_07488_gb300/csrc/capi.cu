@@ -90,11 +90,7 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
   pc->G = 4 * num_sms();
   pc->PG = 16 * num_sms();
   pc->spmv_lanes = choose_spmv_lanes(pc->K);
-  {  // one row group per warp in a single pass, capped at 64 blocks per SM
-    const int64_t want = (pc->N * pc->spmv_lanes + 255) / 256;
-    const int64_t cap = 64ll * num_sms();
-    pc->spmv_blocks = (int)(want < 1 ? 1 : want > cap ? cap : want);
-  }
+  pc->spmv_blocks = spmv_grid(pc, pc->spmv_lanes);
   // coarse space: Galerkin matrix and its inverse
   if (pc->m0 > 0) {
     double* A0 = nullptr;
@@ -115,12 +111,14 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
       (rc = pc->mem.get(&pc->vtmp, N)) || (rc = pc->mem.alloc(&pc->w, (size_t)(pc->sum_s > 0 ? pc->sum_s : 1) * (pc->precision == SPNET_PREC_FP64 ? 8 : 4))) ||
       (rc = pc->mem.get(&pc->rc, pc->m0 > 0 ? pc->m0 : 1)) ||
       (rc = pc->mem.get(&pc->zc, pc->m0 > 0 ? pc->m0 : 1)) ||
-      (rc = pc->mem.get(&pc->partial, 5 * pc->PG)) || (rc = pc->mem.get(&pc->pspmv, pc->spmv_blocks)) ||
+      (rc = pc->mem.get(&pc->partial, 5 * pc->PG)) || (rc = pc->mem.get(&pc->pspmv, 64 * num_sms())) ||
       (rc = pc->mem.get(&pc->scal, 1)) ||
       (rc = pc->mem.get(&pc->epart, (size_t)pc->n_elem * pc->nc * pc->ndof)))
     return bail(rc);
   cudaMemsetAsync(pc->scal, 0, sizeof(Scal), s);
+  if ((rc = spmv_lanes_tune(pc))) return bail(rc);
   if ((rc = star_map_tune(pc))) return bail(rc);
+  if ((rc = batch_jw_tune(pc))) return bail(rc);
   cudaEventRecord(e1, s);
   if (cudaEventSynchronize(e1) != cudaSuccess) return bail(fail(SPNET_ERR_CUDA, "setup_preconditioner: device error"));
   if (cudaGetLastError() != cudaSuccess) return bail(fail(SPNET_ERR_CUDA, "setup_preconditioner: launch error"));
@@ -258,6 +256,7 @@ int spnet_pc_get_info(spnet_pc_t pc, spnet_pc_info* info) {
   info->star_warps_per_block = pc->solve_wpb;
   info->coarse_dropped = pc->coarse_dropped;
   info->panel_stars = pc->panel_stars;
+  info->tuned = pc->spmv_lanes + 256ll * pc->batch_jw;
   return SPNET_OK;
 }
 

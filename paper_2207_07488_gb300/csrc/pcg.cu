@@ -409,6 +409,63 @@ static void launch_update(spnet_pc_s* pc, double* x, const double* r, double* ro
   else launch_update_c<float>(pc, pc->xi32, x, r, rout, p, q, sc, mode, s);
 }
 
+// the SpMV's grid for its lanes per row: one row group per warp in a single pass, capped
+// at 64 blocks per SM
+int spmv_grid(const spnet_pc_s* pc, int lanes) {
+  const int64_t want = (pc->N * lanes + 255) / 256;
+  const int64_t cap = 64ll * num_sms();
+  return (int)(want < 1 ? 1 : want > cap ? cap : want);
+}
+
+// Lanes per row of the SpMV, timed once per size class (half-octaves of the rows and of
+// twice the mean row length, dofs per node) among half, once and twice the value the mean
+// row length suggests; another value must beat that one by 5 %.  The choice changes the
+// order of a row's sum, so every set-up of a class takes the one measured value.
+int spmv_lanes_tune(spnet_pc_s* pc) {
+  const int h = pc->spmv_lanes;
+  if (pc->N < 65536) return SPNET_OK;  // a few microseconds whatever the choice
+  const TuneClass key{{half_octave((double)pc->N), half_octave(2.0 * pc->K.nnz / pc->N), pc->ndof, 0}};
+  int v = 0;
+  if (tune_begin(TUNE_SPMV_LANES, key, &v)) {
+    pc->spmv_lanes = v;
+    pc->spmv_blocks = spmv_grid(pc, v);
+    return SPNET_OK;
+  }
+  cudaStream_t s = pc->op->stream;
+  int best = h, rc = SPNET_OK;
+  float best_ms = 0.0f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+      cudaMemsetAsync(pc->x, 0, sizeof(double) * pc->N, s) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    tune_end(TUNE_SPMV_LANES, key, 0);
+    return fail(SPNET_ERR_CUDA, "setup_preconditioner: timing the SpMV failed");
+  }
+  for (int lanes : {h, h / 2, 2 * h}) {
+    if (lanes < 1 || lanes > 32) continue;
+    launch_spmv(pc->K, pc->x, pc->q, nullptr, pc->G, lanes, nullptr, s);  // warm-up
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 5; ++rep) launch_spmv(pc->K, pc->x, pc->q, nullptr, pc->G, lanes, nullptr, s);
+    cudaEventRecord(e1, s);
+    float ms = 0.0f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = fail(SPNET_ERR_CUDA, "setup_preconditioner: timing the SpMV failed");
+      break;
+    }
+    if (lanes == h || ms < 0.95f * best_ms) {
+      best = lanes;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  tune_end(TUNE_SPMV_LANES, key, rc == SPNET_OK ? best : 0);
+  if (rc != SPNET_OK) return rc;
+  pc->spmv_lanes = best;
+  pc->spmv_blocks = spmv_grid(pc, best);
+  return SPNET_OK;
+}
+
 static void launch_spmv_dir(spnet_pc_s* pc, cudaStream_t s) {
   note_launch();
   ProfScope ps(KID_SPMV, s);

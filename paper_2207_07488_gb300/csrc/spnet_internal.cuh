@@ -89,6 +89,24 @@ struct Scal {
 };
 
 }  // namespace spnet
+struct spnet_pc_s;
+namespace spnet {
+// the tuner's cache (tune.cu): choices per device, kind and size class
+enum : int { TUNE_STAR_MAP = 0, TUNE_SPMV_LANES = 1, TUNE_BATCH_JW = 2, TUNE_KINDS = 3 };
+struct TuneClass {
+  int c[4];
+};
+// 1 and *value: the class's choice is known; 0: the caller measures it and reports it with
+// tune_end (value 0: failed).  Waits while another set-up measures the class.
+int tune_begin(int kind, const TuneClass& c, int* value);
+void tune_end(int kind, const TuneClass& c, int value);
+int tune_peek(int kind, const TuneClass& c, int* value);  // 1 and *value if known; never waits
+int spmv_grid(const spnet_pc_s* pc, int lanes);
+int spmv_lanes_tune(spnet_pc_s* pc);
+int batch_jw_tune(spnet_pc_s* pc);
+int half_octave(double x);
+
+}  // namespace spnet
 
 struct spnet_op_s {
   int dim = 0, ndof = 0;
@@ -191,6 +209,7 @@ struct spnet_pc_s {
   int G = 0;         // reduction grid
   int PG = 0;        // stride of the partial-sum slots (max blocks of a reducing kernel)
   int spmv_lanes = 1;
+  int batch_jw = 0;                // right-hand sides per warp of the batched star solve (0: by k)
   int spmv_blocks = 1;             // grid of the SpMV of an iteration (one pass over the rows)
   double* pspmv = nullptr;         // [spmv_blocks] its partial dot products
   double setup_ms = 0;

@@ -1469,7 +1469,9 @@ static int star_batch_t(spnet_pc_s* pc, const double* R, int k, int kp, T* W, co
 // the 200000-fibre network with 32 right-hand sides 74 against 52 ms per solve.)
 template <class T>
 static int star_batch_p(spnet_pc_s* pc, const double* R, int k, int kp, T* W, const int* done, cudaStream_t s) {
-  switch (batch_jw(kp)) {
+  int jw = batch_jw(kp);
+  if (pc->batch_jw > 0 && pc->batch_jw < jw) jw = pc->batch_jw;  // the tuned width
+  switch (jw) {
     case 1: return star_batch_t<T, 1>(pc, R, k, kp, W, done, s);
     case 2: return star_batch_t<T, 2>(pc, R, k, kp, W, done, s);
     default: return star_batch_t<T, 4>(pc, R, k, kp, W, done, s);
@@ -1544,29 +1546,20 @@ static int build_star_map(spnet_pc_s* pc, int wpb) {
   return SPNET_OK;
 }
 
-// Size classes of the star solve (half-octaves of the star count, the largest
-// star and the stream bytes per star) and the warps per block timed best for
-// each, once per process and device.
-static std::mutex map_mu;
-static std::map<std::tuple<int, int, int, int, int>, int> map_cache;
-
-static int half_octave(double x) { return x <= 1.0 ? 0 : (int)std::floor(2.0 * std::log2(x)); }
-
-static std::tuple<int, int, int, int, int> map_key(const spnet_pc_s* pc) {
-  int dev = 0;
-  cudaGetDevice(&dev);
+// Size class of the star solve: the solve precision, half-octaves of the star count, the
+// largest star and the stream bytes per star (the tuner's cache keeps the warps per block
+// timed best for each, per device).
+static TuneClass map_class(const spnet_pc_s* pc) {
   const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
-  return std::make_tuple(dev, vb, half_octave(pc->S), half_octave(pc->max_star),
-                         half_octave((double)pc->stream_bytes / pc->S));
+  return TuneClass{{vb, half_octave(pc->S), half_octave(pc->max_star), half_octave((double)pc->stream_bytes / pc->S)}};
 }
 
 // the mapping to build first: the fixed one, the one cached for the size class, else the widest
 static int initial_wpb(const spnet_pc_s* pc, int wmax) {
   if (pc->star_map > 0) return pc->star_map < wmax ? pc->star_map : wmax;
-  std::lock_guard<std::mutex> lk(map_mu);
-  auto it = map_cache.find(map_key(pc));
-  if (it == map_cache.end() || it->second < 1) return wmax;  // unknown, or being tuned
-  return it->second < wmax ? it->second : wmax;
+  int v = 0;
+  if (pc->S == 0 || !tune_peek(TUNE_STAR_MAP, map_class(pc), &v)) return wmax;
+  return v < wmax ? v : wmax;
 }
 
 int star_map_tune(spnet_pc_s* pc) {
@@ -1574,16 +1567,14 @@ int star_map_tune(spnet_pc_s* pc) {
   // fewer stars than four per SM: one wave holds them whatever the mapping
   if (pc->S < 4 * num_sms()) return SPNET_OK;
   const int wmax = pc->solve_wpb_max;
-  const auto key = map_key(pc);
+  const TuneClass key = map_class(pc);
   {
-    std::lock_guard<std::mutex> lk(map_mu);
-    auto it = map_cache.find(key);
-    if (it != map_cache.end()) {  // known (or being tuned by another set-up: keep the widest)
-      const int w = it->second < 1 ? pc->solve_wpb : it->second < wmax ? it->second : wmax;
+    int v = 0;
+    if (tune_begin(TUNE_STAR_MAP, key, &v)) {  // known
+      const int w = v < wmax ? v : wmax;
       if (w != pc->solve_wpb) SPNET_TRY(build_star_map(pc, w));
       return SPNET_OK;
     }
-    map_cache[key] = 0;  // this set-up tunes the class; the others do not wait for it
   }
   // candidates: the most warps per block the shared memory holds, half and a quarter of it
   std::vector<int> cand;
@@ -1620,14 +1611,75 @@ int star_map_tune(spnet_pc_s* pc) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  {
-    std::lock_guard<std::mutex> lk(map_mu);
-    if (rc != SPNET_OK) map_cache.erase(key);
-    else map_cache[key] = best;
-  }
+  tune_end(TUNE_STAR_MAP, key, rc == SPNET_OK ? best : 0);
   if (rc != SPNET_OK) return rc;
   if (best != pc->solve_wpb) SPNET_TRY(build_star_map(pc, best));
   return SPNET_OK;
+}
+
+// Right-hand sides per warp of the batched star solve (2 or 4), timed once per size class
+// (precision and block width, half-octaves of the star count and the largest star, whether
+// dense blocks are solved by panels) on the preconditioner's own stars, for the block
+// width the preconditioner steps (batch_rhs).  The choice changes the order of the sums,
+// so every set-up of a class takes the one measured value.
+int batch_jw_tune(spnet_pc_s* pc) {
+  pc->batch_jw = 0;
+  const int k = pc->batch_rhs < 32 ? pc->batch_rhs : 32;
+  if (pc->S == 0 || k < 4 || star_batch_max_k(pc) < 4) return SPNET_OK;
+  const int kp = k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
+  const int vb = pc->precision == SPNET_PREC_FP64 ? 8 : 4;
+  const TuneClass key{{vb * 64 + kp, half_octave(pc->S), half_octave(pc->max_star), pc->panel_stars > 0 ? 1 : 0}};
+  int v = 0;
+  if (tune_begin(TUNE_BATCH_JW, key, &v)) {
+    pc->batch_jw = v;
+    return SPNET_OK;
+  }
+  cudaStream_t s = pc->op->stream;
+  DevArena tmp;
+  tmp.stream = s;
+  struct Guard {
+    DevArena& a;
+    ~Guard() { a.free_all(); }
+  } guard{tmp};
+  const int64_t rbytes = 8ll * pc->N * k, wbytes = (int64_t)vb * pc->sum_s * k;
+  int best = 4, rc = SPNET_OK;
+  if (rbytes + wbytes > (2ll << 30)) {  // too large to time on the side: the default
+    tune_end(TUNE_BATCH_JW, key, best);
+    pc->batch_jw = best;
+    return SPNET_OK;
+  }
+  double* R = nullptr;
+  void* W = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if ((rc = tmp.get(&R, (size_t)pc->N * k)) || (rc = tmp.alloc(&W, (size_t)wbytes)) ||
+      cudaMemsetAsync(R, 0, (size_t)rbytes, s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    tune_end(TUNE_BATCH_JW, key, 0);
+    return rc ? rc : fail(SPNET_ERR_CUDA, "setup_preconditioner: timing the batched star solve failed");
+  }
+  float best_ms = 0.0f;
+  for (int jw : {4, 2}) {
+    pc->batch_jw = jw;
+    rc = launch_star_batch(pc, R, k, W, nullptr, s);  // warm-up
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 2 && rc == SPNET_OK; ++rep) rc = launch_star_batch(pc, R, k, W, nullptr, s);
+    cudaEventRecord(e1, s);
+    float ms = 0.0f;
+    if (rc != SPNET_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      if (rc == SPNET_OK) rc = fail(SPNET_ERR_CUDA, "setup_preconditioner: timing the batched star solve failed");
+      break;
+    }
+    if (jw == 4 || ms < 0.95f * best_ms) {  // the narrower one must beat four per warp by 5 %
+      best = jw;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  tune_end(TUNE_BATCH_JW, key, rc == SPNET_OK ? best : 0);
+  pc->batch_jw = rc == SPNET_OK ? best : 0;
+  return rc;
 }
 
 // ---------------------------------------------------------------------------

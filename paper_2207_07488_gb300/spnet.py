@@ -38,7 +38,8 @@ EXPORTED = [
     "spnet_profile_enable", "spnet_profile_read", "spnet_profile_reset", "spnet_pc_restrict_static",
     "spnet_server_create", "spnet_server_submit", "spnet_server_wait", "spnet_server_destroy",
     "spnet_pc_apply_batch", "spnet_server_poll", "spnet_server_cancel", "spnet_server_estimate",
-    "spnet_server_budget",
+    "spnet_server_budget", "spnet_tune_cache_load", "spnet_tune_cache_save", "spnet_tune_cache_clear",
+    "spnet_tune_counts",
 ]
 KERNELS = ["spmv", "update", "restrict", "stars", "coarse", "combine", "direction",
            "star_symbolic", "star_numeric", "sweep", "galerkin"]
@@ -90,7 +91,7 @@ class PcInfo(C.Structure):
                 ("precision", C.c_int), ("star_set", C.c_int), ("flexible", C.c_int),
                 ("setup_ms", C.c_double), ("device_bytes", C.c_int64), ("star_stream_bytes", C.c_int64),
                 ("star_warps_per_block", C.c_int64), ("coarse_dropped", C.c_int64),
-                ("panel_stars", C.c_int64), ("reserved", C.c_int64 * 1)]
+                ("panel_stars", C.c_int64), ("tuned", C.c_int64)]
 
 
 _lib = None
@@ -139,6 +140,10 @@ def load(build_if_missing: bool = True):
     lib.spnet_server_cancel.argtypes = [P, i64, C.POINTER(C.c_int)]
     lib.spnet_server_estimate.argtypes = [C.POINTER(Request), C.POINTER(i64)]
     lib.spnet_server_budget.argtypes = [P, C.POINTER(i64)]
+    lib.spnet_tune_cache_load.argtypes = [C.c_char_p]
+    lib.spnet_tune_cache_save.argtypes = [C.c_char_p]
+    lib.spnet_tune_cache_clear.argtypes = []
+    lib.spnet_tune_counts.argtypes = [C.POINTER(i64), C.POINTER(i64)]
     lib.spnet_server_destroy.argtypes = [P]
     for name in EXPORTED:
         getattr(lib, name).restype = C.c_int
@@ -175,6 +180,27 @@ def profile_read() -> dict:
         _check(lib.spnet_profile_read(k, C.byref(n), C.byref(ms)))
         out[name] = (int(n.value), float(ms.value))
     return out
+
+
+def tune_cache_load(path):
+    """Add the tuner's choices saved in a file to the process-wide cache."""
+    _check(load().spnet_tune_cache_load(os.fsencode(path)))
+
+
+def tune_cache_save(path):
+    """Write the tuner's measured choices to a file."""
+    _check(load().spnet_tune_cache_save(os.fsencode(path)))
+
+
+def tune_cache_clear():
+    _check(load().spnet_tune_cache_clear())
+
+
+def tune_counts():
+    """(choices measured, choices taken from the cache) since the last clear."""
+    m, r = C.c_int64(0), C.c_int64(0)
+    _check(load().spnet_tune_counts(C.byref(m), C.byref(r)))
+    return int(m.value), int(r.value)
 
 
 def _check(rc):
