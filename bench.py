@@ -61,7 +61,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--inflight", type=int, default=4)
-    ap.add_argument("--mode", default="served", choices=["served", "single", "multi_rhs", "c5", "lap_conv"],
+    ap.add_argument("--struct-hinv", default="4,8,16,32",
+                    help="--mode struct: the coarse meshes H^-1 of Tables struct2D and struct3d")
+    ap.add_argument("--mode", default="served", choices=["served", "single", "multi_rhs", "c5", "lap_conv",
+                                                          "struct"],
                     help="single: only the one-request-at-a-time measurement (for profiling runs)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
@@ -549,6 +552,19 @@ def run_gb300(args, rank, world, local):
                           "setup_s": round(t2 - t1, 3), "solve_s": round(t3 - t2, 3),
                           "iterations": [int(min(x.iterations for x in st)), int(max(x.iterations for x in st))],
                           "relres": max(x.relres for x in st)}
+            if label == "one_at_a_time":
+                # the iteration kernels at this size: one more solve, every launch timed
+                spnet.profile_reset()
+                spnet.profile_enable(True)
+                spnet.pcg_solve(op, pc, F[:1], G[:1], rtol=rtol, maxit=2000, raise_on_noconv=False)
+                spnet.profile_enable(False)
+                prof = spnet.profile_read()
+                kb, ko = kernel_bytes(op, pc, 4)
+                peak, _ = peaks()
+                out["kernel_roofline_one_vector"] = {
+                    kname: {"algorithmic_bytes": int(kb[kname]), "avg_launch_us": round(v[1] / v[0] * 1e3, 2),
+                            "frac": round(kb[kname] / (v[1] / v[0] / 1e3) / 1e9 / peak, 4)}
+                    for kname, v in prof.items() if kname in kb and v[0] > 0}
             if label == "batched":
                 core = pc.export(spnet.EXPORT_STAR_CORE)
                 cores = {"panel_stars": int(info.panel_stars), "core_mean": round(float(core.mean()), 1),
@@ -611,6 +627,8 @@ def run_gb300(args, rank, world, local):
 
     if args.mode == "lap_conv":  # the paper's heat experiments (Section 6.2, Table lap_conv)
         return dict(lap_conv=lap_conv_table())
+    if args.mode == "struct":  # the structural experiments (Section 6.3, Tables struct2D, struct3d)
+        return dict(struct=struct_tables(h_inv=tuple(int(v) for v in args.struct_hinv.split(","))))
     if args.mode == "multi_rhs":  # the k-right-hand-side measurement only (profiling runs of the batched kernels)
         return dict(mrhs=multi_rhs())
     if args.mode == "c5":  # a large network with 32 right-hand sides
@@ -750,6 +768,47 @@ def lap_conv_table(seed=6000):
     return out
 
 
+# Tables struct2D and struct3d (Section 6.3): mean PCG rate at H^-1 = 4, 8, 16, 32
+STRUCT_PAPER = {"pure_displacement": [0.54, 0.62, 0.65, 0.65], "lateral_load": [0.56, 0.64, 0.74, 0.76]}
+
+
+def struct_tables(seed=6100, h_inv=(4, 8, 16, 32)):
+    """The two structural problems of Section 6.3 through the library (beam model with the
+    bending term): the in-plane pull on the orientation-biased network and the lateral
+    load on the placement-biased one (fibres of length 0.05, total length 1000; the bias
+    distributions are stand-ins, the paper does not give them); FP64 textbook PCG, mean and
+    largest rate until the K-norm error has fallen by 1e-8."""
+    from paper_2207_07488_gb300.experiments import pcg_rates
+    out = {}
+    for name, lateral, bias in (("pure_displacement", False, "orientation"), ("lateral_load", True, "placement")):
+        t0 = time.perf_counter()
+        net = nw.fiber_network_2d(0, 0.05, seed + (1 if lateral else 0), midpoint_pad=0.025, keep="boundary",
+                                  total_length=1000.0, bias=bias)
+        rows = []
+        for Hinv in h_inv:
+            k = (4, 8, 16, 32).index(Hinv)
+            p = nw.beam_problem(net, 1.0 / Hinv, lateral=lateral)
+            t1 = time.perf_counter()
+            try:
+                r = pcg_rates(p)
+            except Exception as e:  # stars beyond the library's 65535 dofs at coarse H
+                rows.append({"H_inv": Hinv, "paper_tau_mean": STRUCT_PAPER[name][k], "not_run": str(e)[:160]})
+                continue
+            print(f"[struct] {name} H^-1 = {Hinv}: tau mean {r['mean']:.3f}, {r['steps']} steps, "
+                  f"{time.perf_counter() - t1:.1f} s", file=sys.stderr, flush=True)
+            rows.append({"H_inv": Hinv, "tau_mean": round(r["mean"], 3), "tau_max": round(r["max"], 3),
+                         "paper_tau_mean": STRUCT_PAPER[name][k], "steps": r["steps"], "n_free": r["n_free"],
+                         "stars": r["stars"], "max_star": r["max_star"], "max_dense_block": r["max_dense_block"],
+                         "reference_steps": r["reference_steps"], "solve_ms_per_step":
+                         round(r["solve_ms"] / max(r["reference_steps"], 1), 2),
+                         "s": round(time.perf_counter() - t1, 2)})
+        out[name] = {"nodes": int(p.net.n_nodes), "triples": int(p.meta["triples"].shape[0]),
+                     "generation_s": round(t1 - t0, 1), "rows": rows}
+    out["note"] = ("beam model (eq. tensile + eq. bend, steel wire r_w = 2.5 mm, E = 210 GPa); rates as in "
+                   "lap_conv; the biased networks are stand-ins of the paper's unspecified distributions")
+    return out
+
+
 def cpu_oracle_sample(problem, iters_full, sample_iters=3):
     """Bounded CPU sample: the oracle's set-up plus a few PCG iterations.
 
@@ -816,6 +875,10 @@ def main():
     if args.mode == "lap_conv":
         if rank == 0:
             print(json.dumps({"mode": "lap_conv", "table": r["lap_conv"]}))
+        return
+    if args.mode == "struct":
+        if rank == 0:
+            print(json.dumps({"mode": "struct", "tables": r["struct"]}))
         return
     if args.mode == "c5":
         if rank == 0:

@@ -166,6 +166,29 @@ int spnet_assemble(int model, int64_t n_nodes, int64_t n_edges, const int64_t* e
                    int64_t* row_ptr, int32_t* col, double* val, int64_t cap_nnz,
                    int64_t* nnz_out);
 
+/* spnet_assemble_beam -- K of the structural model of Example 3.3 for a planar network
+ * (d = 2, n = 3: two displacement components in the plane, one lateral), Section 6.3.
+ *
+ * K = K^(T) + K^(B) on 3 * n_nodes dofs (node-major).  eq. (tensile) without the lateral
+ * term: each edge e = {i, j} of length L adds (coef[e] / L) (d . (v_i - v_j))^2, d the unit
+ * edge direction (coef: gamma_xy = A E).  eq. (bend): each triple (x, y, z, along) of
+ * triples [4 * n_triples] (x with two distinct neighbours y, z; the fourth entry is ignored
+ * here) adds, for k = 1, 2, EI / (L_y + L_z) (a_y + a_z)^2 with a_w = (v(w) - v(x)) .
+ * eta_w / L_w: k = 2 with eta_y = d_xy x e_3 and eta_z = -d_xz x e_3 (the change of the angle
+ * between the two edges), k = 1 with eta_y = eta_z = e_3 (this is the paper's form summed over
+ * ordered pairs, each unordered pair counted twice; the sign of eta_z for k = 2 is read so
+ * that a kink costs energy and a rigid rotation in the plane does not).  EI = E I, the
+ * wire's bending stiffness (gamma_xyz = EI (L_y + L_z)^-2).  coords [2 * n_nodes].
+ * Output CSR as spnet_assemble (rows sorted; a node's rows couple it to itself, its edge
+ * neighbours and the other members of its triples).  Errors: BAD_INPUT (bad ids, repeated
+ * members of a triple, non-finite values), UNSUPPORTED (cap_nnz too small; a node coupled to
+ * more than 64 nodes).
+ */
+int spnet_assemble_beam(int64_t n_nodes, int64_t n_edges, const int64_t* edges, const double* coords,
+                        const double* coef, int64_t n_triples, const int64_t* triples, double EI, int mem,
+                        void* stream, int64_t* row_ptr, int32_t* col, double* val, int64_t cap_nnz,
+                        int64_t* nnz_out);
+
 /* build_network_operator -- the free-dof operator of a network problem.
  *
  * Section 3: with Dirichlet dofs D (values g) and free dofs I, the solver
@@ -402,6 +425,23 @@ int spnet_pc_export(spnet_pc_t pc, int what, void* host_buf, size_t bytes);
  * written earlier in the same call, so nothing has to be cleared between
  * calls.  Runs on the operator's stream and returns when rc is complete. */
 int spnet_pc_restrict_static(spnet_pc_t pc, const double* r, double* rc);
+
+/* spnet_pc_record_iterates -- keep the PCG iterates of later solves (the rate
+ * experiments of Section 6: the K-norm error |u - u^(l)|_K after every step l,
+ * eq. conv_rate).  While set, every spnet_pcg_solve that takes its right-hand
+ * sides one at a time (batch_rhs = 1) writes, for each right-hand side in turn,
+ * u^(l) restricted to the free dofs (free order, n_free doubles) to
+ * buf + l * n_free for the step counts l = 0 (the initial guess), 1, 2, ...
+ * below max_iterates; later steps are not kept, and the next right-hand side
+ * writes over the previous one's.  Steps keep counting across restarts.
+ * buf: device memory of the preconditioner's device, the caller's, at least
+ * max_iterates * n_free doubles, 8-byte aligned.  buf = NULL with
+ * max_iterates = 0 stops recording.  Recording runs the iterations as separate
+ * launches (not the chunked CUDA graph), one more kernel per step.  Errors:
+ * BAD_INPUT (null pc; buf NULL with max_iterates > 0 or the reverse;
+ * max_iterates < 0; buf not device memory of the preconditioner's device;
+ * max_iterates * n_free beyond 2^62). */
+int spnet_pc_record_iterates(spnet_pc_t pc, double* buf, int64_t max_iterates);
 
 /* Instrumentation (process-wide; not part of the paper's method).
  * spnet_launch_count   kernels the library has launched since it was loaded.

@@ -9,6 +9,20 @@ Structural model, eq. (tensile) with the lateral regularisation of the 3-dof
 workload: each edge contributes c_e (v_i - v_j)^T (n n^T + 0.1 I)(w_i - w_j),
 c_e = EA / L_eff.  Dofs are node-major (3*node + component).
 
+Beam model (Example 3.3 with d = 2, n = 3; Section 6.3): K = K^(T) + K^(B).
+eq. (tensile) without the lateral term: each edge adds gamma_xy / L (d . (v_i - v_j))^2,
+d the unit edge direction, gamma_xy = A E.  eq. (bend): node x with neighbours y != z
+adds, for k = 1, 2, gamma_xyz (L_y + L_z) / 2 (a_y + a_z)^2 per ordered pair (y, z),
+a_w = (v(w) - v(x)) . eta^(w,k) / L_w, gamma_xyz = E I (L_y + L_z)^-2,
+E I = gamma_xy r_w^2 / 4.  Readings: k = 2 (in the plane) with eta^(y,2) = d_xy x e_3 and
+eta^(z,2) = -d_xz x e_3, the change of the angle between the two edges, so that the term
+vanishes on rigid motions and a kink of a straight wire costs energy (with both normals
+d_xw x e_3 as printed, a kink would cost nothing and a rigid rotation would); k = 1 (out
+of the plane) as printed, eta^(1) = e_3 on both sides, for every pair (for an angled
+pair no out-of-plane form of this kind vanishes on rotations about in-plane axes; the
+Dirichlet sides remove those).  Each unordered pair appears twice in the ordered sum, so
+it adds E I / (L_y + L_z) (a_y + a_z)^2 for each k.
+
 Section 3: with u_hat = u + g, g the Dirichlet data extended by zero, the free
 block solves A u_I = b with A = K_II and b = f_I - K_ID g_D.
 """
@@ -43,6 +57,46 @@ def assemble(problem) -> sp.csr_matrix:
                 R += [3 * i + a, 3 * j + a, 3 * i + a, 3 * j + a]
                 C += [3 * i + b, 3 * j + b, 3 * j + b, 3 * i + b]
                 V += [v, v, -v, -v]
+        K = sp.coo_matrix((np.concatenate(V), (np.concatenate(R), np.concatenate(C))),
+                          shape=(3 * n, 3 * n))
+        return K.tocsr()
+    if problem.model == "beam":
+        c = net.stiff
+        X = net.coords
+        L = np.linalg.norm(X[j] - X[i], axis=1)
+        d3 = np.zeros((net.n_edges, 3))
+        d3[:, :2] = (X[j] - X[i]) / L[:, None]
+        R, C, V = [], [], []
+        for a in range(3):  # tensile: (c / L) b b^T, b = [d, -d]
+            for b in range(3):
+                v = c / L * d3[:, a] * d3[:, b]
+                R += [3 * i + a, 3 * j + a, 3 * i + a, 3 * j + a]
+                C += [3 * i + b, 3 * j + b, 3 * j + b, 3 * i + b]
+                V += [v, v, -v, -v]
+        T = problem.meta["triples"]
+        x, y, z = T[:, 0], T[:, 1], T[:, 2]
+        Ly = np.linalg.norm(X[y] - X[x], axis=1)
+        Lz = np.linalg.norm(X[z] - X[x], axis=1)
+        EI = c[0] * problem.meta["r_w"] ** 2 / 4.0  # gamma_xy = A E is the same on every edge
+        cb = EI / (Ly + Lz)
+        ty = (X[y] - X[x]) / Ly[:, None]
+        tz = (X[z] - X[x]) / Lz[:, None]
+        zero = np.zeros(T.shape[0])
+        e3 = np.stack([zero, zero, zero + 1.0], axis=1)
+        # k = 2: eta^(y) = d_xy x e_3, eta^(z) = -d_xz x e_3; k = 1: e_3 on both sides
+        terms = [(np.stack([ty[:, 1], -ty[:, 0], zero], axis=1), np.stack([-tz[:, 1], tz[:, 0], zero], axis=1),
+                  np.ones(T.shape[0])),
+                 (e3, e3, np.ones(T.shape[0]))]
+        nodes = [x, y, z]
+        for ey, ez, on in terms:  # (cb on) g g^T, g over the 9 dofs of (x, y, z)
+            gv = [-(ey / Ly[:, None] + ez / Lz[:, None]), ey / Ly[:, None], ez / Lz[:, None]]
+            for p_ in range(3):
+                for q_ in range(3):
+                    for a in range(3):
+                        for b in range(3):
+                            R.append(3 * nodes[p_] + a)
+                            C.append(3 * nodes[q_] + b)
+                            V.append(cb * on * gv[p_][:, a] * gv[q_][:, b])
         K = sp.coo_matrix((np.concatenate(V), (np.concatenate(R), np.concatenate(C))),
                           shape=(3 * n, 3 * n))
         return K.tocsr()

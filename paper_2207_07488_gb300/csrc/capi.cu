@@ -142,6 +142,18 @@ int spnet_assemble(int model, int64_t n_nodes, int64_t n_edges, const int64_t* e
                          row_ptr, col, val, cap_nnz, nnz_out);
 }
 
+int spnet_assemble_beam(int64_t n_nodes, int64_t n_edges, const int64_t* edges, const double* coords,
+                        const double* coef, int64_t n_triples, const int64_t* triples, double EI, int mem,
+                        void* stream, int64_t* row_ptr, int32_t* col, double* val, int64_t cap_nnz,
+                        int64_t* nnz_out) {
+  cudaGetLastError();
+  if ((!edges || !coef) && n_edges > 0) return fail(SPNET_ERR_BAD_INPUT, "spnet_assemble_beam: null edges");
+  if (!coords || (!triples && n_triples > 0)) return fail(SPNET_ERR_BAD_INPUT, "spnet_assemble_beam: null input");
+  if (!row_ptr || !col || !val) return fail(SPNET_ERR_BAD_INPUT, "spnet_assemble_beam: null output");
+  return spnet::assemble_beam(n_nodes, n_edges, edges, coords, coef, n_triples, triples, EI, mem,
+                              (cudaStream_t)stream, row_ptr, col, val, cap_nnz, nnz_out);
+}
+
 int build_network_operator(int dim, int ndof, int64_t n_nodes, const double* coords,
                            const int64_t* row_ptr, const int32_t* col_idx, const double* vals,
                            int64_t n_dirichlet, const int64_t* dirichlet_dofs,
@@ -453,6 +465,29 @@ int spnet_profile_read(int kernel, int64_t* launches, double* total_ms) {
 int spnet_profile_reset(void) {
   cudaGetLastError();  // start from a clean error state
   profile_reset();
+  return SPNET_OK;
+}
+
+int spnet_pc_record_iterates(spnet_pc_t pc, double* buf, int64_t max_iterates) {
+  cudaGetLastError();  // start from a clean error state
+  if (!pc) return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_record_iterates: null preconditioner");
+  if (max_iterates < 0 || (buf == nullptr) != (max_iterates == 0))
+    return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_record_iterates: buf and max_iterates disagree");
+  if (buf) {
+    if (reinterpret_cast<uintptr_t>(buf) % 8 != 0)
+      return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_record_iterates: buf not 8-byte aligned");
+    if (pc->N > 0 && max_iterates > (((int64_t)1 << 62) / pc->N))
+      return fail(SPNET_ERR_BAD_INPUT, "spnet_pc_record_iterates: max_iterates * n_free beyond 2^62");
+    cudaPointerAttributes a{};
+    const cudaError_t e = cudaPointerGetAttributes(&a, buf);
+    if (e != cudaSuccess) cudaGetLastError();
+    if (e != cudaSuccess || (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) ||
+        a.device != pc->op->device)
+      return fail(SPNET_ERR_BAD_INPUT,
+                  "spnet_pc_record_iterates: buf is not device memory of the preconditioner's device");
+  }
+  pc->rec_buf = buf;
+  pc->rec_max = max_iterates;
   return SPNET_OK;
 }
 

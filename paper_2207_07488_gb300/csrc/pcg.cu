@@ -547,6 +547,21 @@ static void precond_any(spnet_pc_s* pc, double* r, double* z, int with_coarse, i
 // The residual alternates between pc->r and pc->r2 (parity): the update writes
 // the new residual into the other buffer while the star solves, started right
 // after the SpMV, form the same values from the old residual, q and alpha.
+// spnet_pc_record_iterates: x^(l) in free order at buf + l N, l = the step count
+__global__ void k_record_iterate(int64_t N, const int32_t* perm, const double* xp, const Scal* sc, double* buf,
+                                 int64_t max) {
+  const int64_t l = sc->iter;
+  if (l >= max) return;
+  double* out = buf + l * N;
+  GRID_STRIDE(p, N) out[perm[p]] = xp[p];
+}
+
+static void record_iterate(spnet_pc_s* pc, cudaStream_t s) {
+  if (!pc->rec_buf) return;
+  note_launch();
+  k_record_iterate<<<pc->G, 256, 0, s>>>(pc->N, pc->perm, pc->x, pc->scal, pc->rec_buf, pc->rec_max);
+}
+
 static void iteration(spnet_pc_s* pc, cudaStream_t s, cudaStream_t side, int parity) {
   const int* done = &pc->scal->done;
   double* rc = parity ? pc->r2 : pc->r;  // residual of the previous iteration
@@ -595,9 +610,13 @@ static int chunk_graph(spnet_pc_s* pc, cudaStream_t s) {
 }
 
 static int run_chunk(spnet_pc_s* pc, cudaStream_t s) {
-  if (profiling_on()) {
-    // eager launches so that every kernel can be timed with its own events
-    for (int it = 0; it < CHUNK; ++it) iteration(pc, s, nullptr, it & 1);
+  if (profiling_on() || pc->rec_buf) {
+    // eager launches so that every kernel can be timed with its own events, and
+    // the iterate of every step can be recorded
+    for (int it = 0; it < CHUNK; ++it) {
+      iteration(pc, s, nullptr, it & 1);
+      record_iterate(pc, s);
+    }
     return SPNET_OK;
   }
   SPNET_TRY(chunk_graph(pc, s));
@@ -771,6 +790,7 @@ int pcg_run(spnet_op_s* op, spnet_pc_s* pc, int nrhs, const double* f, const dou
       SPNET_CUDA_TRY(cudaMemsetAsync(pc->x, 0, sizeof(double) * N, s));
       SPNET_CUDA_TRY(cudaMemsetAsync(pc->q, 0, sizeof(double) * N, s));
     }
+    record_iterate(pc, s);  // l = 0
     int restarts = 0;
     Scal h{};
     for (;;) {

@@ -101,6 +101,9 @@ struct TuneClass {
 int tune_begin(int kind, const TuneClass& c, int* value);
 void tune_end(int kind, const TuneClass& c, int value);
 int tune_peek(int kind, const TuneClass& c, int* value);  // 1 and *value if known; never waits
+int assemble_beam(int64_t n_nodes, int64_t n_edges, const int64_t* edges, const double* coords,
+                  const double* coef, int64_t n_tri, const int64_t* tri, double EI, int mem, cudaStream_t s,
+                  int64_t* row_ptr, int32_t* col, double* val, int64_t cap_nnz, int64_t* nnz_out);
 int spmv_grid(const spnet_pc_s* pc, int lanes);
 int spmv_lanes_tune(spnet_pc_s* pc);
 int batch_jw_tune(spnet_pc_s* pc);
@@ -133,6 +136,8 @@ struct spnet_pc_s {
   int batch_rhs = 1;            // right-hand sides pcg_solve steps together
   int star_map = 0;             // warps per block of the star solve: 0 tuned per size class
   int patch = SPNET_PATCH_ELEMENT;  // dofs a star holds (SPNET_PATCH_*)
+  double* rec_buf = nullptr;    // spnet_pc_record_iterates: the caller's [rec_max*N], free order
+  int64_t rec_max = 0;
   int d = 0, ndof = 1, nc = 4;  // nc = 2^d corners
   int gamma[3] = {0, 0, 0};     // Dirichlet face bitmask per component
   int nH[3] = {1, 1, 1};

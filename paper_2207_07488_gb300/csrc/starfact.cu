@@ -30,8 +30,19 @@
 
 namespace spnet {
 
-constexpr int CAP = 32;          // adjacency slots per node during elimination
-constexpr int SWITCH_DEG = 24;   // minimum degree above which the rest is dense
+// Adjacency slots per node during elimination: 32, or for matrices with longer rows
+// (the beam model couples a node with its neighbours' neighbours, up to ~60 entries
+// a row) half as many again as the longest row holds off the diagonal, rounded up to
+// a multiple of 32 and at most 128.  The rest of a star turns dense once the minimum
+// degree passes three quarters of the capacity.
+constexpr int CAP_MIN = 32;
+constexpr int CAP_MAX = 128;
+__host__ __device__ inline int adjacency_cap(int max_offdiag) {
+  if (max_offdiag <= 24) return CAP_MIN;
+  int c = (max_offdiag + max_offdiag / 2 + 31) / 32 * 32;
+  return c < CAP_MAX ? c : CAP_MAX;
+}
+__host__ __device__ inline int switch_degree(int cap) { return cap - cap / 4; }
 constexpr int CORE_FIRST = 256;  // dense block capacity of the first attempt (raised 4x on overflow)
 
 __host__ __device__ inline int64_t core_entries(int core_max) { return (int64_t)core_max * (core_max - 1) / 2; }
@@ -97,14 +108,16 @@ struct StarArgs {
   int* flags;
   int* next;
   int vbytes;
+  int cap;            // adjacency slots per node (adjacency_cap)
   int patch;          // SPNET_PATCH_*
   const double* q1w;  // [nc][N] Q1 values (the support rule tests them against zero)
   int64_t N;
 };
 
 struct Scratch {
-  uint16_t* nbr;     // [nmax*CAP]
-  uint16_t* colent;  // [nmax*CAP + core_entries(core_max)]
+  int cap;
+  uint16_t* nbr;     // [nmax*cap]
+  uint16_t* colent;  // [nmax*cap + core_entries(core_max)]
   int32_t* deg;      // [nmax]
   int32_t* state;    // [nmax]: -1 alive, else elimination position
   int32_t* posnode;  // [nmax]
@@ -117,26 +130,27 @@ struct Scratch {
 
 // hot arrays (adjacency, degrees, states, selection), touched in every round:
 // in shared memory when they fit, else with the cold ones in global scratch
-__host__ __device__ inline int64_t hot_bytes(int nmax) {
-  return align_up(2ll * nmax * CAP, 16) + align_up(8ll * nmax, 16) + align_up((int64_t)nmax, 16);
+__host__ __device__ inline int64_t hot_bytes(int nmax, int cap) {
+  return align_up(2ll * nmax * cap, 16) + align_up(8ll * nmax, 16) + align_up((int64_t)nmax, 16);
 }
 
-__host__ __device__ inline int64_t cold_bytes(int nmax, int core_max) {
-  int64_t o = 2ll * ((int64_t)nmax * CAP + core_entries(core_max));
+__host__ __device__ inline int64_t cold_bytes(int nmax, int core_max, int cap) {
+  int64_t o = 2ll * ((int64_t)nmax * cap + core_entries(core_max));
   o = align_up(o, 8);
   o += 4ll * (nmax + 1) * 6;
   return align_up(o, 256);
 }
 
-__device__ inline Scratch carve(char* cold, char* hot, int nmax, int core_max) {
+__device__ inline Scratch carve(char* cold, char* hot, int nmax, int core_max, int cap) {
   Scratch s;
+  s.cap = cap;
   int64_t o = 0;
-  s.nbr = (uint16_t*)(hot + o);   o = align_up(o + 2ll * nmax * CAP, 16);
+  s.nbr = (uint16_t*)(hot + o);   o = align_up(o + 2ll * nmax * cap, 16);
   s.deg = (int32_t*)(hot + o);    o += 4ll * nmax;
   s.state = (int32_t*)(hot + o);  o = align_up(o + 4ll * nmax, 16);
   s.sel = (uint8_t*)(hot + o);
   o = 0;
-  s.colent = (uint16_t*)(cold + o); o += 2ll * ((int64_t)nmax * CAP + core_entries(core_max));
+  s.colent = (uint16_t*)(cold + o); o += 2ll * ((int64_t)nmax * cap + core_entries(core_max));
   o = align_up(o, 8);
   s.posnode = (int32_t*)(cold + o);  o += 4ll * (nmax + 1);
   s.colstart = (int32_t*)(cold + o); o += 4ll * (nmax + 1);
@@ -224,7 +238,7 @@ __device__ inline int warp_incl_scan(int v, int lane) {
 __device__ inline void compact_all(const Scratch& W, int n, int lane) {
   for (int t = lane; t < n; t += 32) {
     if (W.state[t] >= 0) continue;
-    uint16_t* lst = W.nbr + (int64_t)t * CAP;
+    uint16_t* lst = W.nbr + (int64_t)t * W.cap;
     int c = 0, d = W.deg[t];
     for (int q = 0; q < d; ++q) {
       int u = lst[q];
@@ -240,8 +254,9 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
   const int lane = threadIdx.x & 31;
   const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   char* cold = A.scratch + wg * A.stride;
-  char* hot = A.hot_in_smem ? sm_hot + (threadIdx.x >> 5) * A.hot : cold + cold_bytes(A.nmax, A.core_max);
-  const Scratch W = carve(cold, hot, A.nmax, A.core_max);
+  char* hot = A.hot_in_smem ? sm_hot + (threadIdx.x >> 5) * A.hot : cold + cold_bytes(A.nmax, A.core_max, A.cap);
+  const Scratch W = carve(cold, hot, A.nmax, A.core_max, A.cap);
+  const int CAP = A.cap, SWITCH_DEG = switch_degree(A.cap);
   const unsigned FULL = 0xffffffffu;
   for (;;) {
     int s = 0;
@@ -405,6 +420,29 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
       nlev++;
       if (full) dense = true;
     }
+    if (dense && npos < n && A.patch == SPNET_PATCH_SUPPORT) {
+      // dofs off the support still alive (all of them when the first adjacency
+      // overflowed) are isolated: one level of their own ahead of the dense block,
+      // so that the block couples none of them
+      const int p0 = npos;
+      for (int base = 0; base < n; base += 32) {
+        int t = base + lane;
+        bool al = t < n && W.state[t] < 0 && off_support(se, A.elem_ptr, A.q1w, A.N, t);
+        unsigned b = __ballot_sync(FULL, al);
+        if (al) {
+          int pos = npos + __popc(b & ((1u << lane) - 1u));
+          W.posnode[pos] = t;
+          W.colstart[pos] = ncol;
+          W.state[t] = pos;
+        }
+        npos += __popc(b);
+      }
+      if (npos > p0) {
+        if (lane == 0) W.lvl[nlev] = p0;
+        nlev++;
+      }
+      __syncwarp();
+    }
     int core_c = 0;  // nodes of the dense block
     if (dense && npos < n) {
       // the rest, in ascending node order, one node per level, columns dense
@@ -512,6 +550,15 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
     }
     __syncwarp();
   }
+}
+
+// the longest row of K (entries), for the adjacency capacity
+__global__ void k_max_row(int64_t n, const int64_t* __restrict__ ptr, int* out) {
+  int m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (int)(ptr[i + 1] - ptr[i]));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
 __device__ inline double k_entry(const int64_t* kptr, const int32_t* kcol, const double* kval, int row,
@@ -2014,7 +2061,19 @@ int pc_factor_stars(spnet_pc_s* pc) {
   } guard{tmp};
   const int nmax = pc->max_star;
   if (nmax > 65535) return fail(SPNET_ERR_UNSUPPORTED, "setup_preconditioner: a star beyond 65535 dofs");
-  const int64_t hot = hot_bytes(nmax);
+  int max_row = 0;
+  {
+    int* d = nullptr;
+    SPNET_TRY(tmp.get(&d, 1));
+    SPNET_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(int), s));
+    note_launch();
+    k_max_row<<<4 * num_sms(), 256, 0, s>>>(pc->N, pc->K.ptr, d);
+    SPNET_CUDA_TRY(cudaGetLastError());
+    SPNET_CUDA_TRY(cudaMemcpyAsync(&max_row, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPNET_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  const int acap = adjacency_cap(max_row - 1);
+  const int64_t hot = hot_bytes(nmax, acap);
   // hot arrays in shared memory when four warps' worth fit in 200 KiB, one
   // block of four warps per SM at least; otherwise everything in global scratch
   const int hot_in_smem = 4 * hot <= 200 * 1024 ? 1 : 0;
@@ -2038,7 +2097,7 @@ int pc_factor_stars(spnet_pc_s* pc) {
   int64_t stride = 0, warps = 0;
   char* scratch = nullptr;
   auto size_scratch = [&]() -> int {
-    stride = cold_bytes(nmax, core_max) + (hot_in_smem ? 0 : align_up(hot, 256));
+    stride = cold_bytes(nmax, core_max, acap) + (hot_in_smem ? 0 : align_up(hot, 256));
     warps = (int64_t)4 * wpb_blocks * num_sms();
     const int64_t budget = (int64_t)1 << 30;
     if (warps * stride > budget) warps = budget / stride;
@@ -2092,6 +2151,7 @@ int pc_factor_stars(spnet_pc_s* pc) {
     A.flags = flags;
     A.next = counters;
     A.vbytes = 8;  // the set-up blobs keep FP64 values; the solve sections are packed later
+    A.cap = acap;
     A.patch = pc->patch;
     A.q1w = pc->q1w;
     A.N = pc->N;

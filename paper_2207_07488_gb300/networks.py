@@ -51,6 +51,7 @@ class Network:
     stiff: np.ndarray           # (n_edges,) float64 structural coefficient EA/L_eff
     dirs: np.ndarray            # (n_edges, dim) float64 unit edge direction
     domain: tuple = (1.0, 1.0)  # (l_1, ..., l_d)
+    fiber: np.ndarray | None = None  # (n_edges,) int64: the fibre of a fibre edge, -1 for contacts
 
     @property
     def n_nodes(self) -> int:
@@ -203,6 +204,7 @@ def _build(dim, pts, fib, pos, joins, contacts, merge_tol, keep_mask, fiber_dir,
     na, nb = lab[order[:-1]], lab[order[1:]]
     fe = (fs[1:] == fs[:-1]) & (na != nb)
     ei, ej = [na[fe]], [nb[fe]]
+    fids = [fs[1:][fe].astype(np.int64)]
     kinds = [np.full(int(fe.sum()), FIBER, np.int8)]
     cfib = np.zeros((0, 2), np.int64)
     if contacts.size:
@@ -210,10 +212,12 @@ def _build(dim, pts, fib, pos, joins, contacts, merge_tol, keep_mask, fiber_dir,
         ok = ci != cj
         ei.append(ci[ok])
         ej.append(cj[ok])
+        fids.append(np.full(int(ok.sum()), -1, np.int64))
         kinds.append(np.full(int(ok.sum()), CONTACT, np.int8))
         cfib = np.stack([fib[contacts[ok, 0]], fib[contacts[ok, 1]]], axis=1)
     ei = np.concatenate(ei)
     ej = np.concatenate(ej)
+    fid = np.concatenate(fids)
     kind = np.concatenate(kinds)
     # keep components that reach the Dirichlet region
     A = sp.coo_matrix((np.ones(ei.size), (ei, ej)), shape=(n_lab, n_lab))
@@ -230,6 +234,7 @@ def _build(dim, pts, fib, pos, joins, contacts, merge_tol, keep_mask, fiber_dir,
     ek = keep[ei]
     E = np.stack([new_id[ei[ek]], new_id[ej[ek]]], axis=1)
     kind = kind[ek]
+    fid = fid[ek]
     n_fiber_edges = int((kind == FIBER).sum())
     cfib = cfib[ek[ek.size - cfib.shape[0]:]] if cfib.shape[0] else cfib
     vec = coords[E[:, 1]] - coords[E[:, 0]]
@@ -255,16 +260,35 @@ def _build(dim, pts, fib, pos, joins, contacts, merge_tol, keep_mask, fiber_dir,
                 dirs[k] = nv / nn if nn > 0 else np.eye(3)[0]
             else:
                 dirs[k] = np.eye(dim)[0]
-    return coords, E.astype(np.int64), kind, cond, stiff, dirs
+    return coords, E.astype(np.int64), kind, cond, stiff, dirs, fid
 
 
 # ----------------------------------------------------------------------------
 # generators
 # ----------------------------------------------------------------------------
 
+def _draw_fibres(rng, count, pad, bias):
+    """Midpoints and angles of `count` fibres.  bias None: uniform midpoints in
+    [-pad, 1+pad]^2 and uniform angles; "orientation": angles concentrated about the
+    x_1 axis (the doubled angle von Mises with concentration 2); "placement": the x_1 of
+    the midpoints arcsine-distributed over [-pad, 1+pad] (denser near x_1 = 0 and 1).
+    The paper (Section 6.1) names the two biases without their distributions; these are
+    stand-ins of the same kind."""
+    if bias == "placement":
+        c = np.stack([-pad + (1.0 + 2.0 * pad) * rng.beta(0.5, 0.5, size=count),
+                      rng.uniform(-pad, 1.0 + pad, size=count)], axis=1)
+    else:
+        c = rng.uniform(-pad, 1.0 + pad, size=(count, 2))
+    if bias == "orientation":
+        th = 0.5 * rng.vonmises(0.0, 2.0, size=count)
+    else:
+        th = rng.uniform(0.0, np.pi, size=count)
+    return c, th
+
+
 def fiber_network_2d(n_fibers: int, length: float, seed: int, merge_tol: float | None = None,
                      midpoint_pad: float = 0.0, keep: str = "dirichlet_x",
-                     total_length: float | None = None) -> Network:
+                     total_length: float | None = None, bias: str | None = None) -> Network:
     """2D fiber network: straight fibers with a node at every crossing and end.
 
     Midpoints uniform in [-pad, 1+pad]^2, angles uniform in [0, pi), fibers
@@ -272,22 +296,22 @@ def fiber_network_2d(n_fibers: int, length: float, seed: int, merge_tol: float |
     both fibers; nodes closer than ``merge_tol`` (default length*1e-4) along a
     fiber are merged (Section 6.1).  With ``total_length`` set, fibers are
     drawn until their clipped length reaches it and ``n_fibers`` is ignored.
+    ``bias`` ("orientation" or "placement") draws the biased networks (see
+    _draw_fibres).
     """
     rng = np.random.default_rng(seed)
     box = np.array([1.0, 1.0])
     if merge_tol is None:
         merge_tol = length * 1e-4
     if total_length is None:
-        c = rng.uniform(-midpoint_pad, 1.0 + midpoint_pad, size=(n_fibers, 2))
-        th = rng.uniform(0.0, np.pi, size=n_fibers)
+        c, th = _draw_fibres(rng, n_fibers, midpoint_pad, bias)
         d = np.stack([np.cos(th), np.sin(th)], axis=1)
         a, b, ok = _clip_to_box(c, d, length / 2, box)
         a, b, d = a[ok], b[ok], d[ok]
     else:
         As, Bs, Ds, tot = [], [], [], 0.0
         while tot < total_length:
-            c = rng.uniform(-midpoint_pad, 1.0 + midpoint_pad, size=(1, 2))
-            th = rng.uniform(0.0, np.pi, size=1)
+            c, th = _draw_fibres(rng, 1, midpoint_pad, bias)
             dd = np.stack([np.cos(th), np.sin(th)], axis=1)
             a1, b1, ok = _clip_to_box(c, dd, length / 2, box)
             if ok[0] and np.linalg.norm(b1 - a1) > 0:
@@ -313,10 +337,10 @@ def fiber_network_2d(n_fibers: int, length: float, seed: int, merge_tol: float |
     fib = np.concatenate([np.arange(nf), np.arange(nf), i, j])
     pos = np.concatenate([np.zeros(nf), seg, s * seg[i], t * seg[j]])
     joins = np.stack([2 * nf + np.arange(nx), 2 * nf + nx + np.arange(nx)], axis=1)
-    coords, E, kind, cond, stiff, dirs = _build(
+    coords, E, kind, cond, stiff, dirs, fid = _build(
         2, pts, fib, pos, joins, np.zeros((0, 2), np.int64), merge_tol, _keep_fn(keep),
         d, 10.0, 0.0)
-    return Network(2, coords, E, kind, cond, stiff, dirs, (1.0, 1.0))
+    return Network(2, coords, E, kind, cond, stiff, dirs, (1.0, 1.0), fid)
 
 
 def fiber_network_3d(n_fibers: int, length: float, contact_dist: float, seed: int,
@@ -364,10 +388,10 @@ def fiber_network_3d(n_fibers: int, length: float, contact_dist: float, seed: in
     fib = np.concatenate([np.arange(nf), np.arange(nf), i, j])
     pos = np.concatenate([np.zeros(nf), seg, s * seg[i], t * seg[j]])
     contacts = np.stack([2 * nf + np.arange(nc), 2 * nf + nc + np.arange(nc)], axis=1)
-    coords, E, kind, cond, stiff, dirs = _build(
+    coords, E, kind, cond, stiff, dirs, fid = _build(
         3, pts, fib, pos, np.zeros((0, 2), np.int64), contacts, merge_tol, _keep_fn(keep),
         d, 10.0, contact_dist)
-    return Network(3, coords, E, kind, cond, stiff, dirs, (1.0, 1.0, 1.0))
+    return Network(3, coords, E, kind, cond, stiff, dirs, (1.0, 1.0, 1.0), fid)
 
 
 def grid_network_2d(k: int) -> Network:
@@ -495,6 +519,127 @@ def fiber_heat_problem(net: Network, H: float, gamma=None, name="") -> Problem:
     allf = X_FACES | face_bit(1, 0) | face_bit(1, 1)
     return Problem(net, 1, "scalar", on_b.astype(np.int64), np.zeros(on_b.size), f, H, (allf,),
                    STAR_ALL, name, patch=PATCH_SUPPORT)
+
+
+def beam_triples(net: Network) -> np.ndarray:
+    """Node triples (x, y, z, along) of the bending form (eq. bend): every pair of distinct
+    neighbours y < z of a node x, with along = 1 when x-y and x-z are edges of one fibre
+    (y, x, z collinear) and 0 at a joint of two fibres; ascending (x, y, z)."""
+    E = net.edges
+    f = net.fiber if net.fiber is not None else np.full(net.n_edges, -1, np.int64)
+    node = np.concatenate([E[:, 0], E[:, 1]])
+    other = np.concatenate([E[:, 1], E[:, 0]])
+    ff = np.concatenate([f, f])
+    o = np.lexsort((other, node))
+    node, other, ff = node[o], other[o], ff[o]
+    starts = np.concatenate([[0], np.nonzero(node[1:] != node[:-1])[0] + 1, [node.size]])
+    out = []
+    for a0, a1 in zip(starts[:-1], starts[1:]):
+        for i in range(a0, a1):
+            for j in range(i + 1, a1):
+                along = int(ff[i] >= 0 and ff[i] == ff[j])
+                out.append((node[i], other[i], other[j], along))
+    return np.array(out, dtype=np.int64).reshape(-1, 4)
+
+
+def _anchored_fibres(net: Network, dirichlet_fn) -> Network:
+    """Without the fibres held at fewer than two nodes (a node of a fibre holds it when
+    it is a Dirichlet node or a joint with another kept fibre): the bending form does not
+    couple the out-of-plane rotation of a fibre about a single joint, so such a fibre
+    would leave K singular.  Repeated until every fibre left is held twice.  Then, on
+    the graph of the edges between non-Dirichlet nodes, only the components joined to at
+    least two distinct Dirichlet nodes are kept: the in-plane bending form is invariant
+    under a rigid rotation about a node, so a component held at one Dirichlet node
+    (a pin) turns freely about it."""
+    f = net.fiber
+    E = net.edges
+    inc = np.unique(np.stack([np.concatenate([f, f]), np.concatenate([E[:, 0], E[:, 1]])], axis=1), axis=0)
+    dmask = dirichlet_fn(net.coords)
+    alive = np.ones(f.max() + 1, bool)
+    while True:
+        live = alive[inc[:, 0]]
+        nf = np.bincount(inc[live, 1], minlength=net.n_nodes)
+        anchor = dmask | (nf >= 2)
+        held = np.bincount(inc[live, 0], weights=anchor[inc[live, 1]].astype(float), minlength=alive.size)
+        drop = alive & (held < 2)
+        if not drop.any():
+            break
+        alive &= ~drop
+    keep_e = alive[f]
+    E = E[keep_e]
+    n = net.n_nodes
+    dE = dmask[E]
+    inner = ~dE[:, 0] & ~dE[:, 1]
+    A = sp.coo_matrix((np.ones(int(inner.sum())), (E[inner, 0], E[inner, 1])), shape=(n, n))
+    _, comp = connected_components(A, directed=False)
+    pin = dE[:, 0] ^ dE[:, 1]  # edges from a component to a Dirichlet node
+    free_end = np.where(dE[pin, 0], E[pin, 1], E[pin, 0])
+    pins = np.unique(np.stack([comp[free_end], np.where(dE[pin, 0], E[pin, 0], E[pin, 1])], axis=1), axis=0)
+    good = np.bincount(pins[:, 0], minlength=comp.max() + 1) >= 2
+    keep_edge = np.zeros(E.shape[0], bool)
+    keep_edge[inner] = good[comp[E[inner, 0]]]
+    keep_edge[pin] = good[comp[free_end]]
+    keep_n = np.zeros(n, bool)
+    keep_n[E[keep_edge, 0]] = True
+    keep_n[E[keep_edge, 1]] = True
+    new_id = -np.ones(n, np.int64)
+    new_id[keep_n] = np.arange(int(keep_n.sum()))
+    sel = np.nonzero(keep_e)[0][keep_edge]
+    return Network(net.dim, net.coords[keep_n], new_id[net.edges[sel]], net.kind[sel], net.cond[sel],
+                   net.stiff[sel], net.dirs[sel], net.domain, net.fiber[sel])
+
+
+BEAM_E = 210e9      # Young's modulus of the steel wires of Section 6.3 (Pa)
+BEAM_RW = 2.5e-3    # their radius (m)
+
+
+def beam_problem(net: Network, H: float, lateral: bool, strain: float | None = None, name="") -> Problem:
+    """The structural problems of Section 6.3 on a 2D fibre network: 3 displacement
+    components per node (two in the plane, one lateral), the tensile form (eq. tensile)
+    with gamma_xy = A E and the bending form (eq. bend) of the wire (radius BEAM_RW,
+    Young's modulus BEAM_E) on the node triples of beam_triples.  Gamma = the sides
+    x_1 = 0 and x_1 = 1, g(x) = [s x_1, 0, 0] there.
+    lateral False: the pure displacement problem (s = 0.2, in-plane only: the lateral
+    component is held at zero everywhere); True: the lateral load problem (s = 0.1, the
+    load M g' with g' = [0, 0, -1e3]).  Stars at every mesh node, support patches.
+    Parallel edges (two fibres running between the same two merged joints) count once:
+    x ~ y is a relation between nodes, and a pair of them would make a triple with
+    y = z."""
+    assert net.dim == 2
+    net = _anchored_fibres(net, lambda X: (X[:, 0] <= 0.0) | (X[:, 0] >= 1.0))
+    _, first = np.unique(np.sort(net.edges, axis=1), axis=0, return_index=True)
+    if first.size < net.n_edges:
+        k = np.sort(first)
+        net = Network(net.dim, net.coords, net.edges[k], net.kind[k], net.cond[k], net.stiff[k], net.dirs[k],
+                      net.domain, net.fiber[k])
+    from dataclasses import replace
+    A = np.pi * BEAM_RW ** 2
+    net = replace(net, stiff=np.full(net.n_edges, A * BEAM_E))
+    s = (0.1 if lateral else 0.2) if strain is None else strain
+    X = net.coords
+    side = np.nonzero((X[:, 0] <= 0.0) | (X[:, 0] >= 1.0))[0]
+    dd = [3 * side, 3 * side + 1]
+    dv = [s * X[side, 0], np.zeros(side.size)]
+    if lateral:
+        dd.append(3 * side + 2)
+        dv.append(np.zeros(side.size))
+    else:
+        allz = np.arange(net.n_nodes)
+        dd.append(3 * allz + 2)
+        dv.append(np.zeros(allz.size))
+    dd = np.concatenate(dd)
+    dv = np.concatenate(dv)
+    o = np.argsort(dd, kind="stable")
+    f = np.zeros(3 * net.n_nodes)
+    if lateral:  # M g': half the length of the edges at a node times g'
+        lengths = np.linalg.norm(X[net.edges[:, 1]] - X[net.edges[:, 0]], axis=1)
+        m = np.zeros(net.n_nodes)
+        np.add.at(m, net.edges[:, 0], 0.5 * lengths)
+        np.add.at(m, net.edges[:, 1], 0.5 * lengths)
+        f[2::3] = -1e3 * m
+    faces = (X_FACES, X_FACES, X_FACES if lateral else (X_FACES | face_bit(1, 0) | face_bit(1, 1)))
+    return Problem(net, 3, "beam", dd[o].astype(np.int64), dv[o], f, H, faces, STAR_ALL,
+                   name, meta={"triples": beam_triples(net), "r_w": BEAM_RW}, patch=PATCH_SUPPORT)
 
 
 def heat_weights(net: Network, seed: int, lo: float = 0.1, hi: float = 1.0) -> np.ndarray:

@@ -36,10 +36,11 @@ EXPORTED = [
     "spnet_pc_get_info", "spnet_spmv", "spnet_pc_apply", "spnet_pc_restrict", "spnet_pc_coarse",
     "spnet_pc_prolong", "spnet_pc_stars", "spnet_pc_export", "spnet_launch_count",
     "spnet_profile_enable", "spnet_profile_read", "spnet_profile_reset", "spnet_pc_restrict_static",
+    "spnet_pc_record_iterates",
     "spnet_server_create", "spnet_server_submit", "spnet_server_wait", "spnet_server_destroy",
     "spnet_pc_apply_batch", "spnet_server_poll", "spnet_server_cancel", "spnet_server_estimate",
     "spnet_server_budget", "spnet_tune_cache_load", "spnet_tune_cache_save", "spnet_tune_cache_clear",
-    "spnet_tune_counts",
+    "spnet_tune_counts", "spnet_assemble_beam",
 ]
 KERNELS = ["spmv", "update", "restrict", "stars", "coarse", "combine", "direction",
            "star_symbolic", "star_numeric", "sweep", "galerkin"]
@@ -129,6 +130,7 @@ def load(build_if_missing: bool = True):
     lib.spnet_pc_export.argtypes = [P, i32, P, C.c_size_t]
     lib.spnet_launch_count.argtypes = [C.POINTER(i64)]
     lib.spnet_pc_restrict_static.argtypes = [P, P, P]
+    lib.spnet_pc_record_iterates.argtypes = [P, P, i64]
     lib.spnet_profile_enable.argtypes = [i32]
     lib.spnet_profile_read.argtypes = [i32, C.POINTER(i64), C.POINTER(dbl)]
     lib.spnet_profile_reset.argtypes = []
@@ -144,6 +146,7 @@ def load(build_if_missing: bool = True):
     lib.spnet_tune_cache_save.argtypes = [C.c_char_p]
     lib.spnet_tune_cache_clear.argtypes = []
     lib.spnet_tune_counts.argtypes = [C.POINTER(i64), C.POINTER(i64)]
+    lib.spnet_assemble_beam.argtypes = [i64, i64, P, P, P, i64, P, dbl, i32, P, P, P, P, i64, C.POINTER(i64)]
     lib.spnet_server_destroy.argtypes = [P]
     for name in EXPORTED:
         getattr(lib, name).restype = C.c_int
@@ -266,6 +269,29 @@ def assemble(model, n_nodes, edges, coef, dirs=None, stream=None):
     return rp, col[:n].copy(), val[:n].copy()
 
 
+def assemble_beam(n_nodes, edges, coords, coef, triples, EI, stream=None):
+    """spnet_assemble_beam: K of the planar beam model (3 dofs per node) as host CSR arrays."""
+    lib = load()
+    edges = np.ascontiguousarray(edges, dtype=np.int64)
+    triples = np.ascontiguousarray(triples, dtype=np.int64).reshape(-1, 4)
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    # a node's rows hold at most itself, its neighbours and the members of its triples
+    deg = np.bincount(edges.ravel(), minlength=n_nodes)
+    tcnt = np.bincount(triples[:, :3].ravel(), minlength=n_nodes)
+    cap = int(9 * (n_nodes + deg.sum() + 2 * tcnt.sum()))
+    rp = np.zeros(3 * n_nodes + 1, np.int64)
+    col = np.zeros(max(cap, 1), np.int32)
+    val = np.zeros(max(cap, 1), np.float64)
+    nnz = C.c_int64(0)
+    _check(lib.spnet_assemble_beam(int(n_nodes), edges.shape[0], edges.ctypes.data, coords.ctypes.data,
+                                   coef.ctypes.data, triples.shape[0], triples.ctypes.data if triples.size else None,
+                                   float(EI), MEM_HOST, _stream_ptr(stream), rp.ctypes.data, col.ctypes.data,
+                                   val.ctypes.data, cap, C.byref(nnz)))
+    n = nnz.value
+    return rp, col[:n].copy(), val[:n].copy()
+
+
 class Operator:
     """build_network_operator: A = K_II and K_ID of a network problem."""
 
@@ -298,6 +324,10 @@ class Operator:
         net = problem.net
         if problem.model == "scalar":
             rp, col, val = assemble(MODEL_SCALAR, net.n_nodes, net.edges, net.cond, stream=stream)
+        elif problem.model == "beam":
+            EI = float(net.stiff[0]) * problem.meta["r_w"] ** 2 / 4.0
+            rp, col, val = assemble_beam(net.n_nodes, net.edges, net.coords, net.stiff, problem.meta["triples"], EI,
+                                         stream=stream)
         else:
             rp, col, val = assemble(MODEL_TRUSS3, net.n_nodes, net.edges, net.stiff, net.dirs,
                                     stream=stream)
@@ -353,6 +383,19 @@ def check_static_restrict_args(r, rc, n_free, m0):
         raise ValueError(f"restrict_static: r has {r.numel()} entries, the operator {n_free} free dofs")
     if rc.numel() < m0:
         raise ValueError(f"restrict_static: rc has {rc.numel()} entries, fewer than m0 = {m0}")
+
+
+def check_record_args(buf, n_free):
+    """Argument of spnet_pc_record_iterates, checked before the library is called: a
+    contiguous float64 torch CUDA tensor of shape (max_iterates, n_free)."""
+    if not _is_torch(buf) or not buf.is_cuda:
+        raise ValueError("record_iterates: buf must be a CUDA tensor")
+    if str(buf.dtype) != "torch.float64":
+        raise ValueError(f"record_iterates: buf must be float64, not {buf.dtype}")
+    if not buf.is_contiguous() or buf.dim() != 2:
+        raise ValueError("record_iterates: buf must be a contiguous 2-D tensor")
+    if buf.shape[1] != n_free or buf.shape[0] < 1:
+        raise ValueError(f"record_iterates: buf has shape {tuple(buf.shape)}, wanted (k >= 1, {n_free})")
 
 
 class Preconditioner:
@@ -423,6 +466,20 @@ class Preconditioner:
         _check(self._lib.spnet_pc_restrict_static(self.handle, C.c_void_p(r.data_ptr()),
                                                   C.c_void_p(rc.data_ptr())))
         return rc
+
+    def record_iterates(self, buf=None):
+        """spnet_pc_record_iterates: later one-at-a-time solves write u^(l) (free dofs) to
+        row l of buf, a contiguous float64 CUDA tensor (max_iterates, n_free) on the
+        preconditioner's device; None stops recording."""
+        if buf is None:
+            _check(self._lib.spnet_pc_record_iterates(self.handle, None, 0))
+            self._rec = None
+            return
+        check_record_args(buf, self.op.info.n_free)
+        import torch
+        torch.cuda.current_stream(buf.device).synchronize()
+        _check(self._lib.spnet_pc_record_iterates(self.handle, C.c_void_p(buf.data_ptr()), int(buf.shape[0])))
+        self._rec = buf  # the library writes into it until recording stops
 
     def coarse(self, rc):
         return self._vec_call(self._lib.spnet_pc_coarse, rc, self.info.m0)

@@ -87,3 +87,30 @@ def test_static_restrict_argument_checks_on_host():
     for a, b in bad:
         with pytest.raises(ValueError):
             check_static_restrict_args(a, b, 10, 4)
+
+
+def test_record_iterates_argument_checks_on_host():
+    # the binding's checks of spnet_pc_record_iterates' buffer, with stand-ins that
+    # report CUDA placement without a GPU
+    import torch
+
+    from paper_2207_07488_gb300.spnet import check_record_args
+
+    class T:
+        def __init__(self, shape, dtype=torch.float64, contiguous=True, device="cuda:0"):
+            self.shape, self.dtype, self._c, self.device = shape, dtype, contiguous, device
+            self.is_cuda = device.startswith("cuda")
+
+        def is_contiguous(self):
+            return self._c
+
+        def dim(self):
+            return len(self.shape)
+
+    T.__module__ = "torch.stand_in"
+    check_record_args(T((5, 10)), 10)
+    check_record_args(T((1, 10)), 10)
+    for bad in (T((5, 9)), T((0, 10)), T((50,)), T((5, 10), dtype=torch.float32), T((5, 10), contiguous=False),
+                T((5, 10), device="cpu"), np.zeros((5, 10))):
+        with pytest.raises(ValueError):
+            check_record_args(bad, 10)

@@ -4,6 +4,7 @@ import pytest
 
 from conftest import read_golden
 from oracle import operator as op
+from oracle.solve import OracleSolver
 from paper_2207_07488_gb300 import networks as nw
 
 
@@ -87,3 +88,88 @@ def test_free_block_spd():
     p = nw.config1()
     free, A, _ = op.split(p)
     np.linalg.cholesky(A.toarray())   # raises if not SPD (Example 3.2)
+
+
+# ---------------------------------------------------------------------------
+# the beam model (eq. tensile + eq. bend, Section 6.3)
+# ---------------------------------------------------------------------------
+def _three_node_wire():
+    X = np.array([[0.5, 0.5], [0.4, 0.5], [0.6, 0.5]])
+    E = np.array([[0, 1], [0, 2]], dtype=np.int64)
+    AE = np.pi * nw.BEAM_RW ** 2 * nw.BEAM_E
+    net = nw.Network(2, X, E, np.zeros(2, np.int8), np.ones(2), np.full(2, AE), np.zeros((2, 2)),
+                     (1.0, 1.0), np.zeros(2, np.int64))
+    p = nw.Problem(net, 3, "beam", np.zeros(0, np.int64), np.zeros(0), np.zeros(9), 0.5,
+                   (0, 0, 0), "all", meta={"triples": nw.beam_triples(net), "r_w": nw.BEAM_RW})
+    return p, AE, AE * nw.BEAM_RW ** 2 / 4.0
+
+
+def test_beam_three_node_energies():
+    p, AE, EI = _three_node_wire()
+    assert p.meta["triples"].tolist() == [[0, 1, 2, 1]]
+    K = op.assemble(p).toarray()
+    g = read_golden("beam_three_nodes.txt")["energies"]
+    d = 1e-3
+    motions = {0: (1, 0, -d), 1: (0, 1, d), 2: (0, 2, d)}  # (node, component, displacement)
+    for mid, want in g:
+        node, comp, val = motions[int(mid)]
+        v = np.zeros(9)
+        v[3 * node + comp] = val
+        scale = AE if int(mid) == 0 else EI
+        assert abs(v @ K @ v - want * scale * d * d) <= 1e-12 * want * scale * d * d
+
+
+def _small_beam(lateral):
+    net = nw.fiber_network_2d(0, 0.05, 7, midpoint_pad=0.025, keep="boundary", total_length=40.0,
+                              bias="placement" if lateral else "orientation")
+    return nw.beam_problem(net, 0.25, lateral=lateral)
+
+
+def test_beam_rigid_motions_are_the_kernel():
+    # three translations and the in-plane rotation cost nothing; the rotations about
+    # in-plane axes cost nothing on wires (pairs along one fibre), and do cost at joints
+    p = _small_beam(True)
+    K = op.assemble(p)
+    X = p.net.coords
+    n = p.net.n_nodes
+    modes = []
+    for a in range(3):
+        m = np.zeros(3 * n)
+        m[a::3] = 1.0
+        modes.append(m)
+    rot = np.zeros(3 * n)
+    rot[0::3], rot[1::3] = -X[:, 1], X[:, 0]
+    modes.append(rot)
+    kmax = np.abs(K.data).max()
+    for m in modes:
+        assert np.abs(K @ m).max() <= 1e-10 * kmax * np.abs(m).max()
+    # a single straight wire: the rotations about in-plane axes are in the kernel too
+    q, _, _ = _three_node_wire()
+    Kw = op.assemble(q)
+    Xw = q.net.coords
+    for axis in range(2):
+        m = np.zeros(9)
+        m[2::3] = Xw[:, 1] if axis == 0 else -Xw[:, 0]
+        assert np.abs(Kw @ m).max() <= 1e-10 * np.abs(Kw.data).max()
+    # and a bent wire does cost: a random motion has positive energy
+    v = np.random.default_rng(0).standard_normal(3 * n)
+    assert v @ (K @ v) > 0
+    assert abs(K - K.T).max() <= 1e-14 * kmax
+
+
+@pytest.mark.parametrize("lateral", [False, True])
+def test_beam_free_block_spd_and_pcg_matches_direct(lateral):
+    p = _small_beam(lateral)
+    S = OracleSolver(p)
+    Ad = S.A.toarray()
+    np.linalg.cholesky(Ad)  # SPD once Gamma holds the wires
+    res = S.solve(rtol=1e-11)
+    assert np.linalg.norm(res.b - Ad @ res.x) <= 1e-11 * np.linalg.norm(res.b) * (1 + 1e-9)
+    # against the dense direct solve: both are accurate to cond(A) times the rounding unit
+    ev = np.linalg.eigvalsh(Ad)
+    x = np.linalg.solve(Ad, res.b)
+    tol = max(1e-10, 100 * ev[-1] / ev[0] * np.finfo(float).eps)
+    assert np.linalg.norm(res.x - x) <= tol * np.linalg.norm(x)
+    X = p.net.coords
+    hi = np.nonzero(X[:, 0] >= 1.0)[0]
+    np.testing.assert_allclose(res.u[3 * hi], 0.1 if lateral else 0.2)
