@@ -12,6 +12,19 @@ c in {0,1}^d of the host element, phi_{e+c}(x) = prod_i (xi_i if c_i else
 k = sum_i k_i s_i, s_0 = 1, s_i = prod_{j<i} (n_j + 1).  Corners are numbered
 c = sum_i c_i 2^i.
 
+P1 on simplices (Remark 2.1), for the Kuhn triangulation of the same box mesh:
+each box is split into the d! simplices S_pi = {t : t_pi(0) >= ... >= t_pi(d-1)}
+(pi a permutation of the axes), with vertices at the box corners whose bit sets
+are the prefixes {pi(0), .., pi(j-1)}, j = 0..d; the simplices are shape regular
+and aligned with the box faces.  Elements are numbered box by box (boxes in the
+linear order above), the d! simplices of a box by the lexicographic order of pi.
+A node goes to the lowest-numbered element whose closure holds it: along each
+axis the lowest box, e_i = min(max(ceil(x_i n_i / l_i) - 1, 0), n_i - 1) (a point
+on an interior box face belongs to the box below), then the lexicographically
+first pi along which t is non-increasing.  The basis function of a vertex is its
+barycentric coordinate: lambda_0 = 1 - t_pi(0), lambda_j = t_pi(j-1) - t_pi(j),
+lambda_d = t_pi(d-1); it is zero at the other corners of the box.
+
 Coarse dofs (the basis of V_H, ordered m_0 first): the pair (mesh node k,
 component a) is a coarse dof unless y_k lies on a Dirichlet face of
 component a, or phi_k vanishes at every free dof of component a (its
@@ -39,6 +52,47 @@ def host_elements(coords, domain, nH):
     for i in range(d):
         e[:, i] = np.minimum(np.floor(coords[:, i] * nH[i] / domain[i]), nH[i] - 1).astype(np.int64)
     return e
+
+
+def host_simplices(coords, domain, nH):
+    """Remark 2.1 on the Kuhn triangulation: (box multi-index e (n, d), permutation
+    index of the host simplex (n,), local coordinates t (n, d)) by the lowest-element
+    rule; permutations are numbered in the lexicographic order of itertools."""
+    coords = np.asarray(coords, dtype=np.float64)
+    d = coords.shape[1]
+    e = np.empty(coords.shape, dtype=np.int64)
+    t = np.empty(coords.shape)
+    for i in range(d):
+        s = coords[:, i] * nH[i] / domain[i]
+        e[:, i] = np.minimum(np.maximum(np.ceil(s) - 1, 0), nH[i] - 1).astype(np.int64)
+        t[:, i] = s - e[:, i]
+    perms = list(itertools.permutations(range(d)))
+    index = {p: j for j, p in enumerate(perms)}
+    order = np.argsort(-t, axis=1, kind="stable")   # t non-increasing, ties: smaller axis first
+    pidx = np.array([index[tuple(int(a) for a in row)] for row in order], dtype=np.int64)
+    return e, pidx, t
+
+
+def p1_values(t, pidx, d):
+    """Barycentric coordinates of every node in its host simplex, as values at the
+    2^d corners of the host box (zero at the corners that are not vertices), and the
+    mask of the corners that are vertices: arrays (n, 2^d)."""
+    perms = list(itertools.permutations(range(d)))
+    n = t.shape[0]
+    W = np.zeros((n, 2 ** d))
+    V = np.zeros((n, 2 ** d), dtype=bool)
+    for r in range(n):
+        p = perms[pidx[r]]
+        c = 0
+        prev = 1.0
+        for j in range(d + 1):
+            cur = t[r, p[j]] if j < d else 0.0
+            W[r, c] = prev - cur
+            V[r, c] = True
+            if j < d:
+                c |= 1 << p[j]
+                prev = cur
+    return W, V
 
 
 def corner_list(d):
@@ -104,8 +158,14 @@ class CoarseSpace:
         node_of = free // nd
         comp_of = free % nd
         X = net.coords[node_of]
-        self.elem = host_elements(X, net.domain, nH)
-        self.W = q1_values(X, net.domain, nH, self.elem)
+        self.space = getattr(problem, "coarse", "q1")
+        self.V = None  # P1: corners of the host box that are vertices of the host simplex
+        if self.space == "p1":
+            self.elem, self.simplex, t = host_simplices(X, net.domain, nH)
+            self.W, self.V = p1_values(t, self.simplex, d)
+        else:
+            self.elem = host_elements(X, net.domain, nH)
+            self.W = q1_values(X, net.domain, nH, self.elem)
         strides = mesh_strides(nH)
         corners = corner_list(d)
         n_mesh = int(np.prod([n + 1 for n in nH]))

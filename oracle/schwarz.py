@@ -93,12 +93,14 @@ def star_mesh_nodes(nH, star_set):
     return out
 
 
-def star_dofs(elem, k_multi, nH, W=None):
+def star_dofs(elem, k_multi, nH, W=None, V=None):
     """Free dofs whose host element touches mesh node k (the patch U(y_k)).
 
-    With the Q1 values W (n, 2^d) given, only the dofs where phi_k is nonzero
+    With the basis values W (n, 2^d) given, only the dofs where phi_k is nonzero
     are kept ("support" patches): phi_k at a dof is W at the corner of the
-    dof's host element that sits at y_k.
+    dof's host element that sits at y_k.  With the P1 vertex mask V (n, 2^d)
+    given (Remark 2.1, element patches), only the dofs whose host simplex has
+    y_k as a vertex are kept.
     """
     inside = np.ones(elem.shape[0], dtype=bool)
     for i in range(len(nH)):
@@ -109,6 +111,11 @@ def star_dofs(elem, k_multi, nH, W=None):
         for i in range(len(nH)):
             corner += (k_multi[i] - elem[S, i]) << i
         S = S[W[S, corner] != 0.0]
+    if V is not None and S.size:
+        corner = np.zeros(S.size, dtype=np.int64)
+        for i in range(len(nH)):
+            corner += (k_multi[i] - elem[S, i]) << i
+        S = S[V[S, corner]]
     return S
 
 
@@ -132,8 +139,9 @@ class SchwarzPreconditioner:
         elem = self.coarse.elem
         self.patch = getattr(problem, "patch", "element")
         Wsup = self.coarse.W if self.patch == "support" else None
+        Vel = self.coarse.V if self.patch != "support" else None  # P1 element patches
         for k in star_mesh_nodes(self.nH, star_set):
-            S = star_dofs(elem, mesh_multi(k, self.nH), self.nH, Wsup)
+            S = star_dofs(elem, mesh_multi(k, self.nH), self.nH, Wsup, Vel)
             if S.size == 0:
                 continue
             Aj = self.A[S][:, S]

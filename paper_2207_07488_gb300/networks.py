@@ -32,6 +32,7 @@ from scipy.spatial import cKDTree
 FIBER, CONTACT = 0, 1
 STAR_INTERIOR, STAR_ALL = "interior", "all"
 PATCH_ELEMENT, PATCH_SUPPORT = "element", "support"
+COARSE_Q1, COARSE_P1 = "q1", "p1"
 
 
 def face_bit(axis: int, side: int) -> int:
@@ -75,7 +76,8 @@ class Problem:
     "element" (every node whose half-open host element touches the star's mesh
     node) or "support" (only the nodes where that mesh node's Q1 basis
     function is nonzero, which leaves out nodes on the outer boundary of the
-    patch).
+    patch).  ``coarse`` picks the coarse space: Q1 on the box mesh (Section 2.3) or
+    P1 on the simplices of its Kuhn triangulation (Remark 2.1).
     """
 
     net: Network
@@ -90,6 +92,7 @@ class Problem:
     name: str = ""
     meta: dict = field(default_factory=dict)
     patch: str = PATCH_ELEMENT
+    coarse: str = COARSE_Q1         # Q1 on the boxes, or P1 on their Kuhn simplices (Remark 2.1)
 
     @property
     def n_dof(self) -> int:
