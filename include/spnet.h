@@ -73,6 +73,18 @@ extern "C" {
                                   (v - I v) phi_j of the proof of Lemma 4.1 live in.  Differs
                                   from ELEMENT only at dofs on the outer boundary of the patch */
 
+/* The coarse space V_H (Section 2.3, Remark 2.1). */
+#define SPNET_COARSE_Q1 0  /* multilinear Lagrange functions on the box mesh; a node's host element
+                              is the half-open box min(floor(x_i n_i / l_i), n_i - 1) */
+#define SPNET_COARSE_P1 1  /* continuous piecewise affine functions on the Kuhn triangulation of
+                              the box mesh (Remark 2.1): each box split into the d! simplices
+                              {t_pi(0) >= ... >= t_pi(d-1)} (t the local coordinates, pi a
+                              permutation of the axes); elements numbered box by box, the
+                              simplices of a box by the lexicographic order of pi; a node goes
+                              to the lowest-numbered element whose closure holds it.  The basis
+                              values are the barycentric coordinates; ELEMENT patches hold the
+                              dofs whose host simplex has y_j as a vertex */
+
 typedef struct spnet_op_s* spnet_op_t;
 typedef struct spnet_pc_s* spnet_pc_t;
 
@@ -98,7 +110,8 @@ typedef struct {
                         precision with batch_rhs >= 2, blocks of 32 nodes or more are solved
                         by 16-row panels with tensor-core products (TF32 inputs split in high
                         and low parts, FP32 accumulation) */
-  int reserved[8];
+  int coarse_space;  /* SPNET_COARSE_* (default SPNET_COARSE_Q1) */
+  int reserved[7];
 } spnet_options;
 
 typedef struct {

@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(256) k_bupdate(int n_elem, int64_t N, int k, i
                                                  const int8_t* __restrict__ comp_of, const CT* __restrict__ xi,
                                                  double* __restrict__ X, double* __restrict__ R,
                                                  const double* __restrict__ P, const double* __restrict__ Q,
-                                                 double* __restrict__ EP, double* part, BScal* bs, int mode) {
+                                                 double* __restrict__ EP, double* part, BScal* bs, int mode,
+                                                 int simplex) {
   constexpr int D = NC == 4 ? 2 : 3;
   __shared__ double sh[8][KMAX];
   pdl_wait();
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(256) k_bupdate(int n_elem, int64_t N, int k, i
           }
           rr = fma(v, v, rr);
           CT w[NC];
-          q1_from_xi<NC>(t[u], w);
+          basis_from_xi<NC>(t[u], w, simplex);
           const CT vc = (CT)v;
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(256) k_bcombine(int n_elem, int64_t N, int k, 
                                                   const WS* __restrict__ W, const double* __restrict__ R,
                                                   double* __restrict__ Z, double* part1, double* part2,
                                                   const double* prr, int nrr, int with_coarse, int with_stars,
-                                                  BScal* bs, int dots, int flexible) {
+                                                  BScal* bs, int dots, int flexible, int simplex) {
   constexpr int D = NC == 4 ? 2 : 3;
   __shared__ double sh[8][KMAX];
   pdl_wait();
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(256) k_bcombine(int n_elem, int64_t N, int k, 
       for (int u = 0; u < BU; ++u) {
         if (!ok[u]) continue;
         CT w[NC];
-        q1_from_xi<NC>(t[u], w);
+        basis_from_xi<NC>(t[u], w, simplex);
         CT v = CT(0);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
@@ -386,7 +387,7 @@ template <int NC, int ND, class CT>
 static void bupdate_t(spnet_pc_s* pc, Batch& b, const CT* xi, int mode, cudaStream_t s) {
   launch_pdl(k_bupdate<NC, ND, CT>, elem_blocks(pc), 256, 0, s, pc->n_elem, pc->N, b.k, b.kp,
              (const int32_t*)pc->elem_ptr, (const int8_t*)pc->comp_of, xi, b.X, b.R, (const double*)b.P,
-             (const double*)b.Q, b.EP, b.p1, b.bs, mode);
+             (const double*)b.Q, b.EP, b.p1, b.bs, mode, pc->coarse_space == SPNET_COARSE_P1 ? 1 : 0);
 }
 
 template <class CT>
@@ -410,7 +411,7 @@ static void bcombine_t(spnet_pc_s* pc, Batch& b, const CT* xi, int wc, int ws, i
              (const int32_t*)pc->elem_ptr, (const int8_t*)pc->comp_of, xi, (const int32_t*)pc->ecoarse,
              (const int64_t*)pc->estar, (const double*)b.ZC, (const WS*)b.W, (const double*)b.R, b.Z, b.p2, b.p3,
              (const double*)b.p1, elem_blocks(pc), (int)(wc && pc->m0 > 0), (int)(ws && pc->S > 0), b.bs, dots,
-             pc->flexible);
+             pc->flexible, pc->coarse_space == SPNET_COARSE_P1 ? 1 : 0);
 }
 
 template <class CT, class WS>

@@ -36,6 +36,8 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
     return fail(SPNET_ERR_BAD_INPUT, "setup_preconditioner: star_map must be in 0..8");
   if (o.patch != SPNET_PATCH_ELEMENT && o.patch != SPNET_PATCH_SUPPORT)
     return fail(SPNET_ERR_BAD_INPUT, "setup_preconditioner: unknown patch rule");
+  if (o.coarse_space != SPNET_COARSE_Q1 && o.coarse_space != SPNET_COARSE_P1)
+    return fail(SPNET_ERR_BAD_INPUT, "setup_preconditioner: unknown coarse space");
   spnet_pc_s* pc = new spnet_pc_s();
   pc->op = op;
   pc->mem.stream = op->stream;
@@ -46,6 +48,7 @@ static int setup_impl(spnet_op_s* op, double H, const int* gamma_faces, const sp
   pc->batch_rhs = o.batch_rhs < 1 ? 1 : o.batch_rhs;
   pc->star_map = o.star_map;
   pc->patch = o.patch;
+  pc->coarse_space = o.coarse_space;
   pc->panels = o.no_panels ? 0 : 1;
   pc->d = op->dim;
   pc->nc = 1 << op->dim;

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256, ND == 1 ? 4 : 2) k_update(int n_elem, int
                                                 const double* __restrict__ r, double* __restrict__ rout,
                                                 const double* __restrict__ p,
                                                 const double* __restrict__ q, double* __restrict__ epart,
-                                                double* partial, Scal* sc, int mode) {
+                                                double* partial, Scal* sc, int mode, int simplex) {
   constexpr int D = NC == 4 ? 2 : 3;
   __shared__ double sh[32];
   pdl_wait();
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256, ND == 1 ? 4 : 2) k_update(int n_elem, int
         }
         rr = fma(v, v, rr);
         CT w[NC];
-        q1_from_xi<NC>(t[h], w);
+        basis_from_xi<NC>(t[h], w, simplex);
         const CT vc = (CT)v;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(128, ND == 1 ? 7 : 4) k_combine(int n_elem, in
                                                  const double* __restrict__ r, double* __restrict__ z,
                                                  double* part1, double* part2, const double* __restrict__ prr,
                                                  int nrr, int with_coarse, int with_stars, Scal* sc,
-                                                 int flexible, int first) {
+                                                 int flexible, int first, int simplex) {
   constexpr int D = NC == 4 ? 2 : 3;
   __shared__ double sh[32];
   pdl_wait();
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(128, ND == 1 ? 7 : 4) k_combine(int n_elem, in
 #pragma unroll
       for (int h = 0; h < U; ++h) {  // every lane computes (the shuffles need all lanes); valid ones write
         CT qw[NC];
-        q1_from_xi<NC>(t[h], qw);
+        basis_from_xi<NC>(t[h], qw, simplex);
         CT vc = CT(0);
 #pragma unroll
         for (int c = 0; c < NC; ++c) vc = fma(qw[c], __shfl_sync(0xffffffffu, zl, c * ND + cm[h]), vc);
@@ -386,7 +386,8 @@ template <int NC, int ND, class CT>
 static void launch_update_t(spnet_pc_s* pc, const CT* xi, double* x, const double* r, double* rout,
                             const double* p, const double* q, Scal* sc, int mode, cudaStream_t s) {
   launch_pdl(k_update<NC, ND, CT>, elem_grid(pc, 8), 256, 0, s, pc->n_elem, pc->N, (const int32_t*)pc->elem_ptr,
-             (const int8_t*)pc->comp_of, xi, x, r, rout, p, q, pc->epart, pc->partial + pc->PG, sc, mode);
+             (const int8_t*)pc->comp_of, xi, x, r, rout, p, q, pc->epart, pc->partial + pc->PG, sc, mode,
+             pc->coarse_space == SPNET_COARSE_P1 ? 1 : 0);
 }
 
 template <class CT>
@@ -504,7 +505,7 @@ static void launch_combine_t(spnet_pc_s* pc, const CT* xi, const WS* w, const do
              (const int64_t*)pc->estar, (const double*)pc->zc, w, r, z, pc->partial + 2 * pc->PG,
              pc->partial + 3 * pc->PG, (const double*)(pc->partial + pc->PG), elem_grid(pc, 8),
              (int)(with_coarse && pc->m0 > 0), (int)(with_stars && pc->S > 0), dots ? pc->scal : nullptr,
-             pc->flexible, dots == 2 ? 1 : 0);
+             pc->flexible, dots == 2 ? 1 : 0, pc->coarse_space == SPNET_COARSE_P1 ? 1 : 0);
 }
 
 template <class CT, class WS>

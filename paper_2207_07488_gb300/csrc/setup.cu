@@ -13,15 +13,15 @@
 
 namespace spnet {
 
-// host element (half-open rule) and Q1 values of a point; the arithmetic
-// x * n / l, floor, clamp, xi = x * n / l - e, and the product over axes in
-// ascending order fix the rounding of every weight.
+// host element and local coordinates of a point; the arithmetic x * n / l, floor
+// (Q1: the half-open rule) or ceil - 1 (P1: the lowest box whose closure holds the
+// point, Remark 2.1), clamp, xi = x * n / l - e fixes the rounding of every weight.
 __device__ __forceinline__ int host_element(const Mesh& m, const double* x, const double* l,
                                             double* xi) {
   int e = 0, stride = 1;
   for (int a = 0; a < m.d; ++a) {
     double s = x[a] * (double)m.n[a] / l[a];
-    int ea = (int)floor(s);
+    int ea = m.simplex ? (int)ceil(s) - 1 : (int)floor(s);
     if (ea > m.n[a] - 1) ea = m.n[a] - 1;
     if (ea < 0) ea = 0;
     xi[a] = s - (double)ea;
@@ -75,7 +75,7 @@ __global__ void k_pc_maps(int64_t N, const int32_t* perm, const int32_t* elem_fr
                           const int8_t* comp_free, const int64_t* free_dofs, int ndof,
                           const double* coords, Mesh m, double l0, double l1, double l2,
                           int32_t* iperm, int32_t* elem_of, int8_t* comp_of, double* q1w, double* xio,
-                          float* xio32) {
+                          float* xio32, double* vind) {
   double l[3] = {l0, l1, l2};
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -91,10 +91,29 @@ __global__ void k_pc_maps(int64_t N, const int32_t* perm, const int32_t* elem_fr
       xio[(int64_t)a * N + p] = xi[a];
       xio32[(int64_t)a * N + p] = (float)xi[a];
     }
-    for (int c = 0; c < m.nc; ++c) {
-      double w = 1.0;
-      for (int a = 0; a < m.d; ++a) w *= ((c >> a) & 1) ? xi[a] : (1.0 - xi[a]);
-      q1w[(int64_t)c * N + p] = w;
+    if (m.simplex) {  // P1 on the Kuhn simplex; vind: 1 at the corners that are its vertices
+      const double t3[3] = {xi[0], xi[1], m.d == 3 ? xi[2] : 0.0};
+      double w[8];
+      int vm;
+      if (m.nc == 4) {
+        double w4[4];
+        p1_from_xi<4>(t3, w4);
+        for (int c = 0; c < 4; ++c) w[c] = w4[c];
+        vm = p1_vertex_mask<4>(t3);
+      } else {
+        p1_from_xi<8>(t3, w);
+        vm = p1_vertex_mask<8>(t3);
+      }
+      for (int c = 0; c < m.nc; ++c) {
+        q1w[(int64_t)c * N + p] = w[c];
+        if (vind) vind[(int64_t)c * N + p] = (vm >> c) & 1 ? 1.0 : 0.0;
+      }
+    } else {
+      for (int c = 0; c < m.nc; ++c) {
+        double w = 1.0;
+        for (int a = 0; a < m.d; ++a) w *= ((c >> a) & 1) ? xi[a] : (1.0 - xi[a]);
+        q1w[(int64_t)c * N + p] = w;
+      }
     }
   }
 }
@@ -179,6 +198,19 @@ __global__ void k_star_count(int n_mesh, Mesh m, int star_set, const int64_t* ep
     }
     sflag[k] = (in && cnt > 0) ? 1 : 0;
     scnt[k] = (in && cnt > 0) ? (int32_t)cnt : 0;
+  }
+}
+
+// with a patch test in use (support patches, P1 element patches) a free dof may lie in no
+// star: the star term is then zero there and B singular
+__global__ void k_star_cover(int64_t N, Mesh m, const int32_t* elem_of, const double* patch_w,
+                             const int32_t* star_of_mesh, int* flags) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    const int e = elem_of[p];
+    bool cov = false;
+    for (int c = 0; c < m.nc; ++c)
+      cov |= star_of_mesh[mesh_of(m, e, c)] >= 0 && patch_w[(int64_t)c * N + p] != 0.0;
+    if (!cov) atomicOr(flags, FLAG_UNCOVERED);
   }
 }
 
@@ -267,6 +299,16 @@ int pc_setup_structure(spnet_pc_s* pc) {
   SPNET_TRY(pc->mem.get(&pc->q1w, (int64_t)pc->nc * N));
   SPNET_TRY(pc->mem.get(&pc->xi, (int64_t)m.d * N));
   SPNET_TRY(pc->mem.get(&pc->xi32, (int64_t)m.d * N));
+  // the star kernels' patch test (see spnet_pc_s::star_rule)
+  double* vind = nullptr;
+  if (pc->coarse_space == SPNET_COARSE_P1 && pc->patch == SPNET_PATCH_ELEMENT) {
+    SPNET_TRY(pc->mem.get(&vind, (int64_t)pc->nc * N));
+    pc->star_rule = SPNET_PATCH_SUPPORT;
+    pc->patch_w = vind;
+  } else {
+    pc->star_rule = pc->patch;
+    pc->patch_w = pc->q1w;
+  }
   note_launch();
   k_segment_sort<<<grid, 128, 0, s>>>(pc->n_elem, eptr, ptmp, pc->perm);
   note_launch();
@@ -274,7 +316,7 @@ int pc_setup_structure(spnet_pc_s* pc) {
   note_launch();
   k_pc_maps<<<grid, 256, 0, s>>>(N, pc->perm, elem_free, comp_free, op->free_dofs, op->ndof,
                                  op->coords, m, op->domain[0], op->domain[1], op->domain[2],
-                                 pc->iperm, pc->elem_of, pc->comp_of, pc->q1w, pc->xi, pc->xi32);
+                                 pc->iperm, pc->elem_of, pc->comp_of, pc->q1w, pc->xi, pc->xi32, vind);
   // A in pc order
   int32_t* len = nullptr;
   SPNET_TRY(tmp.get(&len, N + 1));
@@ -334,6 +376,12 @@ int pc_setup_structure(spnet_pc_s* pc) {
   SPNET_TRY(pc->mem.get(&pc->elem_star_off, (int64_t)pc->n_elem * pc->nc));
   note_launch();
   k_elem_star_off<<<grid, 256, 0, s>>>(pc->n_elem, m, eptr, pc->star_of_mesh, pc->elem_star_off);
+  if (S > 0 && pc->star_rule == SPNET_PATCH_SUPPORT) {
+    SPNET_CUDA_TRY(cudaMemsetAsync(op->dflags, 0, sizeof(int), s));
+    note_launch();
+    k_star_cover<<<grid, 256, 0, s>>>(N, m, pc->elem_of, pc->patch_w, pc->star_of_mesh, op->dflags);
+    SPNET_TRY(check_flags(op->dflags, s, "setup_preconditioner"));
+  }
   // largest star
   std::vector<int32_t> sn(S);
   if (S > 0)

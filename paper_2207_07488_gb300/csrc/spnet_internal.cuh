@@ -51,6 +51,7 @@ enum : int {
   FLAG_OUT_OF_BOX = 64,
   FLAG_UNSORTED = 128,
   FLAG_COARSE_SPD = 256,
+  FLAG_UNCOVERED = 512,  // a free dof in no star (a patch test in use and too few stars)
 };
 
 // ---------------------------------------------------------------------------
@@ -136,6 +137,13 @@ struct spnet_pc_s {
   int batch_rhs = 1;            // right-hand sides pcg_solve steps together
   int star_map = 0;             // warps per block of the star solve: 0 tuned per size class
   int patch = SPNET_PATCH_ELEMENT;  // dofs a star holds (SPNET_PATCH_*)
+  int coarse_space = SPNET_COARSE_Q1;  // SPNET_COARSE_*
+  // The star kernels' patch test: a dof is off the star of the mesh node at its host element's
+  // corner c when patch_w[c][dof] == 0 (star_rule SUPPORT) -- the basis values for support
+  // patches, the vertex indicator of the host simplex for P1 element patches -- or never
+  // (star_rule ELEMENT: Q1 element patches).
+  int star_rule = SPNET_PATCH_ELEMENT;
+  double* patch_w = nullptr;    // [nc][N]: q1w, or the vertex indicator (P1 element patches)
   double* rec_buf = nullptr;    // spnet_pc_record_iterates: the caller's [rec_max*N], free order
   int64_t rec_max = 0;
   int d = 0, ndof = 1, nc = 4;  // nc = 2^d corners
@@ -229,7 +237,8 @@ namespace spnet {
 // ---------------------------------------------------------------------------
 struct Mesh {
   int d, nc;
-  int n[3];  // elements per axis
+  int n[3];         // elements per axis
+  int simplex = 0;  // 1: P1 on the Kuhn simplices of the boxes (SPNET_COARSE_P1)
 };
 
 __device__ __forceinline__ void elem_multi(const Mesh& m, int e, int* ex) {
@@ -273,6 +282,7 @@ inline Mesh mesh_of_pc(const spnet_pc_s* pc) {
   m.d = pc->d;
   m.nc = pc->nc;
   for (int a = 0; a < 3; ++a) m.n[a] = pc->nH[a];
+  m.simplex = pc->coarse_space == SPNET_COARSE_P1 ? 1 : 0;
   return m;
 }
 
@@ -430,6 +440,63 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// P1 values on the Kuhn simplex that holds local coordinates t (Remark 2.1): with pi the
+// axes in order of non-increasing t (ties: the smaller axis first), the corner with bits
+// {pi(0), .., pi(j-1)} gets t_pi(j-1) - t_pi(j) (t_pi(-1) = 1, t_pi(d) = 0), the other
+// corners zero; the same differences, in the same order, as the stored P1 values.
+// pi by insertion with strict comparisons (a stable sort); the values are placed with
+// selects against compile-time corners, so nothing is indexed at run time.
+template <int NC, class CT>
+__device__ __forceinline__ void p1_sorted(const CT (&t)[3], CT& a0, CT& a1, CT& a2, int& b0, int& b1, int& b2) {
+  constexpr int D = NC == 4 ? 2 : 3;
+  a0 = t[0];
+  a1 = t[1];
+  a2 = D == 3 ? t[2] : CT(0);
+  b0 = 1;
+  b1 = 2;
+  b2 = 4;
+  if (a1 > a0) {
+    const CT x = a0; a0 = a1; a1 = x;
+    const int y = b0; b0 = b1; b1 = y;
+  }
+  if (D == 3 && a2 > a1) {
+    { const CT x = a1; a1 = a2; a2 = x; }
+    { const int y = b1; b1 = b2; b2 = y; }
+    if (a1 > a0) {
+      const CT x = a0; a0 = a1; a1 = x;
+      const int y = b0; b0 = b1; b1 = y;
+    }
+  }
+}
+
+template <int NC, class CT>
+__device__ __forceinline__ void p1_from_xi(const CT (&t)[3], CT (&w)[NC]) {
+  constexpr int D = NC == 4 ? 2 : 3;
+  CT a0, a1, a2;
+  int b0, b1, b2;
+  p1_sorted<NC>(t, a0, a1, a2, b0, b1, b2);
+  const int m1 = b0, m2 = b0 | b1;
+  const CT v0 = CT(1) - a0, v1 = a0 - a1, v2 = D == 3 ? a1 - a2 : a1, v3 = a2;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    CT v = CT(0);
+    if (c == 0) v = v0;
+    else if (c == m1) v = v1;
+    else if (c == m2) v = v2;
+    else if (D == 3 && c == NC - 1) v = v3;
+    w[c] = v;
+  }
+}
+
+// the corners of the host box that are vertices of the Kuhn simplex holding t (bit c)
+template <int NC, class CT>
+__device__ __forceinline__ int p1_vertex_mask(const CT (&t)[3]) {
+  CT a0, a1, a2;
+  int b0, b1, b2;
+  p1_sorted<NC>(t, a0, a1, a2, b0, b1, b2);
+  return 1 | (1 << b0) | (1 << (b0 | b1)) | (1 << (NC - 1));
+}
+
 // Q1 values phi_c = prod_a (bit a of c ? xi_a : 1 - xi_a) at local coordinates
 // t, multiplied in axis order (the same products as the stored Q1 values)
 template <int NC, class CT>
@@ -447,6 +514,13 @@ __device__ __forceinline__ void q1_from_xi(const CT (&t)[3], CT (&w)[NC]) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) w[c] = g[c & 3] * f2[(c >> 2) & 1];
   }
+}
+
+// the coarse basis values at local coordinates t: Q1, or P1 (simplex = 1)
+template <int NC, class CT>
+__device__ __forceinline__ void basis_from_xi(const CT (&t)[3], CT (&w)[NC], int simplex) {
+  if (simplex) p1_from_xi<NC>(t, w);
+  else q1_from_xi<NC>(t, w);
 }
 
 template <int N>

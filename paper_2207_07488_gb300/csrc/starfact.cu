@@ -1983,7 +1983,7 @@ static int pack_panels(spnet_pc_s* pc, DevArena& tmp) {
   note_launch();
   k_panel_pack<float><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_core,
                                                   pc->star_mesh, pc->elem_ptr, (const StarHdr*)pc->shdr, boff, coff,
-                                                  (BatchHdr*)pc->bhdr, pc->brec, pc->patch, pc->q1w, pc->N);
+                                                  (BatchHdr*)pc->bhdr, pc->brec, pc->star_rule, pc->patch_w, pc->N);
   note_launch();
   const int grid = S < 8 * num_sms() ? S : 8 * num_sms();
   k_core_pack<<<grid, 256, 0, s>>>(S, pc->pool, pc->star_off, pc->star_core, coff, pc->coreL);
@@ -2018,11 +2018,11 @@ static int pack_streams(spnet_pc_s* pc, DevArena& tmp, const std::vector<int32_t
   if (vb == 8)
     k_stream_pack<double><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_mesh,
                                                       pc->elem_ptr, pc->star_ptr, roff, (StarHdr*)pc->shdr,
-                                                      pc->iperm_star, pc->srec, pc->patch, pc->q1w, pc->N);
+                                                      pc->iperm_star, pc->srec, pc->star_rule, pc->patch_w, pc->N);
   else
     k_stream_pack<float><<<(S + 3) / 4, 128, 0, s>>>(S, mesh_of_pc(pc), pc->pool, pc->star_off, pc->star_mesh,
                                                      pc->elem_ptr, pc->star_ptr, roff, (StarHdr*)pc->shdr,
-                                                     pc->iperm_star, pc->srec, pc->patch, pc->q1w, pc->N);
+                                                     pc->iperm_star, pc->srec, pc->star_rule, pc->patch_w, pc->N);
   SPNET_CUDA_TRY(cudaGetLastError());
   // warps per block: as many as the shared-memory budget holds, at most eight
   const int64_t wb = stream_warp_bytes(vb, pc->max_star, pc->max_star > LARGE_STAR);
@@ -2169,8 +2169,8 @@ int pc_factor_stars(spnet_pc_s* pc) {
     A.next = counters;
     A.vbytes = 8;  // the set-up blobs keep FP64 values; the solve sections are packed later
     A.cap = acap;
-    A.patch = pc->patch;
-    A.q1w = pc->q1w;
+    A.patch = pc->star_rule;
+    A.q1w = pc->patch_w;
     A.N = pc->N;
     note_launch();
     ProfScope ps(KID_STAR_SYMBOLIC, s);

@@ -200,6 +200,9 @@ int check_flags(int* dflags, cudaStream_t s, const char* where) {
   if (h & FLAG_UNSORTED) return fail(SPNET_ERR_BAD_INPUT, w + ": column indices not strictly ascending");
   if (h & FLAG_STAR_BIG) return fail(SPNET_ERR_UNSUPPORTED, w + ": a star exceeds the local solver's capacity");
   if (h & FLAG_POOL) return fail(SPNET_ERR_NO_MEMORY, w + ": factor pool overflow");
+  if (h & FLAG_UNCOVERED)
+    return fail(SPNET_ERR_BAD_INPUT, w + ": a free dof lies in no star, so B is singular there (take stars at "
+                                         "every mesh node, SPNET_STARS_ALL)");
   return fail(SPNET_ERR_BAD_INPUT, w + ": invalid input (index out of range or malformed)");
 }
 

@@ -29,7 +29,8 @@ def pcg_rates(problem, reduction: float = 1e-8, max_steps: int = 300):
     op = spnet.Operator.from_problem(problem)
     pc = spnet.Preconditioner(op, problem.H, problem.gamma_faces, precision=spnet.PREC_FP64,
                               star_set=spnet.STARS_ALL if problem.star_set == "all" else spnet.STARS_INTERIOR,
-                              patch=problem.patch, flexible=0, max_restarts=0)
+                              patch=problem.patch, flexible=0, max_restarts=0,
+                              coarse=getattr(problem, "coarse", "q1"))
     import torch
     free = np.setdiff1d(np.arange(problem.n_dof), problem.dirichlet_dofs)
     hist = torch.empty((max_steps + 1, int(op.info.n_free)), dtype=torch.float64,

@@ -27,6 +27,7 @@ MODEL_SCALAR, MODEL_TRUSS3 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 STARS_INTERIOR, STARS_ALL = 0, 1
 PATCH_ELEMENT, PATCH_SUPPORT = 0, 1
+COARSE_Q1, COARSE_P1 = 0, 1
 EXPORT_ELEMENTS, EXPORT_Q1, EXPORT_COARSE_MAP, EXPORT_STAR_SIZES = 0, 1, 2, 3
 EXPORT_STAR_MESH, EXPORT_A0, EXPORT_STAR_LEVELS, EXPORT_STAR_CORE = 4, 5, 6, 7
 
@@ -55,7 +56,7 @@ class SpnetError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("star_set", C.c_int), ("flexible", C.c_int),
                 ("max_restarts", C.c_int), ("batch_rhs", C.c_int), ("star_map", C.c_int),
-                ("patch", C.c_int), ("no_panels", C.c_int), ("reserved", C.c_int * 8)]
+                ("patch", C.c_int), ("no_panels", C.c_int), ("coarse_space", C.c_int), ("reserved", C.c_int * 7)]
 
 
 class Request(C.Structure):
@@ -402,7 +403,8 @@ class Preconditioner:
     """setup_preconditioner: the two-level additive Schwarz preconditioner."""
 
     def __init__(self, op: Operator, H, gamma_faces, precision=PREC_MIXED, star_set=STARS_INTERIOR,
-                 flexible=-1, max_restarts=2, batch_rhs=1, star_map=0, patch=PATCH_ELEMENT, panels=True):
+                 flexible=-1, max_restarts=2, batch_rhs=1, star_map=0, patch=PATCH_ELEMENT, panels=True,
+                 coarse=COARSE_Q1):
         self._lib = op._lib
         self.op = op
         self.handle = C.c_void_p()
@@ -413,6 +415,7 @@ class Preconditioner:
         o.no_panels = 0 if panels else 1
         o.patch = patch if isinstance(patch, int) else (PATCH_SUPPORT if patch == "support"
                                                          else PATCH_ELEMENT)
+        o.coarse_space = coarse if isinstance(coarse, int) else (COARSE_P1 if coarse == "p1" else COARSE_Q1)
         gf = (C.c_int * 3)(*(list(gamma_faces) + [0, 0, 0])[:3])
         _check(self._lib.setup_preconditioner(op.handle, float(H), gf, C.byref(o),
                                               C.byref(self.handle)))
