@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--struct-which", default="pure_displacement,lateral_load",
                     help="--mode struct: which of the two problems to run")
     ap.add_argument("--mode", default="served", choices=["served", "single", "multi_rhs", "c5", "lap_conv",
-                                                          "struct"],
+                                                          "struct", "coarse_spaces"],
                     help="single: only the one-request-at-a-time measurement (for profiling runs)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
@@ -629,6 +629,8 @@ def run_gb300(args, rank, world, local):
 
     if args.mode == "lap_conv":  # the paper's heat experiments (Section 6.2, Table lap_conv)
         return dict(lap_conv=lap_conv_table())
+    if args.mode == "coarse_spaces":  # Q1 against P1 on simplices (Remark 2.1)
+        return dict(coarse_spaces=coarse_spaces())
     if args.mode == "struct":  # the structural experiments (Section 6.3, Tables struct2D, struct3d)
         return dict(struct=struct_tables(h_inv=tuple(int(v) for v in args.struct_hinv.split(",")),
                                          which=tuple(args.struct_which.split(","))))
@@ -766,8 +768,64 @@ def lap_conv_table(seed=6000):
                          "m0": r["m0"], "s": round(time.perf_counter() - t1, 2)})
         out[name] = rows
     out["note"] = ("rates tau_l = |e_l|_K / |e_{l-1}|_K for l >= 2 until |e_l|_K <= 1e-8 |e_0|_K; FP64 "
-                   "textbook PCG through the library (iterate l = the solve with maxit = l), reference "
-                   "solution at relres 1e-13; paper values from Table lap_conv")
+                   "textbook PCG through the library (the iterates of the reference solve at relres 1e-13, "
+                   "recorded on the device); paper values from Table lap_conv")
+    return out
+
+
+def coarse_spaces(seed=6000, nrhs=4):
+    """Q1 on the boxes against P1 on their Kuhn simplices (Remark 2.1), both through the
+    library with stars at every mesh node: the rates of the heat experiments (the (2^9+1)^2
+    grid and the uniform fibre network, support patches, as Table lap_conv), and the 3D
+    diffusion workload (40000 fibres, H = 1/16, element patches) solved to relres 1e-8 in
+    mixed precision, nrhs load cases f ~ U(0, 1) one at a time."""
+    from dataclasses import replace
+
+    from paper_2207_07488_gb300 import spnet
+    from paper_2207_07488_gb300.experiments import pcg_rates
+    out = {"rates": {}}
+    net = nw.fiber_heat_network(seed)
+    for name in ("grid", "fibre"):
+        rows = []
+        for Hinv in (16, 32):
+            p = nw.grid_heat_problem(9, 1.0 / Hinv) if name == "grid" else nw.fiber_heat_problem(net, 1.0 / Hinv)
+            row = {"H_inv": Hinv}
+            for space in ("q1", "p1"):
+                t1 = time.perf_counter()
+                r = pcg_rates(replace(p, coarse=space))
+                row[space] = {"tau_mean": round(r["mean"], 3), "tau_max": round(r["max"], 3), "steps": r["steps"],
+                              "m0": r["m0"], "s": round(time.perf_counter() - t1, 2)}
+                print(f"[coarse] {name} H^-1 = {Hinv} {space}: tau mean {r['mean']:.3f}, {r['steps']} steps",
+                      file=sys.stderr, flush=True)
+            rows.append(row)
+        out["rates"][name] = rows
+    p = replace(nw.config2(), star_set="all")
+    rng = np.random.default_rng(seed + 2)
+    F = rng.uniform(0.0, 1.0, size=(nrhs, p.n_dof))
+    sols = {}
+    res = {}
+    for space in ("q1", "p1"):
+        op = spnet.Operator.from_problem(p)
+        t0 = time.perf_counter()
+        pc = spnet.Preconditioner(op, p.H, p.gamma_faces, precision=spnet.PREC_MIXED, star_set=spnet.STARS_ALL,
+                                  coarse=space)
+        setup_s = time.perf_counter() - t0
+        spnet.pcg_solve(op, pc, F[0], p.dirichlet_vals, rtol=1e-8, maxit=2000)  # warm-up
+        t1 = time.perf_counter()
+        U, st = spnet.pcg_solve(op, pc, F, np.tile(p.dirichlet_vals, (nrhs, 1)), rtol=1e-8, maxit=2000)
+        solve_s = time.perf_counter() - t1
+        sols[space] = U
+        res[space] = {"setup_s": round(setup_s, 3), "solves_per_s": round(nrhs / solve_s, 2),
+                      "iterations": [int(s.iterations) for s in st], "relres": max(float(s.relres) for s in st),
+                      "m0": int(pc.info.m0), "stars": int(pc.info.n_stars)}
+        print(f"[coarse] c2 {space}: {res[space]}", file=sys.stderr, flush=True)
+        pc.close()
+        op.close()
+    res["relerr_p1_vs_q1"] = float(np.linalg.norm(sols["p1"] - sols["q1"]) / np.linalg.norm(sols["q1"]))
+    out["c2_all_stars"] = res
+    out["note"] = ("rates as in lap_conv; the c2 solves on the host clock around each call, host arrays; "
+                   "both spaces on the same mesh nodes (m0 equal), so the iteration counts compare the two "
+                   "interpolants")
     return out
 
 
@@ -884,6 +942,10 @@ def main():
     if args.mode == "lap_conv":
         if rank == 0:
             print(json.dumps({"mode": "lap_conv", "table": r["lap_conv"]}))
+        return
+    if args.mode == "coarse_spaces":
+        if rank == 0:
+            print(json.dumps({"mode": "coarse_spaces", "result": r["coarse_spaces"]}))
         return
     if args.mode == "struct":
         if rank == 0:

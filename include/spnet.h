@@ -66,10 +66,11 @@ extern "C" {
 #define SPNET_STARS_ALL 1       /* stars at every mesh node y_1..y_m (Section 4.1) */
 
 /* Which free dofs the star of mesh node y_j holds (Sections 2.3, 4.1). */
-#define SPNET_PATCH_ELEMENT 0  /* every dof whose half-open host element touches y_j: the
-                                  union of the (up to 2^d) elements around y_j */
-#define SPNET_PATCH_SUPPORT 1  /* only the dofs where the Q1 basis function of y_j is nonzero
-                                  (max-norm distance below H): the space the local parts
+#define SPNET_PATCH_ELEMENT 0  /* every dof whose host element touches y_j: Q1, the union of
+                                  the (up to 2^d) boxes around y_j; P1, the simplices that have
+                                  y_j as a vertex */
+#define SPNET_PATCH_SUPPORT 1  /* only the dofs where the basis function of y_j is nonzero
+                                  (Q1: max-norm distance below H): the space the local parts
                                   (v - I v) phi_j of the proof of Lemma 4.1 live in.  Differs
                                   from ELEMENT only at dofs on the outer boundary of the patch */
 
@@ -234,7 +235,9 @@ int build_network_operator(int dim, int ndof, int64_t n_nodes, const double* coo
  * is inverted in FP32 unless a pivot falls to 1e-3 of its diagonal entry or
  * below, in which case the inverse is formed in FP64 and rounded.  opts may be
  * NULL (defaults).  Errors: BAD_H, NOT_SPD (a local pivot <= 0), UNSUPPORTED
- * (a star beyond 65535 dofs), NO_MEMORY.
+ * (a star beyond 65535 dofs), NO_MEMORY, BAD_INPUT (an unknown option; or, with
+ * support patches or P1 element patches, a free dof that lies in no star, which
+ * would leave B singular there: take stars at every mesh node).
  */
 int setup_preconditioner(spnet_op_t op, double H, const int* gamma_faces,
                          const spnet_options* opts, spnet_pc_t* out);
