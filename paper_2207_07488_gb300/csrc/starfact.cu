@@ -240,10 +240,16 @@ __device__ inline int warp_incl_scan(int v, int lane) {
   return v;
 }
 
-// remove eliminated neighbours from the adjacency list of every alive node
-__device__ inline void compact_all(const Scratch& W, int n, int lane) {
+// remove the nodes eliminated in this round from the adjacency lists that hold them.
+// Those are the lists of the round's column entries c0..c1 (the alive neighbours of the
+// eliminated nodes; every other list holds alive nodes only), each marked once in sel
+// (free after the round's selection) and compacted in order by the lane that meets it.
+__device__ inline void compact_touched(const Scratch& W, int n, int lane, int c0, int c1) {
+  for (int q = c0 + lane; q < c1; q += 32) W.sel[W.colent[q]] = 2;
+  __syncwarp();
   for (int t = lane; t < n; t += 32) {
-    if (W.state[t] >= 0) continue;
+    if (W.sel[t] != 2) continue;
+    W.sel[t] = 0;
     uint16_t* lst = W.nbr + (int64_t)t * W.cap;
     int c = 0, d = W.deg[t];
     for (int q = 0; q < d; ++q) {
@@ -306,7 +312,6 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
     int npos = 0, nlev = 0, ncol = 0;
     bool dense = ovf;
     while (!dense && npos < n) {
-      compact_all(W, n, lane);
       int md = 1 << 30;  // over the nodes that may still be eliminated
       for (int t = lane; t < n; t += 32)
         if (W.state[t] == -1) md = min(md, W.deg[t]);
@@ -359,7 +364,7 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
       }
       W.colstart[npos] = ncol;
       __syncwarp();
-      compact_all(W, n, lane);
+      compact_touched(W, n, lane, W.colstart[lev_start], ncol);
       // fill among the neighbours of each eliminated node: every pair (a, b) of
       // a column of this round, 32 pairs at a time.  Lanes test adjacency in
       // parallel; pairs repeated inside a batch are merged; new list slots go
