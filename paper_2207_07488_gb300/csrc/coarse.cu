@@ -33,6 +33,7 @@
 namespace spnet {
 
 constexpr int NB = 64;   // pivot block, and the sub-tile a sweep block updates
+constexpr int SP = NB + 8;  // row pitch of the sweep's shared R and Tm slices (conflict-free fragments)
 constexpr int CT = 128;  // storage tile
 
 // ---------------------------------------------------------------------------
@@ -215,6 +216,25 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::);
 }
 
+// TF32 tensor-core products (mma.sync m16n8k8, FP32 accumulation) with each FP32 operand
+// split in a high and a low TF32 part: x = hi + lo, hi = tf32(x), lo = tf32(x - hi)
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_bits(x);
+  lo = tf32_bits(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_m16n8k8_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 template <class T>
 struct V4 {
   T v[4];
@@ -266,9 +286,9 @@ __global__ void __launch_bounds__(256) k_sweep(T* __restrict__ tiles, int nt, in
                                                int k0, const T* __restrict__ P, const T* __restrict__ R,
                                                const T* __restrict__ Tm, T* __restrict__ Pn, T* __restrict__ Rn,
                                                const double* __restrict__ diag0, double tol, int* ndrop) {
-  extern __shared__ __align__(16) char sm_sweep[];  // R and Tm slices, NB x NB each
-  T (*sR)[NB] = reinterpret_cast<T (*)[NB]>(sm_sweep);
-  T (*sT)[NB] = reinterpret_cast<T (*)[NB]>(sm_sweep + sizeof(T) * NB * NB);
+  extern __shared__ __align__(16) char sm_sweep[];  // R and Tm slices, NB rows of pitch SP each
+  T (*sR)[SP] = reinterpret_cast<T (*)[SP]>(sm_sweep);
+  T (*sT)[SP] = reinterpret_cast<T (*)[SP]>(sm_sweep + sizeof(T) * NB * SP);
   const int kp = k0 / NB;
   const bool has_next = (int64_t)(kp + 1) * NB < m0;
   // block -> sub-tile: block 0 takes the next pivot block, the rest go in order
@@ -302,23 +322,70 @@ __global__ void __launch_bounds__(256) k_sweep(T* __restrict__ tiles, int nt, in
   __syncthreads();
   const int kb = (int)((m0 - k0) < NB ? (m0 - k0) : NB);
   if (a != kp && b != kp) {
-    T acc[4][4];
+    if constexpr (sizeof(T) == 4) {
+      // the rank-kb product on the tensor cores: warp w forms rows 16 (w % 4) .. +16 and
+      // columns 32 (w / 4) .. +32 of sum_t R[t][i] Tm[t][j] as four 16 x 8 tiles, each
+      // product as lo*hi + hi*lo + hi*hi of the split operands; then the products go
+      // through shared memory (in place of the R slice) to the 4 x 4 layout of d
+      const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, tq = lane & 3;
+      const int ib = 16 * (w & 3), jb = 32 * (w >> 2);
+      float c[4][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+      for (int n8 = 0; n8 < 4; ++n8)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = (T)0;
-    for (int t = 0; t < kb; ++t) {
-      const V4<T> ri = ld4s(&sR[t][4 * ty]);
-      const V4<T> tj = ld4s(&sT[t][4 * tx]);
+        for (int e = 0; e < 4; ++e) c[n8][e] = 0.f;
+      for (int t0 = 0; t0 < kb; t0 += 8) {
+        const bool k0ok = t0 + tq < kb, k1ok = t0 + tq + 4 < kb;
+        uint32_t ah[4], al[4];
+        tf32_split(k0ok ? (float)sR[t0 + tq][ib + g] : 0.f, ah[0], al[0]);
+        tf32_split(k0ok ? (float)sR[t0 + tq][ib + g + 8] : 0.f, ah[1], al[1]);
+        tf32_split(k1ok ? (float)sR[t0 + tq + 4][ib + g] : 0.f, ah[2], al[2]);
+        tf32_split(k1ok ? (float)sR[t0 + tq + 4][ib + g + 8] : 0.f, ah[3], al[3]);
+#pragma unroll
+        for (int n8 = 0; n8 < 4; ++n8) {
+          uint32_t bh0, bl0, bh1, bl1;
+          tf32_split(k0ok ? (float)sT[t0 + tq][jb + 8 * n8 + g] : 0.f, bh0, bl0);
+          tf32_split(k1ok ? (float)sT[t0 + tq + 4][jb + 8 * n8 + g] : 0.f, bh1, bl1);
+          mma_m16n8k8_tf32(c[n8], al, bh0, bh1);
+          mma_m16n8k8_tf32(c[n8], ah, bl0, bl1);
+          mma_m16n8k8_tf32(c[n8], ah, bh0, bh1);
+        }
+      }
+      __syncthreads();  // every warp is done with the slices
+#pragma unroll
+      for (int n8 = 0; n8 < 4; ++n8) {
+        const int j = jb + 8 * n8 + 2 * tq;
+        sR[ib + g][j] = c[n8][0];
+        sR[ib + g][j + 1] = c[n8][1];
+        sR[ib + g + 8][j] = c[n8][2];
+        sR[ib + g + 8][j + 1] = c[n8][3];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const V4<T> pr = ld4s(&sR[4 * ty + u][4 * tx]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) d[u][v] -= pr.v[v];
+      }
+    } else {
+      T acc[4][4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] += ri.v[u] * tj.v[v];
+        for (int v = 0; v < 4; ++v) acc[u][v] = (T)0;
+      for (int t = 0; t < kb; ++t) {
+        const V4<T> ri = ld4s(&sR[t][4 * ty]);
+        const V4<T> tj = ld4s(&sT[t][4 * tx]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] += ri.v[u] * tj.v[v];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) d[u][v] -= acc[u][v];
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) d[u][v] -= acc[u][v];
   } else {
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -405,7 +472,7 @@ static int sweep_inverse(spnet_pc_s* pc, const double* A0, T* tiles, double tol,
   note_launch();
   k_pivot_inverse<T><<<1, 256, 0, s>>>(tiles, nt, 0, (int)(m0 < NB ? m0 : NB), P, diag0, tol, ndrop);
   const unsigned subtiles = (unsigned)n_upper_tiles(n64);
-  const size_t sweep_smem = 2 * sizeof(T) * NB * NB;
+  const size_t sweep_smem = 2 * sizeof(T) * NB * SP;
   if (sweep_smem > 48 * 1024) {
     static std::atomic<bool> attr_set[64];  // per device; the size depends only on T
     int dev = 0;
