@@ -173,3 +173,49 @@ def test_beam_free_block_spd_and_pcg_matches_direct(lateral):
     X = p.net.coords
     hi = np.nonzero(X[:, 0] >= 1.0)[0]
     np.testing.assert_allclose(res.u[3 * hi], 0.1 if lateral else 0.2)
+
+
+@pytest.mark.parametrize("lateral,seed,total", [(False, 17, 60.0), (False, 3, 60.0), (True, 17, 60.0),
+                                                (True, 0, 60.0)])
+def test_beam_networks_have_no_free_mechanism(lateral, seed, total):
+    """Networks on which, before the component prune, a fibre cluster hung from the clamped
+    sides at a single node (a pin about which the in-plane bending form lets it turn): after
+    beam_problem's pruning every component of the non-Dirichlet graph reaches two Dirichlet
+    nodes, and K on the free dofs is positive definite."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    net = nw.fiber_network_2d(0, 0.05, seed, midpoint_pad=0.025, keep="boundary", total_length=total,
+                              bias="placement" if lateral else "orientation")
+    p = nw.beam_problem(net, 0.25, lateral=lateral)
+    X = p.net.coords
+    dmask = (X[:, 0] <= 0.0) | (X[:, 0] >= 1.0)
+    E = p.net.edges
+    inner = ~dmask[E[:, 0]] & ~dmask[E[:, 1]]
+    n = p.net.n_nodes
+    G = sp.coo_matrix((np.ones(int(inner.sum())), (E[inner, 0], E[inner, 1])), shape=(n, n))
+    _, comp = connected_components(G, directed=False)
+    pins = {}
+    for a, b in E[dmask[E[:, 0]] ^ dmask[E[:, 1]]]:
+        free_end, pin = (b, a) if dmask[a] else (a, b)
+        pins.setdefault(comp[free_end], set()).add(pin)
+    for c in np.unique(comp[~dmask]):
+        assert len(pins.get(c, ())) >= 2, c
+    _, A, _ = op.split(p, op.assemble(p))
+    ev = np.linalg.eigvalsh(A.toarray())
+    # positive definite, well above rounding (edges of 5e-6 to 0.05 put cond(A) near 1e13;
+    # before the prune these networks had zero or negative eigenvalues of order 1e-5)
+    assert ev[0] > 1e-14 * ev[-1], (ev[0], ev[-1])
+
+
+def test_beam_parallel_edges_count_once():
+    """Two fibres between the same two merged joints give one edge of the beam problem, so no
+    bending triple pairs an edge with itself (y = z)."""
+    net = nw.fiber_network_2d(0, 0.05, 6100, midpoint_pad=0.025, keep="boundary", total_length=300.0,
+                              bias="orientation")
+    key = np.sort(net.edges, axis=1)
+    assert np.unique(key, axis=0).shape[0] < key.shape[0]   # the raw network has parallel edges
+    p = nw.beam_problem(net, 0.25, lateral=False)
+    key = np.sort(p.net.edges, axis=1)
+    assert np.unique(key, axis=0).shape[0] == key.shape[0]
+    T = p.meta["triples"]
+    assert np.all((T[:, 0] != T[:, 1]) & (T[:, 0] != T[:, 2]) & (T[:, 1] != T[:, 2]))
