@@ -240,7 +240,8 @@ __device__ inline int warp_incl_scan(int v, int lane) {
   return v;
 }
 
-// remove the nodes eliminated in this round from the adjacency lists that hold them.
+// remove the nodes eliminated by the current elimination step from the adjacency lists
+// that hold them.
 // Those are the lists of the round's column entries c0..c1 (the alive neighbours of the
 // eliminated nodes; every other list holds alive nodes only), each marked once in sel
 // (free after the round's selection) and compacted in order by the lane that meets it.
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(128) k_star_symbolic(StarArgs A) {
       __syncwarp();
       compact_touched(W, n, lane, W.colstart[lev_start], ncol);
       // fill among the neighbours of each eliminated node: every pair (a, b) of
-      // a column of this round, 32 pairs at a time.  Lanes test adjacency in
+      // a column of this elimination step, 32 pairs at a time.  Lanes test adjacency in
       // parallel; pairs repeated inside a batch are merged; new list slots go
       // by rank among the lanes that extend the same list (deterministic).  A
       // list that would pass CAP entries switches the rest to the dense core.
