@@ -23,6 +23,8 @@ schwarz   star spaces V_j = V(U(y_j)), exact local solves and the additive
 pcg       preconditioned conjugate gradients (Section 4.2), flexible variant,
           convergence rates tau_l (Section 6.2)
 solve     end-to-end solve of a problem
+analysis  the homogeneity sigma and the connectivity constant mu of the network
+          assumptions (Section 3.2, Lemma 3.5), as Section 6.1 evaluates them
 
 Readings of the paper that the oracle fixes (each is listed with its reason
 in the design notes of the repository):
